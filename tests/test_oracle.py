@@ -1,0 +1,492 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these checks compares the oracle with itself: each one uses a closed
+form, a textbook routine (numpy's Gauss-Laguerre, sympy's exact Laguerre roots,
+LAPACK's eigen-solver via numpy, scipy quadrature), an invariant of the method,
+a brute-force construction, or a value printed in the paper (tests/golden).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import appendix_a as A
+from paper_2011_06856_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ETA = np.diag([1.0, -1.0, -1.0])
+
+
+def U_of(beta_x, beta_y):
+    g = 1.0 / math.sqrt(1.0 - beta_x ** 2 - beta_y ** 2)
+    return np.array([g, g * beta_x, g * beta_y])
+
+
+def mj_tensors(n, T, U):
+    """N^a = n U^a and T^ab = (eps+P) U^a U^b - P eta^ab with eps = 2P = 2nT (Sec. 2.1-2.2)."""
+    P = n * T
+    eps = 2.0 * P
+    return n * U, (eps + P) * np.outer(U, U) - P * ETA
+
+
+def moments9_to_tensors(m):
+    N = m[0:3]
+    T = np.array([[m[3], m[4], m[5]], [m[4], m[6], m[7]], [m[5], m[7], m[8]]])
+    return N, T
+
+
+# --------------------------------------------------------------- quadrature
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 7])
+def test_radial_rule_matches_textbook_gauss_laguerre(N):
+    """Sec. 2.3: p_r = roots of L_{N+1}, w = p/((N+2)^2 L_{N+2}(p)^2) equal the
+    standard Gauss-Laguerre rule (numpy.polynomial.laguerre.laggauss)."""
+    p, w = O.radial_rule(N)
+    x, wx = np.polynomial.laguerre.laggauss(N + 1)
+    np.testing.assert_allclose(p, x, rtol=1e-13)
+    np.testing.assert_allclose(w, wx, rtol=1e-12)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_radial_rule_exact_roots_sympy(N):
+    sympy = pytest.importorskip("sympy")
+    xs = sympy.Symbol("x")
+    roots = sorted(sympy.Poly(sympy.laguerre(N + 1, xs), xs).nroots(n=30))
+    p, _ = O.radial_rule(N)
+    np.testing.assert_allclose(p, [float(r) for r in roots], rtol=2e-15, atol=0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5])
+def test_radial_rule_integrates_polynomials(N):
+    """Gauss-Laguerre with N+1 nodes integrates p^k e^{-p} exactly (= k!) for k <= 2N+1."""
+    p, w = O.radial_rule(N)
+    for k in range(2 * N + 2):
+        assert abs((w * p ** k).sum() - math.factorial(k)) <= 1e-12 * math.factorial(k)
+    k = 2 * N + 2
+    assert abs((w * p ** k).sum() - math.factorial(k)) > 1e-6 * math.factorial(k)
+
+
+def test_angular_integral_closed_form():
+    from scipy.integrate import quad
+    for a in range(0, 7):
+        for b in range(0, 7):
+            ref = quad(lambda t: math.cos(t) ** a * math.sin(t) ** b, 0, 2 * math.pi,
+                       limit=200, epsabs=1e-14)[0]
+            assert abs(O.angular_integral(a, b) - ref) < 1e-12
+
+
+@pytest.mark.parametrize("N,K", [(2, 5), (2, 16), (3, 7), (3, 12), (3, 64), (2, 48)])
+def test_product_rule_exactness(N, K):
+    """Eq. (quad-integrals): the product rule with rotated shells integrates
+    exp(-p) p^k cos^a sin^b (a+b <= k) exactly for k <= 2N; angular part
+    exact for trig degree < K on every shell whatever its rotation."""
+    q = O.Quadrature(N, K)
+    px, py = q.p0 * q.vx, q.p0 * q.vy
+    for k in range(2 * N + 1):
+        for a in range(k + 1):
+            for b in range(k + 1 - a):
+                e = k - a - b
+                s = (q.w * q.p0 ** e * px ** a * py ** b).sum()
+                ref = math.factorial(k) * O.angular_integral(a, b)
+                assert abs(s - ref) <= 1e-12 * max(1.0, abs(math.factorial(k))), (k, a, b)
+
+
+def test_shell_rotation_and_velocities():
+    """theta_ij = (j + i/(N+1)) 2 pi / K; |v| = 1; weights 2 pi/K times the radial weight."""
+    N, K = 3, 12
+    q = O.Quadrature(N, K)
+    p, wp = O.radial_rule(N)
+    for r in range(N + 1):
+        for j in range(K):
+            i = r * K + j
+            th = (j + r / (N + 1)) * 2 * math.pi / K
+            assert abs(math.atan2(q.vy[i], q.vx[i]) % (2 * math.pi) - th % (2 * math.pi)) < 1e-13
+            assert q.p0[i] == p[r]
+            assert abs(q.w[i] - wp[r] * 2 * math.pi / K) < 1e-16
+    assert np.allclose(q.vx ** 2 + q.vy ** 2, 1.0, atol=1e-15)
+    assert abs(q.w.sum() - 2 * math.pi) < 1e-13  # int e^{-p} dp dtheta = 2 pi
+
+
+def test_population_counts_golden():
+    """N_pop = K (N+1) (Sec. 2.3) for the sizes the paper prints."""
+    with open(os.path.join(GOLDEN, "paper_counts.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    assert rows
+    for N, K, npop, _src in rows:
+        assert O.Quadrature(int(N), int(K)).npop == int(npop)
+
+
+def test_quadrature_rejects_too_few_angles():
+    with pytest.raises(ValueError):
+        O.Quadrature(3, 6)  # K >= 2N+1 required
+
+
+def test_initial_states_golden_satisfy_eos():
+    """The paper's printed initial states obey P = n T (ideal EOS, Sec. 2.2)."""
+    with open(os.path.join(GOLDEN, "paper_initial_states.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    assert len(rows) == 6
+    for _prob, _reg, P, n, T, _bx, _by in rows:
+        assert abs(float(P) - float(n) * float(T)) < 1e-12
+
+
+# --------------------------------------------------------------- MJ moments
+
+def brute_mj_moment(idx, n, T, Ux, Uy):
+    """Direct numerical integral of f^MJ p^idx over d^2p/p0 = dp dtheta:
+    60-point Gauss-Laguerre in p (scaled to the decay rate) x 720-point trapezoid in theta."""
+    U0 = math.sqrt(1 + Ux * Ux + Uy * Uy)
+    th = np.arange(720) * 2 * math.pi / 720
+    c, s = np.cos(th), np.sin(th)
+    rate = (U0 - Ux * c - Uy * s) / T  # exp(-p rate)
+    x, wx = np.polynomial.laguerre.laggauss(60)
+    total = 0.0
+    for j in range(720):
+        p = x / rate[j]
+        comps = {0: p, 1: p * c[j], 2: p * s[j]}
+        prod = np.ones_like(p)
+        for a in idx:
+            prod = prod * comps[a]
+        total += (wx * prod).sum() / rate[j]
+    return n / (2 * math.pi * T * T) * total * (2 * math.pi / 720)
+
+
+@pytest.mark.parametrize("idx", [(), (0,), (1,), (2,), (0, 0), (0, 1), (1, 2), (2, 2),
+                                 (0, 0, 0), (0, 1, 2), (1, 1, 2), (2, 2, 2), (0, 1, 1, 2)])
+def test_mj_moment_vs_brute_integration(idx):
+    for (n, T, Ux, Uy) in [(0.7, 0.8, 0.3, -0.2), (1.3, 0.45, -0.6, 0.5), (0.2, 1.7, 0.0, 0.0)]:
+        got = O.mj_moment(idx, n, T, Ux, Uy)
+        ref = brute_mj_moment(idx, n, T, Ux, Uy)
+        assert abs(got - ref) <= 1e-11 * max(1.0, abs(ref)), (idx, got, ref)
+
+
+def test_mj_moment_eos_and_trace():
+    n, T, Ux, Uy = 0.9, 0.7, 0.4, -0.25
+    U = np.array([math.sqrt(1 + Ux * Ux + Uy * Uy), Ux, Uy])
+    Nref, Tref = mj_tensors(n, T, U)
+    for a in range(3):
+        assert abs(O.mj_moment((a,), n, T, Ux, Uy) - Nref[a]) < 1e-14
+        for b in range(3):
+            assert abs(O.mj_moment((a, b), n, T, Ux, Uy) - Tref[a, b]) < 1e-13
+    tr = O.mj_moment((0, 0), n, T, Ux, Uy) - O.mj_moment((1, 1), n, T, Ux, Uy) - \
+        O.mj_moment((2, 2), n, T, Ux, Uy)
+    assert abs(tr) < 1e-13  # massless: T^a_a = 0
+    assert abs(O.mj_moment((), n, T, Ux, Uy) - n / T) < 1e-14  # invariant scalar
+
+
+# --------------------------------------------------------------- equilibrium
+
+STATES = [(0.7, 0.8, 0.3, -0.2), (1.0, 1.0, 0.0, 0.0), (0.25, 0.6, 0.0, 0.0),
+          (1.4, 1.6, -0.45, 0.1), (0.1, 0.5, 0.05, 0.02)]
+
+
+@pytest.mark.parametrize("N,K", [(2, 16), (2, 48), (3, 12), (3, 64), (4, 9)])
+def test_feq_reproduces_conserved_moments(N, K):
+    """Eqs. (mj-feq-expansion-truncated), (discrete_sum_moments): for N >= 2 the
+    discrete equilibrium carries exactly N^a = n U^a and the ideal-gas T^ab."""
+    q = O.Quadrature(N, K)
+    for (n, T, bx, by) in STATES:
+        U = U_of(bx, by)
+        f = q.feq(n, T, U[1], U[2])
+        Nd, Td = moments9_to_tensors(q.moments(f))
+        Nr, Tr = mj_tensors(n, T, U)
+        np.testing.assert_allclose(Nd, Nr, atol=5e-14 * max(1, n))
+        np.testing.assert_allclose(Td, Tr, atol=5e-13 * max(1, n * T))
+
+
+def rank3(f, q):
+    p = np.stack([q.p0, q.p0 * q.vx, q.p0 * q.vy])
+    return np.einsum("i,ai,bi,ci->abc", f, p, p, p)
+
+
+def test_feq_third_moments_need_N3():
+    """Sec. 2.2: the truncated expansion keeps moments up to order N exactly:
+    rank-3 moments are exact at N = 3 and not at N = 2."""
+    n, T, bx, by = 0.8, 0.9, 0.35, -0.3
+    U = U_of(bx, by)
+    ref = np.zeros((3, 3, 3))
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                ref[a, b, c] = O.mj_moment((a, b, c), n, T, U[1], U[2])
+    q3 = O.Quadrature(3, 12)
+    np.testing.assert_allclose(rank3(q3.feq(n, T, U[1], U[2]), q3), ref, atol=1e-12)
+    q2 = O.Quadrature(2, 16)
+    assert np.abs(rank3(q2.feq(n, T, U[1], U[2]), q2) - ref).max() > 1e-4
+
+
+def test_feq_is_degree_N_polynomial_on_nodes():
+    """f^eq_i / w_i is a polynomial of degree <= N in p^mu: a least-squares fit
+    in the cone-monomial basis at the nodes has zero residual; and the weighted
+    residual of f^MJ/omega is orthogonal to every basis function (projection)."""
+    N, K = 3, 20
+    q = O.Quadrature(N, K)
+    e, a, b = q.basis()
+    P = np.stack([q.p0 ** ee * (q.p0 * q.vx) ** aa * (q.p0 * q.vy) ** bb
+                  for ee, aa, bb in zip(e, a, b)], 1)
+    n, T, bx, by = 0.6, 1.3, -0.2, 0.4
+    U = U_of(bx, by)
+    g = q.feq(n, T, U[1], U[2]) / q.w
+    coef, *_ = np.linalg.lstsq(P, g, rcond=None)
+    assert np.abs(P @ coef - g).max() < 1e-12 * np.abs(g).max()
+    # dense angular/radial integration of the projection residual
+    x, wx = np.polynomial.laguerre.laggauss(40)
+    th = np.arange(400) * 2 * math.pi / 400
+    pp, tt = np.meshgrid(x, th, indexing="ij")
+    fmj_over_w = n / (2 * math.pi * T * T) * np.exp(
+        -pp * (U[0] - U[1] * np.cos(tt) - U[2] * np.sin(tt)) / T + pp)
+    Bgrid = [pp ** ee * (pp * np.cos(tt)) ** aa * (pp * np.sin(tt)) ** bb for ee, aa, bb in zip(e, a, b)]
+    poly = sum(c * B for c, B in zip(coef, Bgrid))
+    resid = fmj_over_w - poly
+    for B in Bgrid:
+        ip = (wx[:, None] * resid * B).sum() * (2 * math.pi / 400)
+        assert abs(ip) < 1e-9, ip
+
+
+@pytest.mark.parametrize("N,K", [(2, 16), (3, 64)])
+def test_feq_rest_state_closed_form(N, K):
+    """At U = 0 and T = T0 = 1, f^MJ/omega = n/(2 pi) is constant, so f^eq_i = n w_i / (2 pi)."""
+    q = O.Quadrature(N, K)
+    for n in (1.0, 0.37):
+        np.testing.assert_allclose(q.feq(n, 1.0, 0.0, 0.0), n * q.w / (2 * math.pi), rtol=1e-13,
+                                   atol=1e-17)
+
+
+# --------------------------------------------------------------- Landau frame
+
+def test_landau_recovers_boosted_equilibria():
+    q = O.Quadrature(3, 24)
+    g = np.random.default_rng(5)
+    for _ in range(50):
+        n, T = g.uniform(0.05, 2.0), g.uniform(0.2, 2.0)
+        r, ph = g.uniform(0, 0.8), g.uniform(0, 2 * math.pi)
+        U = U_of(r * math.cos(ph), r * math.sin(ph))
+        st, mac = O.landau(q.moments(q.feq(n, T, U[1], U[2])))
+        assert st == 0
+        np.testing.assert_allclose(mac, [n, 2 * n * T, T, U[0], U[1], U[2]], rtol=1e-12, atol=1e-13)
+
+
+def test_landau_matches_lapack_on_random_states():
+    """eps U^a = T^ab U_b: compare with numpy.linalg.eig (LAPACK geev) of A = T eta."""
+    q = O.Quadrature(2, 16)
+    g = np.random.default_rng(11)
+    for _ in range(100):
+        f = g.uniform(0.0, 1.0, q.npop) * q.w
+        m = q.moments(f)
+        Nv, Tm = moments9_to_tensors(m)
+        A_ = Tm @ ETA
+        vals, vecs = np.linalg.eig(A_)
+        k = np.argmax(vals.real)
+        u = vecs[:, k].real
+        u = u / math.sqrt(u[0] ** 2 - u[1] ** 2 - u[2] ** 2) * np.sign(u[0])
+        st, mac = O.landau(m)
+        assert st == 0
+        assert abs(mac[1] - vals[k].real) < 1e-12 * abs(vals[k].real)
+        np.testing.assert_allclose(mac[3:], u, rtol=1e-10, atol=1e-12)
+        assert abs(mac[0] - (u[0] * Nv[0] - u[1] * Nv[1] - u[2] * Nv[2])) < 1e-12
+        assert abs(mac[2] - mac[1] / (2 * mac[0])) < 1e-14
+
+
+def test_landau_flags_unphysical_state():
+    # negative energy density: no timelike eigenvector with eps > 0
+    st, _ = O.landau(np.array([1.0, 0, 0, -1.0, 0, 0, -0.5, 0, -0.5]))
+    assert st == 1
+
+
+# --------------------------------------------------------------- stream / collide
+
+@pytest.mark.parametrize("N,K", [(2, 16), (3, 12)])
+def test_collision_conserves_N0_and_T0nu(N, K):
+    """Anderson-Witting with Landau-frame (n, eps, U): sum p^0 df = 0 and
+    sum p^0 p^nu df = 0; the spatial particle current is not conserved."""
+    q = O.Quadrature(N, K)
+    f = W.random_populations(q.npop, 3, 4, seed=3) * q.w[:, None, None]
+    fn, flagged = q.collide(f, tau=1.7)
+    assert flagged == 0
+    d = (fn - f).reshape(q.npop, -1)
+    fr = f.reshape(q.npop, -1)
+    for wgt in [q.p0, q.p0 * q.p0, q.p0 * q.p0 * q.vx, q.p0 * q.p0 * q.vy]:
+        scale = (np.abs(wgt)[:, None] * fr).sum(0)
+        assert (np.abs((wgt[:, None] * d).sum(0)) / scale).max() < 5e-14
+    assert np.abs(((q.p0 * q.vx)[:, None] * d).sum(0)).max() > 1e-6
+
+
+def test_collision_printed_sign_is_antirelaxing():
+    """Eq. (collision) as printed (+omega) moves f away from f^eq; the relaxing sign of
+    Eq. (discrete-rbe) moves it toward f^eq."""
+    q = O.Quadrature(2, 16)
+    f = W.random_populations(q.npop, 1, 1, seed=9)[:, 0, 0] * q.w
+    st, mac = O.landau(q.moments(f))
+    feq = q.feq(mac[0], mac[2], mac[4], mac[5])
+    fn, _ = q.collide(f.reshape(-1, 1, 1), tau=4.0)
+    assert np.linalg.norm(fn[:, 0, 0] - feq) < np.linalg.norm(f - feq)
+
+
+@pytest.mark.parametrize("bcx,bcy", [(O.BC_PERIODIC, O.BC_PERIODIC), (O.BC_COPYOUT, O.BC_COPYOUT),
+                                     (O.BC_COPYOUT, O.BC_PERIODIC)])
+def test_uniform_equilibrium_is_fixed_point(bcx, bcy):
+    q = O.Quadrature(2, 16)
+    fl = W.uniform(6, 5, 0.8, 0.7, 0.2, -0.15)
+    f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
+    f1, flagged = q.run(f0, tau=3.0, nsteps=5, bcx=bcx, bcy=bcy)
+    assert flagged == 0
+    np.testing.assert_allclose(f1, f0, rtol=1e-12, atol=1e-15)
+
+
+def test_periodic_streaming_conserves_population_sums():
+    q = O.Quadrature(2, 16)
+    f = W.random_populations(q.npop, 7, 9, seed=2)
+    fs = q.stream(f, O.BC_PERIODIC, O.BC_PERIODIC)
+    np.testing.assert_allclose(fs.sum((1, 2)), f.sum((1, 2)), rtol=1e-13)
+
+
+def test_axis_aligned_population_shifts_one_cell():
+    """A population with v = (1, 0) moves exactly one cell toward +x per step
+    (Eq. streaming: f*(x) = f(x - v dt)); v = (0, 1) one cell toward +y."""
+    q = O.Quadrature(2, 16)  # shell 0, j = 0: theta = 0; j = 4: theta = pi/2
+    f = W.random_populations(q.npop, 5, 6, seed=4)
+    fs = q.stream(f, O.BC_PERIODIC, O.BC_PERIODIC)
+    assert q.vx[0] == 1.0 and q.vy[0] == 0.0
+    np.testing.assert_array_equal(fs[0], np.roll(f[0], 1, axis=1))
+    assert q.vx[4] == 0.0 and q.vy[4] == 1.0
+    np.testing.assert_array_equal(fs[4], np.roll(f[4], 1, axis=0))
+    assert q.vx[8] == -1.0
+    np.testing.assert_array_equal(fs[8], np.roll(f[8], -1, axis=1))
+
+
+def binomial_ballistic(f0, q, nsteps):
+    """Exact n-step solution of the bilinear pull on a periodic grid: the
+    operator is the tensor product of two 1D upwind operators, so
+    f^n(x) = sum_k,l C(n,k) ax^k (1-ax)^(n-k) C(n,l) ay^l (1-ay)^(n-l) f^0(x - sx k, y - sy l)."""
+    out = np.zeros_like(f0)
+    from math import comb
+    for i in range(q.npop):
+        ax, ay = abs(q.vx[i]), abs(q.vy[i])
+        sx = 1 if q.vx[i] >= 0 else -1
+        sy = 1 if q.vy[i] >= 0 else -1
+        acc = np.zeros_like(f0[i])
+        for k in range(nsteps + 1):
+            cx = comb(nsteps, k) * ax ** k * (1 - ax) ** (nsteps - k)
+            if cx == 0.0:
+                continue
+            for l in range(nsteps + 1):
+                cy = comb(nsteps, l) * ay ** l * (1 - ay) ** (nsteps - l)
+                if cy == 0.0:
+                    continue
+                acc += cx * cy * np.roll(np.roll(f0[i], sx * k, axis=1), sy * l, axis=0)
+        out[i] = acc
+    return out
+
+
+def test_ballistic_exact_binomial_form():
+    q = O.Quadrature(2, 16)
+    f0 = W.random_populations(q.npop, 9, 11, seed=6)
+    nsteps = 7
+    fn, _ = q.run(f0, tau=math.inf, nsteps=nsteps, bcx=O.BC_PERIODIC, bcy=O.BC_PERIODIC)
+    np.testing.assert_allclose(fn, binomial_ballistic(f0, q, nsteps), rtol=1e-13, atol=1e-15)
+
+
+def dense_stream_matrix(q, nx, ny, bcx, bcy, i):
+    """Streaming of population i as an explicit (S x S) matrix of interpolation weights."""
+    S = nx * ny
+    M = np.zeros((S, S))
+    ax, ay = abs(q.vx[i]), abs(q.vy[i])
+    sx = 1 if q.vx[i] >= 0 else -1
+    sy = 1 if q.vy[i] >= 0 else -1
+
+    def wrap(v, L, bc):
+        return v % L if bc == O.BC_PERIODIC else min(max(v, 0), L - 1)
+    for y in range(ny):
+        for x in range(nx):
+            for (dx, wxx) in ((0, 1 - ax), (sx, ax)):
+                for (dy, wyy) in ((0, 1 - ay), (sy, ay)):
+                    M[y * nx + x, wrap(y - dy, ny, bcy) * nx + wrap(x - dx, nx, bcx)] += wxx * wyy
+    return M
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 1), (3, 2), (5, 4)])
+@pytest.mark.parametrize("bcx,bcy", [(O.BC_PERIODIC, O.BC_PERIODIC), (O.BC_COPYOUT, O.BC_COPYOUT)])
+def test_tiny_grids_dense_formulation(nx, ny, bcx, bcy):
+    """Brute force: stream as a dense matrix per population, then the same
+    collision; a full step must agree with the oracle's step."""
+    q = O.Quadrature(2, 16)
+    f = W.random_populations(q.npop, ny, nx, seed=nx * 10 + ny) * q.w[:, None, None]
+    fs = np.stack([(dense_stream_matrix(q, nx, ny, bcx, bcy, i) @ f[i].ravel()).reshape(ny, nx)
+                   for i in range(q.npop)])
+    np.testing.assert_allclose(q.stream(f, bcx, bcy), fs, rtol=1e-14, atol=1e-16)
+    ref, _ = q.collide(fs, tau=2.5)
+    got, _ = q.run(f, tau=2.5, nsteps=1, bcx=bcx, bcy=bcy)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-16)
+    # Stream matrices are stochastic (rows sum to 1): mass-like sums are preserved under uniform data
+    for i in range(q.npop):
+        M = dense_stream_matrix(q, nx, ny, bcx, bcy, i)
+        np.testing.assert_allclose(M.sum(1), 1.0, atol=1e-15)
+
+
+def test_single_site_relaxation_to_closed_form_equilibrium():
+    """A 1x1 periodic site only collides; it must converge to the equilibrium
+    with the same N^0 and T^{0nu}: with E = T^00, M = |T^0i|,
+    beta = (3E - sqrt(9E^2 - 8M^2)) / (2M), eps = 2E / (3 gamma^2 - 1), n = N^0 / gamma."""
+    q = O.Quadrature(2, 16)
+    g = np.random.default_rng(21)
+    f = g.uniform(0.05, 1.0, q.npop) * q.w * (1 + 0.8 * q.vx)
+    m0 = q.moments(f)
+    E, Mx, My = m0[3], m0[4], m0[5]
+    M = math.hypot(Mx, My)
+    beta = (3 * E - math.sqrt(9 * E * E - 8 * M * M)) / (2 * M)
+    gam = 1 / math.sqrt(1 - beta * beta)
+    eps = 2 * E / (3 * gam * gam - 1)
+    n = m0[0] / gam
+    fn, flagged = q.run(f.reshape(-1, 1, 1), tau=2.0, nsteps=400, bcx=O.BC_PERIODIC,
+                        bcy=O.BC_PERIODIC)
+    assert flagged == 0
+    st, mac = O.landau(q.moments(fn[:, 0, 0]))
+    assert abs(mac[0] - n) < 1e-10 and abs(mac[1] - eps) < 1e-10
+    assert abs(mac[4] / mac[3] - beta * Mx / M) < 1e-10
+    assert abs(mac[5] / mac[3] - beta * My / M) < 1e-10
+    np.testing.assert_allclose(fn[:, 0, 0], q.feq(mac[0], mac[2], mac[4], mac[5]), rtol=1e-9,
+                               atol=1e-13)
+
+
+# --------------------------------------------------------------- Appendix A
+
+def test_appendix_a_corrected_against_discrete_velocity_limit():
+    """Appendix A (free streaming, continuous velocities) equals the K -> inf limit
+    of discrete-velocity free streaming; the printed T^tt does not (misprint)."""
+    nL, TL, nR, TR = 1.0, 1.0, 0.2, 0.5
+    PL, PR = nL * TL, nR * TR
+    q = O.Quadrature(2, 4096)
+    fL = q.feq(nL, TL, 0.0, 0.0)
+    fR = q.feq(nR, TR, 0.0, 0.0)
+    w = np.linspace(-0.97, 0.97, 41)
+    disc = A.discrete_velocity_moments(w, 1.0, q.p0, q.vx, q.vy, fL, fR)
+    cont = A.continuum_moments(w, nL, PL, nR, PR)
+    np.testing.assert_allclose(disc, cont, atol=3e-3)
+    printed = A.printed_Ttt(w, PL, PR)
+    assert np.abs(printed - disc[3]).max() > 0.5
+    # end states: T^tt = eps = 2P on both sides
+    assert abs(A.continuum_moments(np.array([-1.0]), nL, PL, nR, PR)[3][0] - 2 * PL) < 1e-15
+    assert abs(A.continuum_moments(np.array([1.0]), nL, PL, nR, PR)[3][0] - 2 * PR) < 1e-15
+
+
+@pytest.mark.slow
+def test_lattice_ballistic_sod_approaches_appendix_a():
+    """Tolerance only (no parity): the tau -> inf lattice run of the 1D Sod tube is
+    close to the Appendix A velocity profile (relative L2 error, Eq. rel_err)."""
+    nx, steps = 800, 300
+    q = O.Quadrature(3, 64)
+    fl = W.shock_tube(nx, 1, (1.0, 1.0), (0.2, 0.5))
+    f, _ = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), math.inf, steps)
+    mac, _ = q.macro(f)
+    beta = mac[4, 0] / mac[3, 0]
+    x = np.arange(nx) + 0.5 - nx / 2
+    cont = A.continuum_moments(x / steps, 1.0, 1.0, 0.2, 0.1)
+    betas = []
+    for s in range(nx):
+        st, m = O.landau(cont[:, s])
+        betas.append(m[4] / m[3])
+    betas = np.array(betas)
+    err = np.linalg.norm(beta - betas) / np.linalg.norm(betas)
+    assert err < 0.01, err
