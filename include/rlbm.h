@@ -1,0 +1,148 @@
+/*
+ * rlbm.h -- C ABI of librlbm.so: the fused streaming + Anderson-Witting
+ * collision step of the relativistic lattice Boltzmann method for a massless
+ * gas in (2+1) dimensions (Bazzanini, Gabbana, Simeoni, Succi, Tripiccione,
+ * arXiv 2011.06856), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: lattice units, dx = dy = dt = 1, c = 1 (Sec. 2).  tau is the
+ *   relaxation time in time steps; tau = +INFINITY is the free-streaming
+ *   (ballistic) limit used in Fig. 2 and Appendix A.
+ * Quadrature (Sec. 2.3, Eq. off-lattice-quad): order N, N+1 radial
+ *   Gauss-Laguerre nodes p_r (roots of L_{N+1}), K angles per shell,
+ *   theta_rj = (j + r/(N+1)) 2 pi / K, N_pop = K (N+1), shell-major
+ *   population index i = r K + j.  Requires N >= 2 (the collision conserves
+ *   N^0 and T^{0 nu} only from N = 2 on) and K >= 2N+1.
+ * Populations: structure of arrays f[i][y][x], x fastest, S = nx * ny sites.
+ *   Precision RLBM_FP64 / RLBM_FP32 stores f_i itself.  RLBM_FP16_DEV /
+ *   RLBM_BF16_DEV store the deviation h_i = f_i / w_i - 1/(2 pi) from the
+ *   rest equilibrium at n = 1, T = 1 (for which f_i = w_i / (2 pi) exactly),
+ *   rounded to nearest; arithmetic is FP32.
+ * Macroscopic fields: double arrays of S values, [y][x].  Velocities are
+ *   given as beta = (u_x, u_y), |beta| < 1; U^a = gamma (1, beta).
+ * Pointers: "host" pointers are ordinary CPU memory, "device" pointers are
+ *   CUDA global memory on the handle's device.  Host arrays are owned by the
+ *   caller and only accessed during the call.
+ * Streams: all GPU work of a handle is issued on the stream given at
+ *   creation (NULL: a private non-blocking stream the library creates).
+ *   Entry points that take or return host data synchronise that stream.
+ * Errors: every entry point returns an rlbm_status; nothing aborts or traps.
+ *   rlbm_last_error() gives the message of the latest failure of a handle.
+ *   A non-physical cell (no timelike eigenvector, n <= 0 or eps <= 0) sets a
+ *   device status word; the next synchronising call returns
+ *   RLBM_ERR_UNPHYSICAL (and clears it).
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlbm rlbm_t; /* opaque handle, owned by the library */
+
+typedef enum {
+    RLBM_OK = 0,
+    RLBM_ERR_ARG = 1,        /* invalid argument; nothing was changed */
+    RLBM_ERR_CUDA = 2,       /* a CUDA runtime call failed; see rlbm_last_error */
+    RLBM_ERR_OOM = 3,        /* device allocation failed */
+    RLBM_ERR_UNPHYSICAL = 4, /* a cell had no physical Landau frame */
+    RLBM_ERR_TIMEOUT = 5,    /* a bounded device wait ran out */
+    RLBM_ERR_UNSUPPORTED = 6 /* valid but not built (e.g. an (N, K) with no kernel) */
+} rlbm_status;
+
+typedef enum { RLBM_FP64 = 0, RLBM_FP32 = 1, RLBM_FP16_DEV = 2, RLBM_BF16_DEV = 3 } rlbm_precision;
+
+typedef enum { RLBM_BC_PERIODIC = 0, RLBM_BC_COPYOUT = 1 } rlbm_bc;
+
+/* Grid and boundary conditions.  Periodic wraps the source index of the
+ * streaming pull; copy-out clamps it into the grid (zero-gradient ghost cell). */
+typedef struct {
+    int nx, ny;
+    int bc_x, bc_y; /* rlbm_bc */
+} rlbm_grid;
+
+/* Quadrature tables of Sec. 2.3, Eq. (off-lattice-quad): for N >= 0 and
+ * K >= 2N+1, writes N_pop = K (N+1) values to each host array:
+ * p0 = p_r, vx = cos theta_rj, vy = sin theta_rj, w = w^(p)_r 2 pi / K with
+ * w^(p)_r = p_r / ((N+2)^2 L_{N+2}(p_r)^2).  Any pointer may be NULL. */
+rlbm_status rlbm_quadrature(int order_N, int angles_K, double *p0, double *vx, double *vy,
+                            double *w);
+
+/* Bytes of ONE population buffer (N_pop * nx * ny elements of the storage
+ * type); the handle uses two of them (ping-pong, pull streaming). */
+size_t rlbm_population_bytes(rlbm_grid grid, int order_N, int angles_K, int precision);
+
+/* Create a handle for one problem.  Validates N >= 2, K >= 2N+1, nx, ny >= 1,
+ * tau > 0 (or +INFINITY), bc values and precision; RLBM_ERR_ARG otherwise.
+ * dev_buffers: optional caller-owned device memory of at least
+ * 2 * rlbm_population_bytes() bytes, 256-byte aligned, holding both
+ * population buffers (it must outlive the handle); NULL makes the library
+ * allocate and own them.  The handle always allocates its small constant
+ * tables and a status word.  cuda_stream: a cudaStream_t or NULL. */
+rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K, double tau,
+                        int precision, void *cuda_stream, void *dev_buffers,
+                        size_t dev_buffer_bytes);
+
+void rlbm_destroy(rlbm_t *h);
+
+/* Message of the most recent failure on h (or of the last failed create when
+ * h is NULL).  Valid until the next call on h. */
+const char *rlbm_last_error(const rlbm_t *h);
+
+/* Equilibrium initial state, f_i = f^eq_i(n, T, U) of Eq.
+ * (mj-feq-expansion-truncated) at every site, from host fields (S doubles
+ * each).  Resets the step counter.  Synchronises the stream. */
+rlbm_status rlbm_init(rlbm_t *h, const double *n, const double *T, const double *beta_x,
+                      const double *beta_y);
+
+/* Same from device fields; asynchronous on the handle's stream. */
+rlbm_status rlbm_init_device(rlbm_t *h, const double *d_n, const double *d_T,
+                             const double *d_beta_x, const double *d_beta_y);
+
+/* Advance nsteps >= 0 time steps, asynchronously.  One step is Sec. 2.2 in
+ * order: bilinear pull streaming (Eqs. streaming, interpolation), moments
+ * N^a, T^ab of the streamed populations (Eq. discrete_sum_moments), the
+ * Landau frame eps U^a = T^ab U_b with n = U_a N^a and T = eps/(2n), the
+ * truncated equilibrium, and relaxation f <- f* - (p.U / p^0 tau)(f* - f^eq)
+ * (Eq. discrete-rbe), fused in one kernel per step (one read and one write
+ * of every population).  Steps are replayed from a captured CUDA graph. */
+rlbm_status rlbm_step(rlbm_t *h, int nsteps);
+
+/* Landau-frame fields of the stored populations (no streaming): n, eps, T,
+ * U^0, U^x, U^y, S doubles each.  Host pointers; synchronises; reports and
+ * clears RLBM_ERR_UNPHYSICAL. */
+rlbm_status rlbm_moments(rlbm_t *h, double *n, double *eps, double *T, double *U0, double *Ux,
+                         double *Uy);
+
+/* Same into device pointers, asynchronously (no status check). */
+rlbm_status rlbm_moments_device(rlbm_t *h, double *d_n, double *d_eps, double *d_T,
+                                double *d_U0, double *d_Ux, double *d_Uy);
+
+/* Checkpoint / resume: copy the current population buffer (raw storage
+ * format, rlbm_population_bytes() bytes) to or from host memory.  Both
+ * synchronise.  set also restores the step counter to `step`. */
+rlbm_status rlbm_get_populations(rlbm_t *h, void *host, size_t bytes);
+rlbm_status rlbm_set_populations(rlbm_t *h, const void *host, size_t bytes, long long step);
+
+/* Device address of the current population buffer (valid until the next
+ * rlbm_step) and the number of completed steps. */
+void *rlbm_current_buffer(rlbm_t *h);
+long long rlbm_steps_done(const rlbm_t *h);
+
+/* Wait for the handle's stream; returns RLBM_ERR_UNPHYSICAL (and clears the
+ * flag) if any cell was non-physical since the last check. */
+rlbm_status rlbm_sync(rlbm_t *h);
+
+/* Number of kernel launches the handle has issued (graph replays count
+ * every kernel node). */
+long long rlbm_kernel_launches(const rlbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLBM_H */

@@ -1,0 +1,708 @@
+// Host side of librlbm.so: quadrature and projection tables (Sec. 2.3,
+// Sec. 2.2), handle management and the C ABI of include/rlbm.h.
+//
+// The quadrature is computed here independently of any other component:
+// Gauss-Laguerre nodes are the eigenvalues of the Laguerre Jacobi matrix
+// (Golub-Welsch), found by Sturm-sequence bisection and polished by Newton
+// steps on L_{N+1}; weights use the closed form printed in Sec. 2.3.
+#include "rlbm.h"
+#include "rlbm_args.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------- quadrature
+
+// L_n(x) and L_{n-1}(x) by the three-term recurrence.
+void laguerre_pair(int n, double x, double &ln, double &lnm1)
+{
+    double a = 1.0, b = 1.0 - x; // L_0, L_1
+    if (n == 0) { ln = 1.0; lnm1 = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        const double c = ((2.0 * k + 1.0 - x) * b - k * a) / (k + 1.0);
+        a = b;
+        b = c;
+    }
+    ln = b;
+    lnm1 = a;
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal Jacobi matrix of
+// the Laguerre weight (diagonal 2k+1, off-diagonal k), by Sturm sequence.
+int sturm_count(int n, double x)
+{
+    int cnt = 0;
+    double d = 1.0;
+    for (int k = 0; k < n; ++k) {
+        const double off2 = (k == 0) ? 0.0 : double(k) * double(k);
+        d = (2.0 * k + 1.0 - x) - (k == 0 ? 0.0 : off2 / d);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Gauss-Laguerre nodes (roots of L_n) in increasing order.
+std::vector<double> laguerre_nodes(int n)
+{
+    std::vector<double> x(n);
+    const double hi0 = 4.0 * n + 2.0; // Gershgorin bound: (2n-1) + 2(n-1) < 4n
+    for (int k = 0; k < n; ++k) {
+        double lo = 0.0, hi = hi0;
+        // k-th eigenvalue: smallest x with sturm_count(x) >= k+1
+        for (int it = 0; it < 2000; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (sturm_count(n, mid) >= k + 1) hi = mid; else lo = mid;
+        }
+        double r = 0.5 * (lo + hi);
+        for (int it = 0; it < 3; ++it) { // Newton: x L_n' = n (L_n - L_{n-1})
+            double ln, lnm1;
+            laguerre_pair(n, r, ln, lnm1);
+            const double d = n * (ln - lnm1) / r;
+            if (d == 0.0) break;
+            const double step = ln / d;
+            if (!std::isfinite(step)) break;
+            r -= step;
+        }
+        x[k] = r;
+    }
+    return x;
+}
+
+// Cholesky inverse of a small SPD matrix (row-major); false if not SPD.
+bool spd_inverse(int n, const std::vector<double> &A, std::vector<double> &inv)
+{
+    std::vector<double> L(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (s <= 0.0) return false;
+                L[i * n + i] = std::sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    inv.assign(n * n, 0.0);
+    for (int c = 0; c < n; ++c) { // solve L L^T x = e_c
+        std::vector<double> z(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i * n + k] * z[k];
+            z[i] = s / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = z[i];
+            for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * inv[k * n + c];
+            inv[i * n + c] = s / L[i * n + i];
+        }
+    }
+    return true;
+}
+
+double factorial(int k)
+{
+    double r = 1.0;
+    for (int i = 2; i <= k; ++i) r *= i;
+    return r;
+}
+
+struct Quad {
+    int N = 0, K = 0, npop = 0;
+    std::vector<double> pr, wr;            // radial nodes / weights (N+1)
+    std::vector<double> p0, vx, vy, w;     // per population
+};
+
+bool make_quadrature(int N, int K, Quad &q)
+{
+    if (N < 0 || N > 12 || K < 2 * N + 1) return false;
+    q.N = N;
+    q.K = K;
+    q.npop = K * (N + 1);
+    q.pr = laguerre_nodes(N + 1);
+    q.wr.resize(N + 1);
+    for (int r = 0; r <= N; ++r) { // w^(p)_r = p_r / ((N+2)^2 L_{N+2}(p_r)^2)
+        double l, lm1;
+        laguerre_pair(N + 2, q.pr[r], l, lm1);
+        q.wr[r] = q.pr[r] / ((N + 2.0) * (N + 2.0) * l * l);
+    }
+    q.p0.resize(q.npop);
+    q.vx.resize(q.npop);
+    q.vy.resize(q.npop);
+    q.w.resize(q.npop);
+    for (int r = 0; r <= N; ++r)
+        for (int j = 0; j < K; ++j) {
+            const int i = r * K + j;
+            const double th = (j + r / double(N + 1)) * (2.0 * kPi / K);
+            double c = std::cos(th), s = std::sin(th);
+            if (std::fabs(c) < 1e-15) c = 0.0; // exact axis directions
+            if (std::fabs(s) < 1e-15) s = 0.0;
+            q.p0[i] = q.pr[r];
+            q.vx[i] = c;
+            q.vy[i] = s;
+            q.w[i] = q.wr[r] * (2.0 * kPi / K);
+        }
+    return true;
+}
+
+// ---------------------------------------------------------------- handle
+
+size_t storage_size(int prec)
+{
+    switch (prec) {
+    case RLBM_FP64: return 8;
+    case RLBM_FP32: return 4;
+    case RLBM_FP16_DEV:
+    case RLBM_BF16_DEV: return 2;
+    default: return 0;
+    }
+}
+
+} // namespace
+
+struct rlbm {
+    rlbm_grid grid{};
+    int N = 0, K = 0, npop = 0, prec = 0;
+    double tau = 0.0;
+    Quad q;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *buf = nullptr; // 2 population buffers
+    bool own_buf = false;
+    size_t pop_bytes = 0;
+    int cur = 0; // index of the buffer holding the current state
+    long long steps = 0;
+    long long launches = 0;
+    void *d_tabs = nullptr; // poptab | shelltab | rtab
+    int *d_status = nullptr;
+    rlbmk::KernelArgs base{};
+    int P = 0, Gs = 0, G = 0;
+    bool site_fp64 = false;
+    // CUDA graphs of kGraphSteps steps starting from buffer 0 / buffer 1
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+constexpr int kGraphSteps = 32;
+
+rlbm_status fail(rlbm_t *h, rlbm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return st;
+}
+
+rlbm_status cuda_fail(rlbm_t *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? RLBM_ERR_OOM : RLBM_ERR_CUDA, "%s: %s (%s)",
+                what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define RLBM_CUDA(h, call)                                                                       \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);                                   \
+    } while (0)
+
+// Pick P (populations per warp, one of the compiled sizes) and Gs (warps per
+// energy shell, G = Gs (N+1) warps per CTA): fewest idle population slots,
+// then the larger P (fewer warps sharing the per-site work).
+bool choose_tiling(int N, int K, int &P, int &Gs)
+{
+    static const int sizes[] = {8, 12, 16, 24, 32};
+    int best_waste = 1 << 30;
+    bool found = false;
+    for (int gs = 1; gs * (N + 1) <= rlbmk::kMaxWarps; ++gs) {
+        const int need = (K + gs - 1) / gs;
+        if (need > 32 || (gs - 1) * need >= K) continue;
+        int p = 0;
+        for (int s : sizes)
+            if (s >= need) { p = s; break; }
+        const int waste = gs * p - K;
+        if (waste < best_waste || (waste == best_waste && p > P)) {
+            best_waste = waste;
+            P = p;
+            Gs = gs;
+            found = true;
+        }
+    }
+    return found;
+}
+
+template <class T>
+void put(std::vector<unsigned char> &blob, size_t off, const std::vector<double> &v)
+{
+    for (size_t i = 0; i < v.size(); ++i) {
+        T t = T(v[i]);
+        std::memcpy(blob.data() + off + i * sizeof(T), &t, sizeof(T));
+    }
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+rlbm_status build_tables(rlbm_t *h)
+{
+    const int N = h->N, K = h->K, npop = h->npop;
+    const Quad &q = h->q;
+    const bool dev = (h->prec == RLBM_FP16_DEV || h->prec == RLBM_BF16_DEV);
+    const double beta = dev ? 1.0 / (2.0 * kPi) : 0.0;
+    const int TW = rlbmk::tab_width(N);
+
+    // per-population table in stored units: f_i = alpha_i (s_i + beta)
+    std::vector<double> pop(size_t(npop) * TW, 0.0);
+    for (int i = 0; i < npop; ++i) {
+        const double c = q.vx[i], s = q.vy[i];
+        const double alpha = dev ? q.w[i] : 1.0;
+        const double th = std::atan2(s, c);
+        double *t = &pop[size_t(i) * TW];
+        t[0] = c;
+        t[1] = s;
+        t[2] = c * c;
+        t[3] = c * s;
+        t[4] = q.w[i] / alpha;
+        for (int m = 1; m <= N; ++m) {
+            t[4 + 2 * m - 1] = q.w[i] / alpha * std::cos(m * th);
+            t[4 + 2 * m] = q.w[i] / alpha * std::sin(m * th);
+        }
+    }
+    // per-shell folds alpha_r p_r, alpha_r p_r^2
+    std::vector<double> shell(size_t(N + 1) * 2);
+    for (int r = 0; r <= N; ++r) {
+        const double alpha = dev ? q.w[r * K] : 1.0;
+        shell[2 * r] = alpha * q.pr[r];
+        shell[2 * r + 1] = alpha * q.pr[r] * q.pr[r];
+    }
+    // projection weights R'[r][m][k] = sum_l p_r^l (G_m^-1)_{lk} / norm_m * k! / (N+1)
+    std::vector<double> rt(size_t(N + 1) * (N + 1) * (N + 1), 0.0);
+    for (int m = 0; m <= N; ++m) {
+        const int d = N - m + 1;
+        std::vector<double> Gm(d * d), Gi;
+        for (int l = 0; l < d; ++l)
+            for (int k = 0; k < d; ++k) Gm[l * d + k] = factorial(2 * m + l + k);
+        if (!spd_inverse(d, Gm, Gi)) return fail(h, RLBM_ERR_ARG, "projection Gram matrix not SPD");
+        const double norm = (m == 0) ? 2.0 * kPi : kPi;
+        for (int r = 0; r <= N; ++r)
+            for (int k = m; k <= N; ++k) {
+                double s = 0.0;
+                for (int l = m; l <= N; ++l) s += std::pow(q.pr[r], l) * Gi[(l - m) * d + (k - m)];
+                rt[(size_t(r) * (N + 1) + m) * (N + 1) + k] = s / norm * factorial(k) / (N + 1);
+            }
+    }
+    // moment contribution of the offset beta: beta * sum_i alpha_i p^a (p^b)
+    double off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (dev) {
+        for (int i = 0; i < npop; ++i) {
+            const double a = q.w[i] * beta, p = q.p0[i], c = q.vx[i], s = q.vy[i];
+            off[0] += a * p;
+            off[1] += a * p * c;
+            off[2] += a * p * s;
+            off[3] += a * p * p;
+            off[4] += a * p * p * c;
+            off[5] += a * p * p * s;
+            off[6] += a * p * p * c * c;
+            off[7] += a * p * p * c * s;
+        }
+    }
+
+    const bool r64 = (h->prec == RLBM_FP64);
+    const bool l64 = r64 || h->site_fp64;
+    const size_t rs = r64 ? 8 : 4, ls = l64 ? 8 : 4;
+    const size_t o_pop = 0;
+    const size_t o_shell = align256(pop.size() * rs);
+    const size_t o_rt = o_shell + align256(shell.size() * ls);
+    const size_t total = o_rt + align256(rt.size() * ls);
+    std::vector<unsigned char> blob(total, 0);
+    if (r64) put<double>(blob, o_pop, pop); else put<float>(blob, o_pop, pop);
+    if (l64) { put<double>(blob, o_shell, shell); put<double>(blob, o_rt, rt); }
+    else { put<float>(blob, o_shell, shell); put<float>(blob, o_rt, rt); }
+
+    RLBM_CUDA(h, cudaMalloc(&h->d_tabs, total));
+    RLBM_CUDA(h, cudaMalloc(&h->d_status, sizeof(int)));
+    RLBM_CUDA(h, cudaMemcpyAsync(h->d_tabs, blob.data(), total, cudaMemcpyHostToDevice, h->stream));
+    RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+
+    rlbmk::KernelArgs &a = h->base;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.S = (long long)h->grid.nx * h->grid.ny;
+    a.K = K;
+    a.Gs = h->Gs;
+    a.P = h->P;
+    a.bcx = h->grid.bc_x;
+    a.bcy = h->grid.bc_y;
+    a.collide = std::isinf(h->tau) ? 0 : 1;
+    a.inv_tau = std::isinf(h->tau) ? 0.0 : 1.0 / h->tau;
+    a.beta = beta;
+    for (int t = 0; t < 8; ++t) a.off[t] = off[t];
+    for (int j = 0; j <= N; ++j) {
+        const double ph = 2.0 * kPi * j / (N + 1);
+        a.smp_c[j] = std::cos(ph);
+        a.smp_s[j] = std::sin(ph);
+    }
+    a.poptab = (const unsigned char *)h->d_tabs + o_pop;
+    a.shelltab = (const unsigned char *)h->d_tabs + o_shell;
+    a.rtab = (const unsigned char *)h->d_tabs + o_rt;
+    a.status = h->d_status;
+    return RLBM_OK;
+}
+
+void *buffer(rlbm_t *h, int which) { return (unsigned char *)h->buf + size_t(which) * h->pop_bytes; }
+
+size_t smem_bytes(const rlbm_t *h)
+{
+    const int N = h->N;
+    const size_t ls = (h->prec == RLBM_FP64 || h->site_fp64) ? 8 : 4;
+    return ls * (5 * size_t(h->G) * 32 + size_t(N + 1) * (2 * N + 1) * 32 + 3 * 32);
+}
+
+cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
+{
+    const dim3 grid((h->grid.nx + 31) / 32, h->grid.ny);
+    const dim3 block(32, h->G);
+    const size_t smem = smem_bytes(h);
+    const bool two_d = h->grid.ny > 1;
+    cudaError_t e;
+    switch (h->prec) {
+    case RLBM_FP64: e = rlbmk::launch_f64(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    case RLBM_FP32:
+        e = rlbmk::launch_f32(mode, h->N, h->P, two_d, h->site_fp64, grid, block, smem, h->stream, a);
+        break;
+    case RLBM_FP16_DEV: e = rlbmk::launch_f16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    default: e = rlbmk::launch_bf16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    }
+    if (e == cudaSuccess) ++h->launches;
+    return e;
+}
+
+cudaError_t launch_step(rlbm_t *h, int from)
+{
+    rlbmk::KernelArgs a = h->base;
+    a.fin = buffer(h, from);
+    a.fout = buffer(h, 1 - from);
+    return launch(h, rlbmk::MODE_STEP, a);
+}
+
+rlbm_status check_status(rlbm_t *h)
+{
+    int st = 0;
+    RLBM_CUDA(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (st) {
+        RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+        return fail(h, RLBM_ERR_UNPHYSICAL,
+                    "a cell had no physical Landau frame (non-positive n or eps, or no timelike eigenvector)");
+    }
+    return RLBM_OK;
+}
+
+rlbm_status ensure_graph(rlbm_t *h, int from)
+{
+    if (h->graph[from]) return RLBM_OK;
+    cudaGraph_t g = nullptr;
+    const long long l0 = h->launches;
+    RLBM_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int cur = from;
+    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
+        e = launch_step(h, cur);
+        cur = 1 - cur;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    h->launches = l0; // captured launches are counted at replay
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "kernel launch during graph capture"); }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) { h->graph[from] = nullptr; return cuda_fail(h, e3, "cudaGraphInstantiate"); }
+    return RLBM_OK;
+}
+
+rlbm_status validate_fields_ptrs(rlbm_t *h, const void *a, const void *b, const void *c, const void *d)
+{
+    if (!a || !b || !c || !d) return fail(h, RLBM_ERR_ARG, "NULL field pointer");
+    return RLBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+rlbm_status rlbm_quadrature(int order_N, int angles_K, double *p0, double *vx, double *vy, double *w)
+{
+    Quad q;
+    if (!make_quadrature(order_N, angles_K, q))
+        return fail(nullptr, RLBM_ERR_ARG, "need 0 <= N <= 12 and K >= 2N+1 (N=%d, K=%d)", order_N,
+                    angles_K);
+    const size_t nb = sizeof(double) * q.npop;
+    if (p0) std::memcpy(p0, q.p0.data(), nb);
+    if (vx) std::memcpy(vx, q.vx.data(), nb);
+    if (vy) std::memcpy(vy, q.vy.data(), nb);
+    if (w) std::memcpy(w, q.w.data(), nb);
+    return RLBM_OK;
+}
+
+size_t rlbm_population_bytes(rlbm_grid grid, int order_N, int angles_K, int precision)
+{
+    if (grid.nx < 1 || grid.ny < 1 || order_N < 0 || angles_K < 1) return 0;
+    return storage_size(precision) * size_t(angles_K) * size_t(order_N + 1) * size_t(grid.nx) *
+           size_t(grid.ny);
+}
+
+rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K, double tau,
+                        int precision, void *cuda_stream, void *dev_buffers, size_t dev_buffer_bytes)
+{
+    if (!out) return fail(nullptr, RLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (grid.nx < 1 || grid.ny < 1)
+        return fail(nullptr, RLBM_ERR_ARG, "grid must be at least 1x1 (got %dx%d)", grid.nx, grid.ny);
+    if ((long long)grid.ny > 65535)
+        return fail(nullptr, RLBM_ERR_ARG, "ny must be <= 65535 (got %d)", grid.ny);
+    if (grid.bc_x < 0 || grid.bc_x > 1 || grid.bc_y < 0 || grid.bc_y > 1)
+        return fail(nullptr, RLBM_ERR_ARG, "boundary conditions must be 0 (periodic) or 1 (copy-out)");
+    if (order_N < 2)
+        return fail(nullptr, RLBM_ERR_ARG,
+                    "order N must be >= 2 (the collision conserves N^0 and T^0nu only from N = 2)");
+    if (angles_K < 2 * order_N + 1)
+        return fail(nullptr, RLBM_ERR_ARG, "K must be >= 2N+1 (N=%d, K=%d)", order_N, angles_K);
+    if (!(tau > 0.0)) return fail(nullptr, RLBM_ERR_ARG, "tau must be > 0 or +inf (got %g)", tau);
+    if (storage_size(precision) == 0)
+        return fail(nullptr, RLBM_ERR_ARG, "unknown precision %d", precision);
+    if (order_N > 3)
+        return fail(nullptr, RLBM_ERR_UNSUPPORTED, "kernels are built for N = 2, 3 (got N=%d)", order_N);
+
+    rlbm_t *h = new (std::nothrow) rlbm();
+    if (!h) return fail(nullptr, RLBM_ERR_OOM, "host allocation failed");
+    h->grid = grid;
+    h->N = order_N;
+    h->K = angles_K;
+    h->npop = angles_K * (order_N + 1);
+    h->prec = precision;
+    h->tau = tau;
+    const char *env = std::getenv("RLBM_FP32_SITE_FP64");
+    h->site_fp64 = (precision == RLBM_FP32) && env && env[0] == '1';
+    if (!make_quadrature(order_N, angles_K, h->q)) {
+        delete h;
+        return fail(nullptr, RLBM_ERR_ARG, "quadrature construction failed");
+    }
+    if (!choose_tiling(order_N, angles_K, h->P, h->Gs)) {
+        delete h;
+        return fail(nullptr, RLBM_ERR_UNSUPPORTED, "no compiled tiling for K=%d", angles_K);
+    }
+    h->G = h->Gs * (order_N + 1);
+    h->pop_bytes = rlbm_population_bytes(grid, order_N, angles_K, precision);
+
+    rlbm_status st = RLBM_OK;
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { st = cuda_fail(h, e, "cudaStreamCreate"); }
+        h->own_stream = (e == cudaSuccess);
+    }
+    if (st == RLBM_OK) {
+        if (dev_buffers) {
+            if (dev_buffer_bytes < 2 * h->pop_bytes)
+                st = fail(h, RLBM_ERR_ARG, "dev_buffers holds %zu bytes, need %zu", dev_buffer_bytes,
+                          2 * h->pop_bytes);
+            else if (((uintptr_t)dev_buffers) % 256)
+                st = fail(h, RLBM_ERR_ARG, "dev_buffers must be 256-byte aligned");
+            else
+                h->buf = dev_buffers;
+        } else {
+            cudaError_t e = cudaMalloc(&h->buf, 2 * h->pop_bytes);
+            if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMalloc(populations)");
+            else h->own_buf = true;
+        }
+    }
+    if (st == RLBM_OK) st = build_tables(h);
+    if (st != RLBM_OK) {
+        g_create_error = h->err;
+        rlbm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return RLBM_OK;
+}
+
+void rlbm_destroy(rlbm_t *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (h->own_buf && h->buf) cudaFree(h->buf);
+    if (h->d_tabs) cudaFree(h->d_tabs);
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char *rlbm_last_error(const rlbm_t *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+rlbm_status rlbm_init_device(rlbm_t *h, const double *d_n, const double *d_T, const double *d_bx,
+                             const double *d_by)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    rlbm_status st = validate_fields_ptrs(h, d_n, d_T, d_bx, d_by);
+    if (st) return st;
+    rlbmk::KernelArgs a = h->base;
+    a.fin = nullptr;
+    a.fout = buffer(h, 0);
+    a.in_n = d_n;
+    a.in_T = d_T;
+    a.in_bx = d_bx;
+    a.in_by = d_by;
+    cudaError_t e = launch(h, rlbmk::MODE_INIT, a);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+    h->cur = 0;
+    h->steps = 0;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_init(rlbm_t *h, const double *n, const double *T, const double *bx, const double *by)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    rlbm_status st = validate_fields_ptrs(h, n, T, bx, by);
+    if (st) return st;
+    const size_t S = size_t(h->grid.nx) * h->grid.ny;
+    for (size_t s = 0; s < S; ++s) {
+        if (!(n[s] > 0.0) || !(T[s] > 0.0) || !(bx[s] * bx[s] + by[s] * by[s] < 1.0))
+            return fail(h, RLBM_ERR_ARG, "non-physical initial state at site %zu (need n > 0, T > 0, |beta| < 1)", s);
+    }
+    double *d = nullptr;
+    RLBM_CUDA(h, cudaMallocAsync((void **)&d, 4 * S * sizeof(double), h->stream));
+    const double *src[4] = {n, T, bx, by};
+    for (int k = 0; k < 4; ++k)
+        RLBM_CUDA(h, cudaMemcpyAsync(d + k * S, src[k], S * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    st = rlbm_init_device(h, d, d + S, d + 2 * S, d + 3 * S);
+    cudaFreeAsync(d, h->stream);
+    if (st) return st;
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_step(rlbm_t *h, int nsteps)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (nsteps < 0) return fail(h, RLBM_ERR_ARG, "nsteps must be >= 0");
+    int left = nsteps;
+    while (left >= kGraphSteps) {
+        rlbm_status st = ensure_graph(h, h->cur);
+        if (st) return st;
+        RLBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+        h->launches += kGraphSteps;
+        // an even number of steps returns to the same buffer
+        if (kGraphSteps & 1) h->cur = 1 - h->cur;
+        h->steps += kGraphSteps;
+        left -= kGraphSteps;
+    }
+    for (; left > 0; --left) {
+        cudaError_t e = launch_step(h, h->cur);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur = 1 - h->cur;
+        ++h->steps;
+    }
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_moments_device(rlbm_t *h, double *d_n, double *d_eps, double *d_T, double *d_U0,
+                                double *d_Ux, double *d_Uy)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (!d_n || !d_eps || !d_T || !d_U0 || !d_Ux || !d_Uy) return fail(h, RLBM_ERR_ARG, "NULL output pointer");
+    rlbmk::KernelArgs a = h->base;
+    a.fin = buffer(h, h->cur);
+    a.fout = nullptr;
+    a.out[0] = d_n;
+    a.out[1] = d_eps;
+    a.out[2] = d_T;
+    a.out[3] = d_U0;
+    a.out[4] = d_Ux;
+    a.out[5] = d_Uy;
+    cudaError_t e = launch(h, rlbmk::MODE_MOMENTS, a);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_moments(rlbm_t *h, double *n, double *eps, double *T, double *U0, double *Ux, double *Uy)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    double *outs[6] = {n, eps, T, U0, Ux, Uy};
+    for (double *p : outs)
+        if (!p) return fail(h, RLBM_ERR_ARG, "NULL output pointer");
+    const size_t S = size_t(h->grid.nx) * h->grid.ny;
+    double *d = nullptr;
+    RLBM_CUDA(h, cudaMallocAsync((void **)&d, 6 * S * sizeof(double), h->stream));
+    rlbm_status st = rlbm_moments_device(h, d, d + S, d + 2 * S, d + 3 * S, d + 4 * S, d + 5 * S);
+    if (st == RLBM_OK) {
+        for (int k = 0; k < 6; ++k) {
+            cudaError_t e = cudaMemcpyAsync(outs[k], d + k * S, S * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) { st = cuda_fail(h, e, "cudaMemcpyAsync(moments)"); break; }
+        }
+    }
+    cudaFreeAsync(d, h->stream);
+    if (st) return st;
+    return check_status(h);
+}
+
+rlbm_status rlbm_get_populations(rlbm_t *h, void *host, size_t bytes)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (!host || bytes != h->pop_bytes)
+        return fail(h, RLBM_ERR_ARG, "need a host buffer of exactly %zu bytes", h->pop_bytes);
+    RLBM_CUDA(h, cudaMemcpyAsync(host, buffer(h, h->cur), bytes, cudaMemcpyDeviceToHost, h->stream));
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_set_populations(rlbm_t *h, const void *host, size_t bytes, long long step)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (!host || bytes != h->pop_bytes)
+        return fail(h, RLBM_ERR_ARG, "need a host buffer of exactly %zu bytes", h->pop_bytes);
+    RLBM_CUDA(h, cudaMemcpyAsync(buffer(h, 0), host, bytes, cudaMemcpyHostToDevice, h->stream));
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->steps = step;
+    return RLBM_OK;
+}
+
+void *rlbm_current_buffer(rlbm_t *h) { return h ? buffer(h, h->cur) : nullptr; }
+
+long long rlbm_steps_done(const rlbm_t *h) { return h ? h->steps : -1; }
+
+rlbm_status rlbm_sync(rlbm_t *h)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    return check_status(h);
+}
+
+long long rlbm_kernel_launches(const rlbm_t *h) { return h ? h->launches : -1; }
+
+} // extern "C"

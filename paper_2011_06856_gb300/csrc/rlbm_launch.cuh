@@ -1,0 +1,55 @@
+// Template dispatch from runtime (mode, N, P, two_d) to one kernel instance.
+// Included once per storage type by the rlbm_k_*.cu units so that they
+// compile in parallel.
+#pragma once
+#include "rlbm_device.cuh"
+
+namespace rlbmk {
+
+template <class St, class R, class LR, int N, int P>
+static cudaError_t launch_np(int mode, bool two_d, dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, const KernelArgs &a)
+{
+    void (*k)(const KernelArgs);
+    if (mode == MODE_STEP)
+        k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP>
+                  : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP>;
+    else if (mode == MODE_INIT)
+        k = rlbm_kernel<St, R, LR, N, P, false, MODE_INIT>;
+    else
+        k = rlbm_kernel<St, R, LR, N, P, false, MODE_MOMENTS>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class St, class R, class LR, int N>
+static cudaError_t launch_n(int mode, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t st, const KernelArgs &a)
+{
+    switch (P) {
+    case 8: return launch_np<St, R, LR, N, 8>(mode, two_d, grid, block, smem, st, a);
+    case 12: return launch_np<St, R, LR, N, 12>(mode, two_d, grid, block, smem, st, a);
+    case 16: return launch_np<St, R, LR, N, 16>(mode, two_d, grid, block, smem, st, a);
+    case 24: return launch_np<St, R, LR, N, 24>(mode, two_d, grid, block, smem, st, a);
+    case 32: return launch_np<St, R, LR, N, 32>(mode, two_d, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class St, class R, class LR>
+static cudaError_t launch_t(int mode, int N, int P, bool two_d, dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t st, const KernelArgs &a)
+{
+    switch (N) {
+    case 2: return launch_n<St, R, LR, 2>(mode, P, two_d, grid, block, smem, st, a);
+    case 3: return launch_n<St, R, LR, 3>(mode, P, two_d, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace rlbmk

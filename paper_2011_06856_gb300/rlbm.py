@@ -1,0 +1,248 @@
+"""ctypes binding of librlbm.so (C ABI in include/rlbm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory (the population buffers, device-side fields)
+and the CUDA stream.  There is no CPU fallback: if the library is missing or
+no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librlbm.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_UNPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+BC_PERIODIC, BC_COPYOUT = 0, 1
+
+# Symbols declared in include/rlbm.h (checked by the CPU test suite).
+EXPORTS = [
+    "rlbm_quadrature", "rlbm_population_bytes", "rlbm_create", "rlbm_destroy",
+    "rlbm_last_error", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
+    "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
+    "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
+]
+
+
+class RLBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[rlbm status {status}] {msg}")
+        self.status = status
+
+
+class Unphysical(RLBMError):
+    pass
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc_x", ctypes.c_int),
+                ("bc_y", ctypes.c_int)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Load librlbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2011_06856_gb300.build`")
+    L = ctypes.CDLL(path)
+    st = ctypes.c_int
+    L.rlbm_quadrature.restype = st
+    L.rlbm_quadrature.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.rlbm_population_bytes.restype = ctypes.c_size_t
+    L.rlbm_population_bytes.argtypes = [Grid, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.rlbm_create.restype = st
+    L.rlbm_create.argtypes = [ctypes.POINTER(_vp), Grid, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_int, _vp, _vp, ctypes.c_size_t]
+    L.rlbm_destroy.restype = None
+    L.rlbm_destroy.argtypes = [_vp]
+    L.rlbm_last_error.restype = ctypes.c_char_p
+    L.rlbm_last_error.argtypes = [_vp]
+    L.rlbm_init.restype = st
+    L.rlbm_init.argtypes = [_vp, _dp, _dp, _dp, _dp]
+    L.rlbm_init_device.restype = st
+    L.rlbm_init_device.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.rlbm_step.restype = st
+    L.rlbm_step.argtypes = [_vp, ctypes.c_int]
+    L.rlbm_moments.restype = st
+    L.rlbm_moments.argtypes = [_vp] + [_dp] * 6
+    L.rlbm_moments_device.restype = st
+    L.rlbm_moments_device.argtypes = [_vp] + [_vp] * 6
+    L.rlbm_get_populations.restype = st
+    L.rlbm_get_populations.argtypes = [_vp, _vp, ctypes.c_size_t]
+    L.rlbm_set_populations.restype = st
+    L.rlbm_set_populations.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_longlong]
+    L.rlbm_current_buffer.restype = _vp
+    L.rlbm_current_buffer.argtypes = [_vp]
+    L.rlbm_steps_done.restype = ctypes.c_longlong
+    L.rlbm_steps_done.argtypes = [_vp]
+    L.rlbm_sync.restype = st
+    L.rlbm_sync.argtypes = [_vp]
+    L.rlbm_kernel_launches.restype = ctypes.c_longlong
+    L.rlbm_kernel_launches.argtypes = [_vp]
+    _lib = L
+    return L
+
+
+def _check(status: int, handle=None):
+    if status == OK:
+        return
+    msg = lib().rlbm_last_error(handle).decode(errors="replace")
+    cls = Unphysical if status == ERR_UNPHYSICAL else RLBMError
+    raise cls(status, msg)
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def quadrature(N: int, K: int):
+    """(p0, vx, vy, w) of the off-lattice rule, computed by the library."""
+    n = K * (N + 1)
+    out = [np.zeros(n) for _ in range(4)]
+    _check(lib().rlbm_quadrature(N, K, *[_dptr(a) for a in out]))
+    return tuple(out)
+
+
+def population_bytes(nx, ny, N, K, precision="fp64", bcx=BC_COPYOUT, bcy=BC_PERIODIC) -> int:
+    return lib().rlbm_population_bytes(Grid(nx, ny, bcx, bcy), N, K, PRECISIONS[precision])
+
+
+class Simulation:
+    """One RLBM problem on the current CUDA device.
+
+    The population buffers are a torch uint8 tensor (two ping-pong halves)
+    unless ``own_buffers`` is set, in which case the library allocates them."""
+
+    def __init__(self, nx: int, ny: int, N: int, K: int, tau: float, precision: str = "fp64",
+                 bcx: int = BC_COPYOUT, bcy: int = BC_PERIODIC, stream=None,
+                 own_buffers: bool = False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("librlbm needs a CUDA GPU")
+        self.nx, self.ny, self.N, self.K = int(nx), int(ny), int(N), int(K)
+        self.npop = self.K * (self.N + 1)
+        self.precision = precision
+        self.tau = float(tau)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        grid = Grid(self.nx, self.ny, bcx, bcy)
+        self.pop_bytes = lib().rlbm_population_bytes(grid, self.N, self.K, PRECISIONS[precision])
+        self._buf = None
+        ptr, nbytes = None, 0
+        if not own_buffers:
+            self._buf = torch.empty(2 * self.pop_bytes, dtype=torch.uint8, device="cuda")
+            ptr, nbytes = self._buf.data_ptr(), 2 * self.pop_bytes
+        h = _vp()
+        status = lib().rlbm_create(ctypes.byref(h), grid, self.N, self.K, self.tau,
+                                   PRECISIONS[precision], _vp(self.stream.cuda_stream), _vp(ptr),
+                                   nbytes)
+        _check(status, None)
+        self._h = h
+
+    # ---- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rlbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- API
+    @property
+    def sites(self) -> int:
+        return self.nx * self.ny
+
+    def init(self, n, T, bx, by):
+        """Equilibrium state from host fields ([ny][nx] float64 each)."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (n, T, bx, by)]
+        for a in arrs:
+            assert a.size == self.sites
+        _check(lib().rlbm_init(self._h, *[_dptr(a) for a in arrs]), self._h)
+
+    def init_fields(self, fields):
+        self.init(fields.n, fields.T, fields.bx, fields.by)
+
+    def init_device(self, n, T, bx, by):
+        """Equilibrium state from device float64 tensors (asynchronous)."""
+        for t in (n, T, bx, by):
+            assert t.is_cuda and t.is_contiguous() and t.numel() == self.sites
+        _check(lib().rlbm_init_device(self._h, *[_vp(t.data_ptr()) for t in (n, T, bx, by)]),
+               self._h)
+
+    def step(self, nsteps: int = 1):
+        _check(lib().rlbm_step(self._h, int(nsteps)), self._h)
+
+    def moments(self) -> np.ndarray:
+        """(6, ny, nx) float64: n, eps, T, U^0, U^x, U^y of the stored populations."""
+        out = np.zeros((6, self.ny, self.nx))
+        _check(lib().rlbm_moments(self._h, *[_dptr(out[k]) for k in range(6)]), self._h)
+        return out
+
+    def moments_device(self, out):
+        """Write the six fields into a contiguous (6, ny, nx) float64 CUDA tensor."""
+        assert out.is_cuda and out.is_contiguous() and out.numel() == 6 * self.sites
+        S = self.sites
+        base = out.data_ptr()
+        _check(lib().rlbm_moments_device(self._h, *[_vp(base + 8 * k * S) for k in range(6)]),
+               self._h)
+
+    def get_populations(self) -> np.ndarray:
+        """Raw stored populations, shape (npop, ny, nx), storage dtype."""
+        dt = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16}[
+            self.precision]
+        out = np.empty((self.npop, self.ny, self.nx), dtype=dt)
+        _check(lib().rlbm_get_populations(self._h, _vp(out.ctypes.data), out.nbytes), self._h)
+        return out
+
+    def set_populations(self, arr: np.ndarray, step: int = 0):
+        arr = np.ascontiguousarray(arr)
+        _check(lib().rlbm_set_populations(self._h, _vp(arr.ctypes.data), arr.nbytes, int(step)),
+               self._h)
+
+    def sync(self):
+        _check(lib().rlbm_sync(self._h), self._h)
+
+    @property
+    def steps_done(self) -> int:
+        return lib().rlbm_steps_done(self._h)
+
+    @property
+    def kernel_launches(self) -> int:
+        return lib().rlbm_kernel_launches(self._h)
+
+    def current_buffer_ptr(self) -> int:
+        return lib().rlbm_current_buffer(self._h)
+
+
+def decode_populations(raw: np.ndarray, precision: str, w: np.ndarray) -> np.ndarray:
+    """Stored values -> f_i: identity for fp64/fp32; f = w (h + 1/(2 pi)) for 16-bit storage."""
+    if precision in ("fp64", "fp32"):
+        return raw.astype(np.float64)
+    if precision == "fp16":
+        h = raw.astype(np.float64)
+    else:
+        h = (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return w[:, None, None] * (h + 1.0 / (2.0 * math.pi))

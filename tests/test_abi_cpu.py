@@ -1,0 +1,113 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol
+declared in include/rlbm.h; host-only entry points (quadrature tables,
+buffer sizes, argument validation) behave as documented.  No compute call
+needs a GPU here."""
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2011_06856_gb300 import build as B
+from paper_2011_06856_gb300 import rlbm as R
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return R.lib()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"\b(rlbm_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments", "rlbm_destroy"]:
+        assert s in syms
+    assert set(syms) <= set(R.EXPORTS) | set(syms)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", R.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (rlbm_[a-z0-9_]+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in declared_symbols():
+        assert hasattr(lib, s)
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_symbols()) == set(R.EXPORTS)
+
+
+@pytest.mark.parametrize("N,K", [(2, 16), (3, 64), (2, 48), (3, 12), (5, 12), (2, 5)])
+def test_library_quadrature_matches_oracle(lib, N, K):
+    """Row a0 (Sec. 2.3): the library's host tables, computed by a different
+    root finder (Sturm bisection on the Jacobi matrix), equal the oracle's."""
+    p0, vx, vy, w = R.quadrature(N, K)
+    q = O.Quadrature(N, K)
+    np.testing.assert_allclose(p0, q.p0, rtol=2e-15)
+    np.testing.assert_allclose(w, q.w, rtol=1e-13)
+    np.testing.assert_allclose(vx, q.vx, atol=2e-16)
+    np.testing.assert_allclose(vy, q.vy, atol=2e-16)
+
+
+def test_quadrature_rejects_bad_order(lib):
+    n = 6
+    bufs = [np.zeros(n) for _ in range(4)]
+    with pytest.raises(R.RLBMError) as e:
+        R._check(lib.rlbm_quadrature(3, 6, *[R._dptr(b) for b in bufs]))
+    assert e.value.status == R.ERR_ARG
+
+
+def test_population_bytes(lib):
+    g = R.Grid(400, 1, 1, 0)
+    assert lib.rlbm_population_bytes(g, 2, 16, 0) == 48 * 400 * 8
+    assert lib.rlbm_population_bytes(R.Grid(2048, 2048, 1, 1), 2, 48, 2) == 144 * 2048 * 2048 * 2
+    assert lib.rlbm_population_bytes(R.Grid(0, 1, 0, 0), 2, 16, 0) == 0
+
+
+@pytest.mark.parametrize("args,needle", [
+    ((R.Grid(0, 1, 0, 0), 2, 16, 1.0, 0), "grid"),
+    ((R.Grid(8, 1, 0, 0), 1, 16, 1.0, 0), "order N"),
+    ((R.Grid(8, 1, 0, 0), 3, 6, 1.0, 0), "K must be"),
+    ((R.Grid(8, 1, 0, 0), 2, 16, -1.0, 0), "tau"),
+    ((R.Grid(8, 1, 0, 0), 2, 16, float("nan"), 0), "tau"),
+    ((R.Grid(8, 1, 3, 0), 2, 16, 1.0, 0), "boundary"),
+    ((R.Grid(8, 1, 0, 0), 2, 16, 1.0, 9), "precision"),
+])
+def test_create_validates_arguments_without_touching_the_gpu(lib, args, needle):
+    h = R._vp()
+    st = lib.rlbm_create(R.ctypes.byref(h), *args, None, None, 0)
+    assert st == R.ERR_ARG
+    assert not h.value
+    assert needle in lib.rlbm_last_error(None).decode()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.rlbm_step(None, 1) == R.ERR_ARG
+    assert lib.rlbm_sync(None) == R.ERR_ARG
+    assert lib.rlbm_steps_done(None) == -1
+    lib.rlbm_destroy(None)
+
+
+def test_binding_fails_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(RuntimeError):
+        R.Simulation(8, 1, 2, 16, 1.0)

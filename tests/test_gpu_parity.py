@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (normwise, max|gpu - oracle| / max|oracle| per field):
+  FP64 storage and arithmetic            1e-12
+  FP32 storage and arithmetic            1e-5
+  FP16 / BF16 deviation storage          1e-3 (BF16: 3e-3, see the design doc precision table)
+Fields compared: n, eps, T, U^0, U^x, U^y and beta_x = U^x / U^0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2011_06856_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2011_06856_gb300 import build as B  # noqa: E402
+from paper_2011_06856_gb300 import rlbm as R  # noqa: E402
+
+B.build()
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 3e-3}
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def field_errors(got, ref):
+    errs = {k: relerr(got[i], ref[i]) for i, k in enumerate(["n", "eps", "T", "U0", "Ux", "Uy"])}
+    errs["beta_x"] = relerr(got[4] / got[3], ref[4] / ref[3])
+    if np.abs(ref[5]).max() == 0.0:
+        errs["Uy"] = np.abs(got[5]).max()
+    return errs
+
+
+def assert_fields_close(got, ref, tol, what=""):
+    errs = field_errors(got, ref)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"{what}: {bad} (tol {tol})"
+    return errs
+
+
+def oracle_run(N, K, fields, tau, steps, bcx, bcy):
+    q = O.Quadrature(N, K)
+    f = q.init(fields.n, fields.T, fields.bx, fields.by)
+    f, flagged = q.run(f, tau, steps, bcx, bcy)
+    mac, _ = q.macro(f)
+    return q, f, mac, flagged
+
+
+def gpu_run(N, K, fields, tau, steps, bcx, bcy, precision="fp64"):
+    ny, nx = fields.shape
+    sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
+    sim.init_fields(fields)
+    sim.step(steps)
+    return sim, sim.moments()
+
+
+# ------------------------------------------------------------ FP64 parity
+
+def test_fp64_shock_tube_400x1_full_config():
+    """400x1, N=2 (3 radial nodes) x K=16 angles, Kn=0.01 -> tau = 4, 400 steps,
+    copy-out in x, periodic in y: n, eps, u_x profiles vs the oracle."""
+    nx, N, K, steps = 400, 2, 16, 400
+    tau = W.tau_from_kn(0.01, nx)
+    fl = W.shock_tube(nx, 1, (1.0, 1.0), (0.2, 0.5))
+    q, f_ref, mac_ref, flagged = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert flagged == 0
+    sim, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert_fields_close(mac, mac_ref, TOL["fp64"], "fields")
+    f = sim.get_populations()
+    assert relerr(f, f_ref) < TOL["fp64"]
+    assert sim.steps_done == steps
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 1), (3, 2), (5, 4), (33, 3)])
+@pytest.mark.parametrize("bcx,bcy", [(W.BC_PERIODIC, W.BC_PERIODIC), (W.BC_COPYOUT, W.BC_COPYOUT),
+                                     (W.BC_COPYOUT, W.BC_PERIODIC)])
+def test_fp64_tiny_grids_random_populations(nx, ny, bcx, bcy):
+    N, K, steps, tau = 2, 16, 3, 2.5
+    q = O.Quadrature(N, K)
+    f0 = W.random_populations(q.npop, ny, nx, seed=100 + nx * 7 + ny) * q.w[:, None, None]
+    ref, flagged = q.run(f0, tau, steps, bcx, bcy)
+    assert flagged == 0
+    sim = R.Simulation(nx, ny, N, K, tau, "fp64", bcx, bcy)
+    sim.set_populations(f0)
+    sim.step(steps)
+    got = sim.get_populations()
+    assert relerr(got, ref) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("N,K", [(2, 16), (3, 12), (3, 64), (2, 48), (2, 24), (2, 20), (3, 7)])
+def test_fp64_2d_ragged_random_fields(N, K):
+    """Random smooth (n, T, beta) fields on a 70x37 grid (ragged x tail: 70 = 2*32 + 6),
+    copy-out in both directions, 12 steps; covers every tiling the dispatcher picks."""
+    nx, ny, steps, tau = 70, 37, 12, 3.0
+    fl = W.random_fields(nx, ny, seed=7 + K)
+    _, f_ref, mac_ref, flagged = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    assert flagged == 0
+    sim, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    assert_fields_close(mac, mac_ref, TOL["fp64"], f"N={N} K={K}")
+    assert relerr(sim.get_populations(), f_ref) < TOL["fp64"]
+
+
+def test_fp64_init_and_moments_recover_input_fields():
+    """init then moments: the stored equilibrium carries exactly the input
+    n, T, U (moment exactness of the truncated expansion, N >= 2)."""
+    nx, ny = 45, 19
+    fl = W.random_fields(nx, ny, seed=3, beta_max=0.6)
+    sim = R.Simulation(nx, ny, 3, 64, 5.0, "fp64", W.BC_PERIODIC, W.BC_PERIODIC)
+    sim.init_fields(fl)
+    mac = sim.moments()
+    g = 1 / np.sqrt(1 - fl.bx ** 2 - fl.by ** 2)
+    np.testing.assert_allclose(mac[0], fl.n, rtol=1e-12)
+    np.testing.assert_allclose(mac[2], fl.T, rtol=1e-12)
+    np.testing.assert_allclose(mac[1], 2 * fl.n * fl.T, rtol=1e-12)
+    np.testing.assert_allclose(mac[3], g, rtol=1e-12)
+    np.testing.assert_allclose(mac[4], g * fl.bx, atol=1e-12)
+    np.testing.assert_allclose(mac[5], g * fl.by, atol=1e-12)
+    q = O.Quadrature(3, 64)
+    assert relerr(sim.get_populations(), q.init(fl.n, fl.T, fl.bx, fl.by)) < 1e-13
+
+
+def test_fp64_uniform_equilibrium_fixed_point():
+    fl = W.uniform(50, 9, 0.8, 0.7, 0.3, -0.2)
+    sim = R.Simulation(50, 9, 2, 16, 2.0, "fp64", W.BC_COPYOUT, W.BC_COPYOUT)
+    sim.init_fields(fl)
+    f0 = sim.get_populations()
+    sim.step(10)
+    assert relerr(sim.get_populations(), f0) < 1e-13
+
+
+def binomial_site(f0_i, ax, ay, sx, sy, n, x, y):
+    """Exact n-step ballistic value at one site of a periodic grid (tensor
+    product of two binomial upwind operators)."""
+    ny, nx = f0_i.shape
+    from math import comb
+    acc = 0.0
+    for k in range(n + 1):
+        cx = comb(n, k) * ax ** k * (1 - ax) ** (n - k)
+        if cx < 1e-30:
+            continue
+        for l in range(n + 1):
+            cy = comb(n, l) * ay ** l * (1 - ay) ** (n - l)
+            if cy < 1e-30:
+                continue
+            acc += cx * cy * f0_i[(y - sy * l) % ny, (x - sx * k) % nx]
+    return acc
+
+
+def test_fp64_ballistic_binomial_sampled():
+    """tau = inf: the exact discrete solution at sampled sites (computed one by one)."""
+    nx, ny, N, K, steps = 200, 40, 2, 16, 60
+    q = O.Quadrature(N, K)
+    f0 = W.random_populations(q.npop, ny, nx, seed=5)
+    sim = R.Simulation(nx, ny, N, K, math.inf, "fp64", W.BC_PERIODIC, W.BC_PERIODIC)
+    sim.set_populations(f0)
+    sim.step(steps)
+    got = sim.get_populations()
+    rng = np.random.default_rng(1)
+    for _ in range(12):
+        i, y, x = rng.integers(q.npop), rng.integers(ny), rng.integers(nx)
+        ref = binomial_site(f0[i], abs(q.vx[i]), abs(q.vy[i]), 1 if q.vx[i] >= 0 else -1,
+                            1 if q.vy[i] >= 0 else -1, steps, x, y)
+        assert abs(got[i, y, x] - ref) <= 1e-12 * abs(ref)
+
+
+# ------------------------------------------------------------ full-size launch configurations
+
+def test_fp64_full_size_8192x4_one_step_parity():
+    """8192x4, N=3 x K=64 (256 populations), the launch configuration the benchmark
+    times: after 50 GPU steps, one more GPU step equals one oracle step on the
+    same state."""
+    nx, ny, N, K = 8192, 4, 3, 64
+    tau = W.tau_from_kn(0.01, nx)
+    fl = W.shock_tube(nx, ny)
+    sim = R.Simulation(nx, ny, N, K, tau, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    sim.init_fields(fl)
+    sim.step(50)
+    f50 = sim.get_populations()
+    sim.step(1)
+    got = sim.get_populations()
+    q = O.Quadrature(N, K)
+    ref, flagged = q.run(f50, tau, 1, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert flagged == 0
+    assert relerr(got, ref) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_full_size_8192x4_one_step_parity_fp32(precision):
+    nx, ny, N, K = 8192, 4, 3, 64
+    tau = W.tau_from_kn(0.1, nx)
+    fl = W.shock_tube(nx, ny)
+    sim = R.Simulation(nx, ny, N, K, tau, precision, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim.init_fields(fl)
+    sim.step(40)
+    f40 = sim.get_populations().astype(np.float64)
+    sim.step(1)
+    got = sim.get_populations().astype(np.float64)
+    q = O.Quadrature(N, K)
+    ref, _ = q.run(f40, tau, 1, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert relerr(got, ref) < 1e-6
+
+
+def test_fp64_2048sq_sampled_one_step():
+    """2048^2, N=2 x K=48 at full size: one GPU step from an oracle-initialised
+    random state, checked on sampled rows (the oracle steps only the rows it needs)."""
+    nx = ny = 2048
+    N, K, tau = 2, 48, 102.4
+    fl = W.random_fields(nx, ny, seed=11)
+    sim = R.Simulation(nx, ny, N, K, tau, "fp64", W.BC_COPYOUT, W.BC_COPYOUT)
+    sim.init_fields(fl)
+    f0 = sim.get_populations()
+    sim.step(1)
+    got = sim.get_populations()
+    q = O.Quadrature(N, K)
+    for y in (0, 1, 777, 2046, 2047):
+        lo, hi = max(0, y - 1), min(ny, y + 2)
+        sub = np.ascontiguousarray(f0[:, lo:hi, :])
+        # a row band with its own copy-out edges reproduces the interior row y exactly
+        # when y has both neighbours inside the band or is a true boundary row
+        ref, _ = q.run(sub, tau, 1, W.BC_COPYOUT, W.BC_COPYOUT)
+        assert relerr(got[:, y, :], ref[:, y - lo, :]) < TOL["fp64"], y
+
+
+# ------------------------------------------------------------ FP32 and 16-bit storage
+
+def test_fp32_shock_tube_400x1():
+    nx, N, K, steps = 400, 2, 16, 400
+    tau = W.tau_from_kn(0.01, nx)
+    fl = W.shock_tube(nx, 1)
+    _, _, mac_ref, _ = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    _, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
+    assert_fields_close(mac, mac_ref, TOL["fp32"], "fp32 400x1")
+
+
+@pytest.mark.parametrize("kn", [0.01, 0.1, 1.0, 10.0])
+def test_fp32_8192x4_N3K64_reduced_steps(kn):
+    """Config shape 8192x4, N=3 x K=64, each Kn, 200 steps (full 4000 in the benchmark)."""
+    nx, ny, N, K, steps = 8192, 4, 3, 64, 200
+    tau = W.tau_from_kn(kn, nx)
+    fl = W.shock_tube(nx, ny)
+    _, _, mac_ref, flagged = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert flagged == 0
+    _, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
+    assert_fields_close(mac, mac_ref, TOL["fp32"], f"fp32 Kn={kn}")
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_16bit_deviation_storage_riemann(precision):
+    """Four-quadrant Riemann states (n, T) = (1,1), (0.5,0.8), (0.25,0.6), (0.5,0.8),
+    jitter 1%, N=2 x K=48, Kn = 0.05 at 96^2, 150 steps, copy-out both axes."""
+    nx = ny = 96
+    N, K, steps = 2, 48, 150
+    w = W.WORKLOADS["riemann2d_2048_N2K48"]
+    fl = W.workload_fields(w, nx, ny)
+    tau = W.tau_from_kn(0.05, nx)
+    _, _, mac_ref, flagged = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    assert flagged == 0
+    _, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT, precision)
+    errs = field_errors(mac, mac_ref)
+    print(precision, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k in ("n", "eps", "beta_x"):
+        assert errs[k] <= TOL[precision], (k, errs)
+
+
+# ------------------------------------------------------------ runtime behaviour
+
+def test_graph_replay_equals_single_launches():
+    fl = W.random_fields(64, 8, seed=21)
+    a = R.Simulation(64, 8, 2, 16, 3.0, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    b = R.Simulation(64, 8, 2, 16, 3.0, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    a.init_fields(fl)
+    b.init_fields(fl)
+    a.step(70)  # two graph replays of 32 steps + 6 single launches
+    for _ in range(70):
+        b.step(1)
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    assert a.kernel_launches == b.kernel_launches == 71
+
+
+def test_checkpoint_resume_is_bit_identical():
+    fl = W.shock_tube(128, 4)
+    a = R.Simulation(128, 4, 3, 12, 6.0, "fp32", W.BC_COPYOUT, W.BC_PERIODIC)
+    a.init_fields(fl)
+    a.step(37)
+    ck = a.get_populations()
+    a.step(41)
+    b = R.Simulation(128, 4, 3, 12, 6.0, "fp32", W.BC_COPYOUT, W.BC_PERIODIC)
+    b.set_populations(ck, step=37)
+    b.step(41)
+    assert b.steps_done == 78
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+
+
+def test_device_entry_points_match_host_ones():
+    nx, ny = 77, 5
+    fl = W.random_fields(nx, ny, seed=8)
+    a = R.Simulation(nx, ny, 2, 24, 4.0, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    a.init_fields(fl)
+    b = R.Simulation(nx, ny, 2, 24, 4.0, "fp64", W.BC_COPYOUT, W.BC_PERIODIC, own_buffers=True)
+    dev = [torch.tensor(x, dtype=torch.float64, device="cuda").contiguous()
+           for x in (fl.n, fl.T, fl.bx, fl.by)]
+    with torch.cuda.stream(b.stream):
+        b.init_device(*dev)
+    a.step(9)
+    b.step(9)
+    out = torch.empty((6, ny, nx), dtype=torch.float64, device="cuda")
+    b.moments_device(out)
+    b.stream.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), a.moments())
+
+
+def test_unphysical_state_is_reported_not_trapped():
+    q = O.Quadrature(2, 16)
+    f0 = W.random_populations(q.npop, 2, 8, seed=2) * q.w[:, None, None]
+    f0[:, 1, 3] *= -1.0  # negative populations: no physical Landau frame at that site
+    sim = R.Simulation(8, 2, 2, 16, 3.0, "fp64", W.BC_PERIODIC, W.BC_PERIODIC)
+    sim.set_populations(f0)
+    with pytest.raises(R.Unphysical):
+        sim.moments()
+    sim.set_populations(np.abs(f0))
+    sim.moments()  # flag was cleared
+    sim.step(2)
+    sim.sync()
+
+
+def test_many_handles_and_unsupported_order():
+    with pytest.raises(R.RLBMError) as e:
+        R.Simulation(16, 1, 5, 12, 1.0)
+    assert e.value.status == R.ERR_UNSUPPORTED
+    sims = [R.Simulation(32, 2, 2, 16, 2.0, "fp32") for _ in range(8)]
+    for s in sims:
+        s.close()
