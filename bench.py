@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: population updates per second of the fused RLBM step on GB300.
+
+Default workload (one benchmark step): the scaled 1D relativistic shock tube,
+grid 8192 x 4 (copy-out in x, periodic in y), quadrature N = 3 (4 radial
+Gauss-Laguerre nodes) x K = 64 angles = 256 populations per site, run for
+4000 time steps at each Kn in {0.01, 0.1, 1, 10} (tau = Kn * 8192): four
+independent problems, 1.34e11 population updates.  FP32 storage and
+arithmetic.  Inputs are synthetic (piecewise-constant MJ states, u = 0, left
+n = 1, T = 1, right n = 0.2, T = 0.5).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision fp32|fp64|fp16|bf16] [--impl ours|reference]
+
+One JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle (the
+method's plain definition) on the host cores on a bounded sample of the same
+workload.  Under torchrun each rank runs its own replica of the problem set
+(independent problems, no collective on the data path), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2011_06856_gb300 import workloads as W  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "population-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shock1d_8192x4_N3K64", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--timesteps", type=int, default=None,
+                    help="override time steps per problem (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h"):
+        with open(os.path.join(ROOT, "paper_2011_06856_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", f"rlbm_step_{workload}_{precision}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w: W.Workload, kn_list, budget_s: float = 12.0):
+    """Time the FP64 oracle (as it stands) on the host cores on a bounded sample:
+    the full grid and quadrature of the workload, a few time steps per Kn."""
+    import oracle as O
+    q = O.Quadrature(w.N, w.K)
+    fl = W.workload_fields(w)
+    f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
+    # calibrate with one step, then fill the budget
+    t0 = time.perf_counter()
+    q.run(f0, W.tau_from_kn(kn_list[0], w.nx), 1, w.bcx, w.bcy)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(t1, 1e-6) / len(kn_list)))
+    t0 = time.perf_counter()
+    for kn in kn_list:
+        q.run(f0, W.tau_from_kn(kn, w.nx), steps, w.bcx, w.bcy)
+    dt = time.perf_counter() - t0
+    updates = w.sites * w.npop * steps * len(kn_list)
+    return {"value": updates / dt, "unit": METRIC, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{w.nx}x{w.ny} N={w.N} K={w.K}, {steps} time steps x {len(kn_list)} Kn "
+                      f"({updates:.3e} updates, {dt:.1f} s, FP64)"}
+
+
+def run_reference(args, w: W.Workload, precision: str):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    kn_list = list(w.kn)
+    cb = cpu_baseline(w, kn_list, budget_s=8.0)
+    # timed steps: each a bounded sample of the workload
+    import oracle as O
+    q = O.Quadrature(w.N, w.K)
+    fl = W.workload_fields(w)
+    f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
+    t0 = time.perf_counter()
+    q.run(f0, W.tau_from_kn(kn_list[0], w.nx), 1, w.bcx, w.bcy)
+    per = time.perf_counter() - t0
+    steps_per = max(1, int(6.0 / max(per, 1e-6) / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        q.run(f0, W.tau_from_kn(kn_list[0], w.nx), steps_per, w.bcx, w.bcy)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        q.run(f0, W.tau_from_kn(kn_list[s % len(kn_list)], w.nx), steps_per, w.bcx, w.bcy)
+        times.append(time.perf_counter() - t0)
+    upd = w.sites * w.npop * steps_per
+    value = upd * len(times) / sum(times)
+    cb["value"] = value
+    cb["sample"] = f"{w.nx}x{w.ny} N={w.N} K={w.K}, {steps_per} time steps per timed step, FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
+                       "npop": w.npop, "kn": kn_list, "time_steps_per_problem": steps_per,
+                       "precision": "fp64", "device": "host cores (oracle)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = W.WORKLOADS[args.workload]
+    precision = args.precision or w.precision
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, w, precision)
+        return
+
+    # CPU baseline first (before any GPU call), rank 0 at N = 1 only
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, list(w.kn))
+
+    import torch
+    import torch.distributed as dist
+    from paper_2011_06856_gb300 import build as B
+    from paper_2011_06856_gb300 import rlbm as R
+
+    B.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+
+    steps_pp = args.timesteps or w.steps
+    kn_list = list(w.kn)
+    fl = W.workload_fields(w)
+    d_fields = [torch.tensor(a, dtype=torch.float64, device=dev).contiguous()
+                for a in (fl.n, fl.T, fl.bx, fl.by)]
+    stream = torch.cuda.Stream(device=dev)
+    sims = [R.Simulation(w.nx, w.ny, w.N, w.K, W.tau_from_kn(kn, w.nx), precision, w.bcx, w.bcy,
+                         stream=stream) for kn in kn_list]
+    out = torch.empty((6, w.ny, w.nx), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def one_step():
+        for sim in sims:
+            sim.init_device(*d_fields)
+            sim.step(steps_pp)
+            sim.moments_device(out)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        barrier()
+        l0 = sum(s.kernel_launches for s in sims)
+        clk = ClockSampler(local)
+        clk.start()
+        ev = []
+        barrier()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.random_(0, 255)  # L2 flush outside the events, on the same stream
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step()
+            e1.record(stream)
+            ev.append((e0, e1))
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        clocks = clk.stop()
+        launches = sum(s.kernel_launches for s in sims) - l0
+        ms = [a.elapsed_time(b) for a, b in ev]
+
+        # dominant kernel alone: a run of step launches timed on its stream
+        sim0 = sims[0]
+        sim0.init_device(*d_fields)
+        sim0.step(64)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        nk = 1024
+        k0.record(stream)
+        sim0.step(nk)
+        k1.record(stream)
+        k1.synchronize()
+        kernel_ms = k0.elapsed_time(k1) / nk
+
+        # end to end through the public API with host buffers
+        host_fields = [np.ascontiguousarray(a) for a in (fl.n, fl.T, fl.bx, fl.by)]
+        barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            for sim in sims:
+                sim.init(*host_fields)
+                sim.step(steps_pp)
+                sim.moments()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    total_ms = float(np.sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    upd_per_step = w.sites * w.npop * steps_pp * len(kn_list)
+    value = upd_per_step * args.steps * world / (total_ms * 1e-3)
+    storage = R.STORAGE_BYTES[precision]
+    alg_bytes = 2 * storage * w.sites * w.npop
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    e2e_value = upd_per_step * world / e2e_s
+    S = w.sites
+    working_set = 2 * storage * S * w.npop
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32",
+                      "bf16": "bf16-storage/f32"}[precision],
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
+                       "npop": w.npop, "kn": kn_list, "time_steps_per_problem": steps_pp,
+                       "problems_per_step": len(kn_list), "precision": precision,
+                       "bc": ["copy-out" if w.bcx else "periodic", "copy-out" if w.bcy else "periodic"],
+                       "l2": f"flushed between timed steps (256 MB write); working set "
+                             f"{working_set / 1e6:.0f} MB {'fits' if working_set < 129e6 else 'exceeds'} "
+                             f"the 129 MB L2 within a step",
+                       "parallelism": f"replicas x{world} (independent problems)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": profiled_traffic(w.name, precision),
+                         "kernel": "rlbmk::rlbm_kernel<MODE_STEP>",
+                         "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cb,
+            "e2e": {"value": e2e_value, "unit": METRIC,
+                    "h2d_bytes_per_step": 4 * 8 * S * len(kn_list),
+                    "d2h_bytes_per_step": 6 * 8 * S * len(kn_list)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -15,10 +15,14 @@
  *   population index i = r K + j.  Requires N >= 2 (the collision conserves
  *   N^0 and T^{0 nu} only from N = 2 on) and K >= 2N+1.
  * Populations: structure of arrays f[i][y][x], x fastest, S = nx * ny sites.
- *   Precision RLBM_FP64 / RLBM_FP32 stores f_i itself.  RLBM_FP16_DEV /
- *   RLBM_BF16_DEV store the deviation h_i = f_i / w_i - 1/(2 pi) from the
- *   rest equilibrium at n = 1, T = 1 (for which f_i = w_i / (2 pi) exactly),
- *   rounded to nearest; arithmetic is FP32.
+ *   Precision RLBM_FP64 / RLBM_FP32 stores f_i itself.  The 16-bit forms
+ *   store f_i relative to the rest equilibrium at n = 1, T = 1, for which
+ *   f^rest_i = w_i / (2 pi) exactly: *_DEV stores s_i = f_i / f^rest_i - 1,
+ *   *_NORM stores s_i = f_i / f^rest_i; arithmetic in FP32.  Steps write them
+ *   with stochastic rounding (counter-based random bits, reproducible: the
+ *   stream of random bits is a function of site, population and step number,
+ *   so a run resumed from a checkpoint at step k repeats the original run);
+ *   the initial state is rounded to nearest.
  * Macroscopic fields: double arrays of S values, [y][x].  Velocities are
  *   given as beta = (u_x, u_y), |beta| < 1; U^a = gamma (1, beta).
  * Pointers: "host" pointers are ordinary CPU memory, "device" pointers are
@@ -54,7 +58,14 @@ typedef enum {
     RLBM_ERR_UNSUPPORTED = 6 /* valid but not built (e.g. an (N, K) with no kernel) */
 } rlbm_status;
 
-typedef enum { RLBM_FP64 = 0, RLBM_FP32 = 1, RLBM_FP16_DEV = 2, RLBM_BF16_DEV = 3 } rlbm_precision;
+typedef enum {
+    RLBM_FP64 = 0,      /* FP64 storage and arithmetic */
+    RLBM_FP32 = 1,      /* FP32 storage and arithmetic */
+    RLBM_FP16_DEV = 2,  /* FP16 s = f / f^rest - 1 (deviation from the rest equilibrium) */
+    RLBM_BF16_DEV = 3,  /* BF16 s = f / f^rest - 1 */
+    RLBM_FP16_NORM = 4, /* FP16 s = f / f^rest (normalised by the rest equilibrium) */
+    RLBM_BF16_NORM = 5  /* BF16 s = f / f^rest */
+} rlbm_precision;
 
 typedef enum { RLBM_BC_PERIODIC = 0, RLBM_BC_COPYOUT = 1 } rlbm_bc;
 
@@ -140,6 +151,21 @@ rlbm_status rlbm_sync(rlbm_t *h);
 /* Number of kernel launches the handle has issued (graph replays count
  * every kernel node). */
 long long rlbm_kernel_launches(const rlbm_t *h);
+
+/* Which step kernel the handle uses: 1 = persistent TMA-staged kernel
+ * (row pitch a multiple of 16 bytes and nx >= one box), 0 = per-tile kernel. */
+int rlbm_step_kernel_variant(const rlbm_t *h);
+
+/* Bound, in SM clock cycles, of every mbarrier wait in the TMA-staged step
+ * kernel (default 4e9, about 2 s).  A wait that runs out makes the kernel
+ * record RLBM_ERR_TIMEOUT, drain its own copies (bounded) and return; the next
+ * synchronising call reports it.  cycles >= 1000. */
+rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles);
+
+/* Test hook for the timeout path: the next step launch expects 16 bytes more
+ * than its copies deliver, so its waits run out after the wait limit.
+ * RLBM_ERR_UNSUPPORTED when the handle uses the per-tile kernel. */
+rlbm_status rlbm_test_stall_next_step(rlbm_t *h);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,7 @@
 // launchers; shared by the host code and the kernel units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace rlbmk {
@@ -23,19 +24,64 @@ struct KernelArgs {
     int collide;    // 0 for tau = +inf (free streaming)
     double inv_tau;
     double beta;    // stored-unit offset: f = alpha (s + beta)
+    double feq_off; // beta / (w_i / alpha_i): subtracted from the m = 0 coefficient
     double off[8];  // moment contribution of the offset beta
     double smp_c[kMaxN + 1], smp_s[kMaxN + 1]; // equispaced sample directions
+    // FP32 copies of the scalars above, so FP32 kernels never touch the FP64 pipe
+    float inv_tau_f, feq_off_f;
+    float off_f[8];
+    float smp_cf[kMaxN + 1], smp_sf[kMaxN + 1];
     const void *poptab;   // npop x tab_width(N), compute type
     const void *shelltab; // (N+1) x 2: alpha_r p_r, alpha_r p_r^2 (site type)
     const void *rtab;     // (N+1)^3 projection weights R'[r][m][k] (site type)
     const double *in_n, *in_T, *in_bx, *in_by; // MODE_INIT fields
     double *out[6];                            // MODE_MOMENTS fields
+    const unsigned long long *masks; // per warp: bit k = (v_x >= 0), (v_y >= 0) of its population k (k < 64)
     int *status;
+    unsigned *ctr; // [0] completed step launches (seeds stochastic rounding), [1] CTAs done
 };
 
 __host__ __device__ constexpr int tab_width(int N) { return ((2 * N + 5) + 3) / 4 * 4; }
 
+// Arguments of the persistent TMA-staged step kernel.
+struct alignas(128) TmaArgs {
+    CUtensorMap tmap;      // 3D map over the input buffer: {nx, ny, npop}, box {BW, 1, BP}
+    KernelArgs a;
+    int BP;                // populations per box
+    int nbox;              // boxes per row slot (npop <= nbox * BP)
+    int ntiles_x, ntiles;  // tiles of 32 sites per row, total tiles
+    long long stage_bytes; // bytes of one pipeline stage
+    long long wait_cycles; // bound of every mbarrier wait
+    unsigned extra_tx;     // test hook: extra expected bytes (0 in normal use)
+};
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared-memory layout of rlbm_step_tma: two stages, the per-warp table
+// slice, two reduction buffers (tiles alternate), two mbarriers, a flag.
+struct TmaSmem {
+    size_t tab, red, bars, flag, total;
+    __host__ __device__ TmaSmem(size_t stage_bytes, int G, int P, int N, size_t rs, size_t ls)
+    {
+        tab = 2 * stage_bytes;
+        red = align_up(tab + size_t(G) * P * tab_width(N) * rs, 16);
+        bars = align_up(red + 2 * 5 * size_t(G) * 32 * ls, 16);
+        flag = bars + 16;
+        total = flag + 16 + 1024; // + slack to align the base to 1 KB
+    }
+};
+
 // Host-side launcher for one storage type (defined in the per-type units).
+// Persistent TMA-staged step launchers; grid <= 0 with blocks_per_sm set only
+// queries the occupancy.
+#define RLBM_DECLARE_TMA(t)                                                                       \
+    cudaError_t launch_tma_##t(int N, int P, bool two_d, bool site_fp64, int grid, dim3 block,     \
+                               size_t smem, cudaStream_t st, const TmaArgs &a, int *bps);
+RLBM_DECLARE_TMA(f64)
+RLBM_DECLARE_TMA(f32)
+RLBM_DECLARE_TMA(f16)
+RLBM_DECLARE_TMA(bf16)
+#undef RLBM_DECLARE_TMA
 cudaError_t launch_f64(int mode, int N, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
                        cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool site_fp64, dim3 grid, dim3 block,

@@ -3,17 +3,17 @@
 // them.  Warp g handles P populations of one energy shell r = g / Gs
 // (Gs warps per shell), lane = site.  A step is:
 //
-//   pass 1  (every warp)   bilinear pull of its P populations (Eqs.
-//           streaming, interpolation), kept in registers, and five
-//           per-shell angular sums S0, Sc, Ss, Scc, Scs of them;
-//   site    (warp 0)       the 5 x G partial sums folded with p_r, p_r^2 into
-//           N^a and T^ab (Eq. discrete_sum_moments; T^yy = T^tt - T^xx on the
-//           light cone), the Landau frame eps U^a = T^ab U_b (trace-free
-//           cubic, Viete root + one Newton step, eigenvector by cross
-//           products), n = U_a N^a, T = eps / 2n, and the truncated
-//           equilibrium as one trigonometric polynomial of degree N in theta
-//           per shell (see feq_coefficients);
-//   pass 2  (every warp)   f^eq_i from those coefficients, relaxation
+//   pass 1  bilinear pull of the warp's P populations (Eqs. streaming,
+//           interpolation), kept in registers, and five angular sums
+//           S0, Sc, Ss, Scc, Scs of them, exchanged through shared memory;
+//   site    every warp folds the G x 5 sums of its 32 sites with p_r, p_r^2
+//           into N^a and T^ab (Eq. discrete_sum_moments; T^yy = T^tt - T^xx
+//           on the light cone), solves the Landau frame eps U^a = T^ab U_b
+//           (landau_fast), n = U_a N^a, T = eps / 2n, and builds the truncated
+//           equilibrium of its own shell as a trigonometric polynomial of
+//           degree N in theta (shell_coefficients).  The work is repeated per
+//           warp so that no warp waits on another;
+//   pass 2  f^eq_i from those coefficients, relaxation
 //           f <- f* + omega_i (f^eq - f*), omega_i = (U^0 - U.v_i)/tau
 //           (Eq. discrete-rbe), one store per population.
 //
@@ -35,10 +35,12 @@ namespace rlbmk {
 template <class St, class R> struct Io;
 template <> struct Io<double, double> {
     static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ double lds(const double *p) { return *p; }
     static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <> struct Io<float, float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float lds(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Io<__half, float> {
@@ -46,6 +48,7 @@ template <> struct Io<__half, float> {
     {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
+    static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Io<__nv_bfloat16, float> {
@@ -54,6 +57,7 @@ template <> struct Io<__nv_bfloat16, float> {
         return __bfloat162float(
             __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
+    static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v)
     {
         *p = __float2bfloat16_rn(v);
@@ -69,62 +73,181 @@ __device__ __forceinline__ double r_sqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float r_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double r_rsqrt(double v) { return rsqrt(v); }
 
+// Stochastic rounding of 16-bit stores.  Round-to-nearest repeats the same
+// rounding error every step wherever the flow is steady, and the conserved
+// moments drift linearly; with stochastic rounding the error has zero mean
+// and only random-walks.  Random bits: one hash per thread and tile (of the
+// site, the warp and the launch counter), then a 32-bit LCG step per store;
+// the top bits are added below the kept mantissa and the value truncated.
+__device__ __forceinline__ unsigned mix32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ unsigned lcg_next(unsigned &s)
+{
+    s = s * 1664525u + 1013904223u;
+    return s;
+}
+template <class St> struct SR {
+    static __device__ __forceinline__ void st(St *p, float v, unsigned &rng);
+};
+template <> struct SR<__half> {
+    static __device__ __forceinline__ void st(__half *p, float v, unsigned &rng)
+    {
+        const unsigned b = __float_as_uint(v) + (lcg_next(rng) >> 19); // 13 dropped bits
+        *p = __float2half_rz(__uint_as_float(b));
+    }
+};
+template <> struct SR<__nv_bfloat16> {
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, unsigned &rng)
+    {
+        const unsigned b = __float_as_uint(v) + (lcg_next(rng) >> 16); // 16 dropped bits
+        *reinterpret_cast<unsigned short *>(p) = (unsigned short)(b >> 16);
+    }
+};
+template <> struct SR<float> {
+    static __device__ __forceinline__ void st(float *p, float v, unsigned &) { *p = v; }
+};
+template <> struct SR<double> {
+    static __device__ __forceinline__ void st(double *p, double v, unsigned &) { *p = v; }
+};
+
+// The last CTA of a step launch advances the launch counter that seeds the
+// rounding of the next launch (graph replays keep their parameters fixed).
+__device__ __forceinline__ void advance_launch_counter(unsigned *ctr, unsigned nblocks)
+{
+    __threadfence();
+    if (atomicAdd(&ctr[1], 1u) == nblocks - 1) {
+        ctr[1] = 0u;
+        __threadfence();
+        atomicAdd(&ctr[0], 1u);
+    }
+}
+
+// Launch scalars in the per-site precision (FP32 kernels read the FP32 copies).
+template <class LR> struct Par;
+template <> struct Par<double> {
+    static __device__ __forceinline__ double inv_tau(const KernelArgs &a) { return a.inv_tau; }
+    static __device__ __forceinline__ double feq_off(const KernelArgs &a) { return a.feq_off; }
+    static __device__ __forceinline__ double off(const KernelArgs &a, int u) { return a.off[u]; }
+    static __device__ __forceinline__ double smp_c(const KernelArgs &a, int j) { return a.smp_c[j]; }
+    static __device__ __forceinline__ double smp_s(const KernelArgs &a, int j) { return a.smp_s[j]; }
+};
+template <> struct Par<float> {
+    static __device__ __forceinline__ float inv_tau(const KernelArgs &a) { return a.inv_tau_f; }
+    static __device__ __forceinline__ float feq_off(const KernelArgs &a) { return a.feq_off_f; }
+    static __device__ __forceinline__ float off(const KernelArgs &a, int u) { return a.off_f[u]; }
+    static __device__ __forceinline__ float smp_c(const KernelArgs &a, int j) { return a.smp_cf[j]; }
+    static __device__ __forceinline__ float smp_s(const KernelArgs &a, int j) { return a.smp_sf[j]; }
+};
+
 __device__ __forceinline__ int bc_index(int i, int L, int bc)
 {
     if (bc == 0) return i < 0 ? i + L : (i >= L ? i - L : i);
     return i < 0 ? 0 : (i >= L ? L - 1 : i);
 }
 
-// Landau frame of the moments m = (N^t, N^x, N^y, T^tt, T^tx, T^ty, T^xx, T^xy)
-// with T^yy = T^tt - T^xx (massless: T^a_a = 0).  A = T eta has zero trace, so
-// its characteristic polynomial is lambda^3 + c1 lambda - c0; the largest
-// real root is the energy density.  Returns false for a non-physical state
-// (then a rest frame with n = N^t is returned so the caller stays finite).
+template <class R>
+__device__ __forceinline__ void ld4(const R *p, R &x, R &y, R &z, R &w);
+template <>
+__device__ __forceinline__ void ld4<float>(const float *p, float &x, float &y, float &z, float &w)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    x = v.x; y = v.y; z = v.z; w = v.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double *p, double &x, double &y, double &z,
+                                            double &w)
+{
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    x = v0.x; y = v0.y; z = v1.x; w = v1.y;
+}
+
+// Sum the per-warp angular sums of one site (lane) and fold them with the
+// shell factors alpha_r p_r, alpha_r p_r^2 into
+// m = (N^t, N^x, N^y, T^tt, T^tx, T^ty, T^xx, T^xy)  (Eq. discrete_sum_moments).
+template <int N, class LR>
+__device__ __forceinline__ void fold_moments(const KernelArgs &a, const LR *red, int G, int lane,
+                                             LR *m)
+{
+    const LR *sh = reinterpret_cast<const LR *>(a.shelltab);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = Par<LR>::off(a, u);
+#pragma unroll
+    for (int rr = 0; rr <= N; ++rr) {
+        LR p0 = LR(0), pc = LR(0), ps = LR(0), pcc = LR(0), pcs = LR(0);
+        for (int qq = 0; qq < a.Gs; ++qq) {
+            const int w = rr * a.Gs + qq;
+            p0 += red[(0 * G + w) * 32 + lane];
+            pc += red[(1 * G + w) * 32 + lane];
+            ps += red[(2 * G + w) * 32 + lane];
+            pcc += red[(3 * G + w) * 32 + lane];
+            pcs += red[(4 * G + w) * 32 + lane];
+        }
+        const LR f1 = __ldg(sh + 2 * rr), f2 = __ldg(sh + 2 * rr + 1);
+        m[0] += f1 * p0;
+        m[1] += f1 * pc;
+        m[2] += f1 * ps;
+        m[3] += f2 * p0;
+        m[4] += f2 * pc;
+        m[5] += f2 * ps;
+        m[6] += f2 * pcc;
+        m[7] += f2 * pcs;
+    }
+}
+
+// Landau frame, eps U^a = T^ab U_b (Sec. 2.2), in a form cheap enough to run
+// per site in every warp.  With E = T^tt and M = |T^ti|, an equilibrium has
+// beta = (3E - sqrt(9E^2 - 8M^2)) / 2M and eps = E - beta M exactly; that is the
+// starting point of Newton's method on the trace-free characteristic cubic
+// lambda^3 + c1 lambda - c0.  If it lies below the root, T^tt (an upper bound
+// of the rest-frame energy density) is used instead, so Newton approaches the
+// largest root from above, monotonically.  The eigenvector is the cross
+// product of the last two rows of A - eps I (A = T eta), whose spatial 2x2
+// block T^ij + eps delta^ij is positive definite for a physical state.
 template <class LR>
-__device__ __forceinline__ bool landau_frame(const LR *m, LR &n, LR &eps, LR &U0, LR &Ux, LR &Uy)
+__device__ __forceinline__ bool landau_fast(const LR *m, LR &n, LR &eps, LR &U0, LR &Ux, LR &Uy)
 {
     const LR Nt = m[0], Nx = m[1], Ny = m[2];
-    const LR Ttt = m[3], Ttx = m[4], Tty = m[5], Txx = m[6], Txy = m[7];
-    const LR Tyy = Ttt - Txx;
-    const LR c1 = -Ttt * Ttt + Ttx * Ttx + Tty * Tty + Txx * Tyy - Txy * Txy;
-    const LR c0 = Ttt * (Txx * Tyy - Txy * Txy) - Ttx * Ttx * Tyy + LR(2) * Ttx * Tty * Txy -
+    const LR E = m[3], Ttx = m[4], Tty = m[5], Txx = m[6], Txy = m[7];
+    const LR Tyy = E - Txx;
+    const LR c1 = -E * E + Ttx * Ttx + Tty * Tty + Txx * Tyy - Txy * Txy;
+    const LR c0 = E * (Txx * Tyy - Txy * Txy) - Ttx * Ttx * Tyy + LR(2) * Ttx * Tty * Txy -
                   Tty * Tty * Txx;
-    bool ok = c1 < LR(0);
-    LR lam;
-    {
-        const LR r = r_sqrt(ok ? -c1 / LR(3) : LR(0));
-        const LR r3 = r * r * r;
-        LR arg = r3 > LR(0) ? c0 / (LR(2) * r3) : LR(1);
-        arg = arg > LR(1) ? LR(1) : (arg < LR(-1) ? LR(-1) : arg);
-        lam = LR(2) * r * r_cos(r_acos(arg) / LR(3));
+    const LR M = r_sqrt(Ttx * Ttx + Tty * Tty);
+    const LR disc = LR(9) * E * E - LR(8) * M * M;
+    const LR b0 = LR(4) * M / (LR(3) * E + r_sqrt(disc > LR(0) ? disc : LR(0)));
+    LR lam = E - b0 * M;
+    if ((lam * lam + c1) * lam - c0 < LR(0)) lam = E;
+    const LR tol = LR(sizeof(LR) == 8 ? 4e-16 : 2e-7);
+#pragma unroll 1
+    for (int it = 0; it < 24; ++it) {
         const LR P = (lam * lam + c1) * lam - c0;
         const LR dP = LR(3) * lam * lam + c1;
-        if (dP != LR(0)) lam -= P / dP;
+        if (!(dP > LR(0))) break;
+        const LR d = P / dP;
+        lam -= d;
+        if (!(fabs(d) > tol * lam)) break;
     }
     eps = lam;
-    // eigenvector: orthogonal to the rows of A - eps I
-    const LR a00 = Ttt - lam, a01 = -Ttx, a02 = -Tty;
-    const LR a10 = Ttx, a11 = -Txx - lam, a12 = -Txy;
-    const LR a20 = Tty, a21 = -Txy, a22 = -Tyy - lam;
-    LR v0 = a01 * a12 - a02 * a11, v1 = a02 * a10 - a00 * a12, v2 = a00 * a11 - a01 * a10;
-    LR nn = v0 * v0 + v1 * v1 + v2 * v2;
-    {
-        const LR w0 = a11 * a22 - a12 * a21, w1 = a12 * a20 - a10 * a22, w2 = a10 * a21 - a11 * a20;
-        const LR wn = w0 * w0 + w1 * w1 + w2 * w2;
-        if (wn > nn) { v0 = w0; v1 = w1; v2 = w2; nn = wn; }
-        const LR z0 = a21 * a02 - a22 * a01, z1 = a22 * a00 - a20 * a02, z2 = a20 * a01 - a21 * a00;
-        const LR zn = z0 * z0 + z1 * z1 + z2 * z2;
-        if (zn > nn) { v0 = z0; v1 = z1; v2 = z2; nn = zn; }
-    }
+    const LR bx = Txx + lam, by = Tyy + lam;
+    const LR v0 = bx * by - Txy * Txy;
+    const LR v1 = Ttx * by - Txy * Tty;
+    const LR v2 = bx * Tty - Ttx * Txy;
     const LR mink = v0 * v0 - v1 * v1 - v2 * v2;
-    if (mink > LR(0)) {
-        LR s = r_rsqrt(mink);
-        if (v0 < LR(0)) s = -s;
+    bool ok = (c1 < LR(0)) && (v0 > LR(0)) && (mink > LR(0));
+    if (ok) {
+        const LR s = r_rsqrt(mink);
         U0 = v0 * s;
         Ux = v1 * s;
         Uy = v2 * s;
     } else {
-        ok = false;
         U0 = LR(1);
         Ux = LR(0);
         Uy = LR(0);
@@ -133,7 +256,7 @@ __device__ __forceinline__ bool landau_frame(const LR *m, LR &n, LR &eps, LR &U0
     if (!(n > LR(0)) || !(eps > LR(0))) {
         ok = false;
         n = Nt > LR(0) ? Nt : LR(1e-30);
-        if (!(eps > LR(0))) eps = Ttt > LR(0) ? Ttt : LR(1e-30);
+        if (!(eps > LR(0))) eps = E > LR(0) ? E : LR(1e-30);
     }
     return ok;
 }
@@ -150,12 +273,13 @@ __device__ __forceinline__ bool landau_frame(const LR *m, LR &n, LR &eps, LR &U0
 // equispaced directions integrate it exactly.  The radial Gram inverse,
 // k!/(N+1), the angular norms and p_r^l are folded into rtab = R'[r][m][k]:
 //   C_{r,m} = sum_k R'[r][m][k] n T^(k-1) acc_{m,k},  acc = sum_j q0^(k-m) z^m.
-// Output coef[r][0] = Re C_{r,0} - beta; coef[r][2m-1], coef[r][2m] = Re, Im C_{r,m}.
-template <int N, class LR>
-__device__ __forceinline__ void feq_coefficients(const KernelArgs &a, const LR *rtab, LR n, LR T,
-                                                 LR U0, LR Ux, LR Uy, LR *coef /* (N+1)(2N+1) */)
+// This returns the coefficients of one energy shell r in stored units:
+// cr[0] = Re C_{r,0} - feq_off, cr[2m-1], cr[2m] = Re, Im C_{r,m}.
+template <int N, class LR, class R>
+__device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, LR n, LR T, LR U0,
+                                                   LR Ux, LR Uy, R *cr)
 {
-    LR accr[N + 1][N + 1], acci[N + 1][N + 1]; // [m][k]
+    LR accr[N + 1][N + 1], acci[N + 1][N + 1];
 #pragma unroll
     for (int m = 0; m <= N; ++m)
 #pragma unroll
@@ -163,7 +287,7 @@ __device__ __forceinline__ void feq_coefficients(const KernelArgs &a, const LR *
     const LR inv1g = LR(1) / (LR(1) + U0);
 #pragma unroll
     for (int j = 0; j <= N; ++j) {
-        const LR cj = LR(a.smp_c[j]), sj = LR(a.smp_s[j]);
+        const LR cj = Par<LR>::smp_c(a, j), sj = Par<LR>::smp_s(a, j);
         const LR un = Ux * cj + Uy * sj;
         const LR q0 = U0 + un;
         const LR h = LR(1) + un * inv1g;
@@ -190,50 +314,23 @@ __device__ __forceinline__ void feq_coefficients(const KernelArgs &a, const LR *
     tk[0] = n / T;
 #pragma unroll
     for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
+    const LR *rt = reinterpret_cast<const LR *>(a.rtab) + r * (N + 1) * (N + 1);
 #pragma unroll
-    for (int r = 0; r <= N; ++r) {
+    for (int m = 0; m <= N; ++m) {
+        LR cre = LR(0), cim = LR(0);
 #pragma unroll
-        for (int m = 0; m <= N; ++m) {
-            LR cr = LR(0), ci = LR(0);
-#pragma unroll
-            for (int k = m; k <= N; ++k) {
-                const LR wgt = rtab[(r * (N + 1) + m) * (N + 1) + k] * tk[k];
-                cr += wgt * accr[m][k];
-                ci += wgt * acci[m][k];
-            }
-            if (m == 0) {
-                coef[r * (2 * N + 1)] = cr - LR(a.beta);
-            } else {
-                coef[r * (2 * N + 1) + 2 * m - 1] = cr;
-                coef[r * (2 * N + 1) + 2 * m] = ci;
-            }
+        for (int k = m; k <= N; ++k) {
+            const LR wgt = __ldg(rt + m * (N + 1) + k) * tk[k];
+            cre += wgt * accr[m][k];
+            cim += wgt * acci[m][k];
+        }
+        if (m == 0) {
+            cr[0] = R(cre - Par<LR>::feq_off(a));
+        } else {
+            cr[2 * m - 1] = R(cre);
+            cr[2 * m] = R(cim);
         }
     }
-}
-
-template <class R> struct Vec4;
-template <> struct Vec4<float> {
-    using T = float4;
-};
-template <> struct Vec4<double> {
-    using T = double4;
-};
-
-template <class R>
-__device__ __forceinline__ void ld4(const R *p, R &x, R &y, R &z, R &w);
-template <>
-__device__ __forceinline__ void ld4<float>(const float *p, float &x, float &y, float &z, float &w)
-{
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-    x = v.x; y = v.y; z = v.z; w = v.w;
-}
-template <>
-__device__ __forceinline__ void ld4<double>(const double *p, double &x, double &y, double &z,
-                                            double &w)
-{
-    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
-    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-    x = v0.x; y = v0.y; z = v1.x; w = v1.y;
 }
 
 // St: storage type; R: per-population arithmetic; LR: per-site arithmetic
@@ -258,130 +355,78 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     const R *tab = reinterpret_cast<const R *>(a.poptab) + (long long)i0 * TW;
     const St *fin = reinterpret_cast<const St *>(a.fin);
     St *fout = reinterpret_cast<St *>(a.fout);
-
-    LR *red = reinterpret_cast<LR *>(smem_raw);                  // [5][G][32]
-    LR *coefs = red + 5 * G * 32;                                  // [(N+1)*NC][32]
-    LR *oms = coefs + (N + 1) * NC * 32;                           // [3][32]
+    LR *red = reinterpret_cast<LR *>(smem_raw); // [5][G][32]
 
     R fs[P];
     const bool stream = (MODE == MODE_STEP);
     const bool need_site = (MODE != MODE_STEP) || a.collide;
 
     if (MODE != MODE_INIT) {
-        R s0 = R(0), sc = R(0), ss = R(0), scc = R(0), scs = R(0);
+        // two partial sums per moment (even / odd populations) halve the add chains
+        R s0[2] = {R(0), R(0)}, sc[2] = {R(0), R(0)}, ss[2] = {R(0), R(0)};
+        R scc[2] = {R(0), R(0)}, scs[2] = {R(0), R(0)};
         const int xm = bc_index(x - 1, a.nx, a.bcx), xp = bc_index(x + 1, a.nx, a.bcx);
         const int ym = TWO_D ? bc_index(y - 1, a.ny, a.bcy) : y;
         const int yp = TWO_D ? bc_index(y + 1, a.ny, a.bcy) : y;
+        const unsigned long long mx = stream ? __ldg(a.masks + 2 * g) : 0ull;
+        const unsigned long long my = stream ? __ldg(a.masks + 2 * g + 1) : 0ull;
         const St *base = fin + (long long)i0 * S + (long long)y * a.nx;
+        const long long dym = (long long)(ym - y) * a.nx, dyp = (long long)(yp - y) * a.nx;
+        // Loads first (a chunk of populations at a time, all independent), then
+        // arithmetic: the pull direction of population k comes from the warp's
+        // sign masks, so no load waits for the table.
+        constexpr int CH = TWO_D ? (P > 16 ? 8 : P) : (P > 32 ? 16 : P);
 #pragma unroll
-        for (int k = 0; k < P; ++k) {
-            if (k < pc) {
-                R c, s, cc, cs;
-                ld4<R>(tab + k * TW, c, s, cc, cs);
-                R v;
-                if (stream) {
-                    const R ax = fabs(c);
-                    const int xs = c >= R(0) ? xm : xp; // pull from x - sgn(v_x)
-                    const R f00 = Io<St, R>::ld(base + x);
-                    const R f01 = Io<St, R>::ld(base + xs);
-                    R lo = f00 + ax * (f01 - f00);
-                    if (TWO_D) {
-                        const R ay = fabs(s);
-                        const long long dy = (long long)((s >= R(0) ? ym : yp) - y) * a.nx;
-                        const R f10 = Io<St, R>::ld(base + dy + x);
-                        const R f11 = Io<St, R>::ld(base + dy + xs);
-                        const R hi = f10 + ax * (f11 - f10);
-                        lo = lo + ay * (hi - lo);
+        for (int c0 = 0; c0 < P; c0 += CH) {
+            R fa[CH], fb[CH], fc[TWO_D ? CH : 1], fd[TWO_D ? CH : 1];
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                const int k = c0 + kk;
+                const St *pk = base + (long long)k * S;
+                if (k < pc) {
+                    fa[kk] = Io<St, R>::ld(pk + x);
+                    if (stream) {
+                        const int xs = ((mx >> k) & 1ull) ? xm : xp; // pull from x - sgn(v_x)
+                        fb[kk] = Io<St, R>::ld(pk + xs);
+                        if (TWO_D) {
+                            const long long dy = ((my >> k) & 1ull) ? dym : dyp;
+                            fc[kk] = Io<St, R>::ld(pk + dy + x);
+                            fd[kk] = Io<St, R>::ld(pk + dy + xs);
+                        }
                     }
-                    v = lo;
-                } else {
-                    v = Io<St, R>::ld(base + x);
                 }
-                fs[k] = v;
-                s0 += v;
-                sc += c * v;
-                ss += s * v;
-                scc += cc * v;
-                scs += cs * v;
             }
-            base += S;
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                const int k = c0 + kk;
+                if (k < pc) {
+                    R c, s, cc, cs;
+                    ld4<R>(tab + k * TW, c, s, cc, cs);
+                    R v = fa[kk];
+                    if (stream) {
+                        v = v + fabs(c) * (fb[kk] - v);
+                        if (TWO_D) {
+                            const R hi = fc[kk] + fabs(c) * (fd[kk] - fc[kk]);
+                            v = v + fabs(s) * (hi - v);
+                        }
+                    }
+                    fs[k] = v;
+                    s0[k & 1] += v;
+                    sc[k & 1] += c * v;
+                    ss[k & 1] += s * v;
+                    scc[k & 1] += cc * v;
+                    scs[k & 1] += cs * v;
+                }
+            }
         }
         if (need_site) {
-            red[(0 * G + g) * 32 + lane] = LR(s0);
-            red[(1 * G + g) * 32 + lane] = LR(sc);
-            red[(2 * G + g) * 32 + lane] = LR(ss);
-            red[(3 * G + g) * 32 + lane] = LR(scc);
-            red[(4 * G + g) * 32 + lane] = LR(scs);
+            red[(0 * G + g) * 32 + lane] = LR(s0[0] + s0[1]);
+            red[(1 * G + g) * 32 + lane] = LR(sc[0] + sc[1]);
+            red[(2 * G + g) * 32 + lane] = LR(ss[0] + ss[1]);
+            red[(3 * G + g) * 32 + lane] = LR(scc[0] + scc[1]);
+            red[(4 * G + g) * 32 + lane] = LR(scs[0] + scs[1]);
         }
     }
-
-    if (need_site) {
-        __syncthreads();
-        if (g == 0) {
-            LR n, eps, U0, Ux, Uy, T;
-            bool ok = true;
-            if (MODE == MODE_INIT) {
-                const double bx = a.in_bx[site], by = a.in_by[site];
-                const double gam = 1.0 / sqrt(1.0 - bx * bx - by * by);
-                n = LR(a.in_n[site]);
-                T = LR(a.in_T[site]);
-                U0 = LR(gam);
-                Ux = LR(gam * bx);
-                Uy = LR(gam * by);
-                eps = LR(2) * n * T;
-            } else {
-                const LR *sh = reinterpret_cast<const LR *>(a.shelltab);
-                LR m[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) m[t] = LR(a.off[t]);
-                for (int rr = 0; rr <= N; ++rr) {
-                    LR p0 = LR(0), pc_ = LR(0), ps = LR(0), pcc = LR(0), pcs = LR(0);
-                    for (int qq = 0; qq < a.Gs; ++qq) {
-                        const int w = rr * a.Gs + qq;
-                        p0 += red[(0 * G + w) * 32 + lane];
-                        pc_ += red[(1 * G + w) * 32 + lane];
-                        ps += red[(2 * G + w) * 32 + lane];
-                        pcc += red[(3 * G + w) * 32 + lane];
-                        pcs += red[(4 * G + w) * 32 + lane];
-                    }
-                    const LR f1 = sh[2 * rr], f2 = sh[2 * rr + 1];
-                    m[0] += f1 * p0;
-                    m[1] += f1 * pc_;
-                    m[2] += f1 * ps;
-                    m[3] += f2 * p0;
-                    m[4] += f2 * pc_;
-                    m[5] += f2 * ps;
-                    m[6] += f2 * pcc;
-                    m[7] += f2 * pcs;
-                }
-                ok = landau_frame<LR>(m, n, eps, U0, Ux, Uy);
-                T = eps / (LR(2) * n);
-                if (!ok && act) atomicOr(a.status, 1);
-            }
-            if (MODE == MODE_MOMENTS) {
-                if (act) {
-                    a.out[0][site] = double(n);
-                    a.out[1][site] = double(eps);
-                    a.out[2][site] = double(T);
-                    a.out[3][site] = double(U0);
-                    a.out[4][site] = double(Ux);
-                    a.out[5][site] = double(Uy);
-                }
-            } else {
-                LR cf[(N + 1) * NC];
-                feq_coefficients<N, LR>(a, reinterpret_cast<const LR *>(a.rtab), n, T, U0, Ux, Uy,
-                                        cf);
-#pragma unroll
-                for (int t = 0; t < (N + 1) * NC; ++t) coefs[t * 32 + lane] = cf[t];
-                const LR it = LR(a.inv_tau);
-                oms[0 * 32 + lane] = U0 * it;
-                oms[1 * 32 + lane] = Ux * it;
-                oms[2 * 32 + lane] = Uy * it;
-            }
-        }
-        __syncthreads();
-    }
-    if (MODE == MODE_MOMENTS) return;
 
     St *obase = fout + (long long)i0 * S + site;
     if (!need_site) { // free streaming: f <- f*
@@ -392,10 +437,45 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         }
         return;
     }
+    if (MODE != MODE_INIT) __syncthreads();
+    if (MODE == MODE_MOMENTS && g != 0) return;
+
+    // every warp: the Landau frame of its 32 sites and its own shell's coefficients
+    LR n, eps, U0, Ux, Uy, T;
+    if (MODE == MODE_INIT) {
+        const double bx = a.in_bx[site], by = a.in_by[site];
+        const double gam = 1.0 / sqrt(1.0 - bx * bx - by * by);
+        n = LR(a.in_n[site]);
+        T = LR(a.in_T[site]);
+        U0 = LR(gam);
+        Ux = LR(gam * bx);
+        Uy = LR(gam * by);
+        eps = LR(2) * n * T;
+    } else {
+        LR m[8];
+        fold_moments<N, LR>(a, red, G, lane, m);
+        const bool ok = landau_fast<LR>(m, n, eps, U0, Ux, Uy);
+        T = eps / (LR(2) * n);
+        if (!ok && act && g == 0) atomicOr(a.status, 1);
+    }
+    if (MODE == MODE_MOMENTS) {
+        if (act) {
+            a.out[0][site] = double(n);
+            a.out[1][site] = double(eps);
+            a.out[2][site] = double(T);
+            a.out[3][site] = double(U0);
+            a.out[4][site] = double(Ux);
+            a.out[5][site] = double(Uy);
+        }
+        return;
+    }
     R cr[NC];
-#pragma unroll
-    for (int t = 0; t < NC; ++t) cr[t] = R(coefs[(r * NC + t) * 32 + lane]);
-    const R o0 = R(oms[lane]), o1 = R(oms[32 + lane]), o2 = R(oms[64 + lane]);
+    shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
+    const LR itau = Par<LR>::inv_tau(a);
+    const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
+    constexpr bool kSR = (sizeof(St) == 2) && (MODE == MODE_STEP);
+    unsigned rng = 0;
+    if (kSR) rng = mix32(unsigned(site) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         if (k < pc) {
@@ -415,8 +495,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
                 const R om = o0 - o1 * c - o2 * s;
                 out = fs[k] + om * (feq - fs[k]);
             }
-            if (act) Io<St, R>::st(obase + (long long)k * S, out);
+            if (kSR) {
+                if (act) SR<St>::st(obase + (long long)k * S, out, rng);
+            } else if (act) {
+                Io<St, R>::st(obase + (long long)k * S, out);
+            }
         }
+    }
+    if (kSR) {
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) advance_launch_counter(a.ctr, gridDim.x * gridDim.y);
     }
 }
 

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -168,7 +169,9 @@ size_t storage_size(int prec)
     case RLBM_FP64: return 8;
     case RLBM_FP32: return 4;
     case RLBM_FP16_DEV:
-    case RLBM_BF16_DEV: return 2;
+    case RLBM_BF16_DEV:
+    case RLBM_FP16_NORM:
+    case RLBM_BF16_NORM: return 2;
     default: return 0;
     }
 }
@@ -195,6 +198,13 @@ struct rlbm {
     bool site_fp64 = false;
     // CUDA graphs of kGraphSteps steps starting from buffer 0 / buffer 1
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // persistent TMA-staged step kernel (when the grid allows it)
+    bool use_tma = false;
+    rlbmk::TmaArgs *tma = nullptr; // [2]: input buffer 0 / 1
+    int tma_grid = 0;
+    size_t tma_smem = 0;
+    int sm_count = 0;
+    bool stall_next = false; // test hook: next launch waits for bytes that never arrive
     std::string err;
 };
 
@@ -230,12 +240,12 @@ rlbm_status cuda_fail(rlbm_t *h, cudaError_t e, const char *what)
 // then the larger P (fewer warps sharing the per-site work).
 bool choose_tiling(int N, int K, int &P, int &Gs)
 {
-    static const int sizes[] = {8, 12, 16, 24, 32};
+    static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
     int best_waste = 1 << 30;
     bool found = false;
     for (int gs = 1; gs * (N + 1) <= rlbmk::kMaxWarps; ++gs) {
         const int need = (K + gs - 1) / gs;
-        if (need > 32 || (gs - 1) * need >= K) continue;
+        if (need > 64 || (gs - 1) * need >= K) continue;
         int p = 0;
         for (int s : sizes)
             if (s >= need) { p = s; break; }
@@ -265,15 +275,19 @@ rlbm_status build_tables(rlbm_t *h)
 {
     const int N = h->N, K = h->K, npop = h->npop;
     const Quad &q = h->q;
+    // 16-bit storage keeps f_i relative to the rest equilibrium at n = 1, T = 1,
+    // f^rest_i = w_i / (2 pi):  f_i = alpha_i (s_i + beta), alpha_i = f^rest_i,
+    // beta = 1 for the deviation form, 0 for the normalised form.
+    const bool scaled = storage_size(h->prec) == 2;
     const bool dev = (h->prec == RLBM_FP16_DEV || h->prec == RLBM_BF16_DEV);
-    const double beta = dev ? 1.0 / (2.0 * kPi) : 0.0;
+    const double beta = dev ? 1.0 : 0.0;
     const int TW = rlbmk::tab_width(N);
 
-    // per-population table in stored units: f_i = alpha_i (s_i + beta)
+    // per-population table in stored units
     std::vector<double> pop(size_t(npop) * TW, 0.0);
     for (int i = 0; i < npop; ++i) {
         const double c = q.vx[i], s = q.vy[i];
-        const double alpha = dev ? q.w[i] : 1.0;
+        const double alpha = scaled ? q.w[i] / (2.0 * kPi) : 1.0;
         const double th = std::atan2(s, c);
         double *t = &pop[size_t(i) * TW];
         t[0] = c;
@@ -289,7 +303,7 @@ rlbm_status build_tables(rlbm_t *h)
     // per-shell folds alpha_r p_r, alpha_r p_r^2
     std::vector<double> shell(size_t(N + 1) * 2);
     for (int r = 0; r <= N; ++r) {
-        const double alpha = dev ? q.w[r * K] : 1.0;
+        const double alpha = scaled ? q.w[r * K] / (2.0 * kPi) : 1.0;
         shell[2 * r] = alpha * q.pr[r];
         shell[2 * r + 1] = alpha * q.pr[r] * q.pr[r];
     }
@@ -313,7 +327,7 @@ rlbm_status build_tables(rlbm_t *h)
     double off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (dev) {
         for (int i = 0; i < npop; ++i) {
-            const double a = q.w[i] * beta, p = q.p0[i], c = q.vx[i], s = q.vy[i];
+            const double a = q.w[i] / (2.0 * kPi) * beta, p = q.p0[i], c = q.vx[i], s = q.vy[i];
             off[0] += a * p;
             off[1] += a * p * c;
             off[2] += a * p * s;
@@ -325,22 +339,39 @@ rlbm_status build_tables(rlbm_t *h)
         }
     }
 
+    // per-warp sign masks of the populations it owns
+    static_assert(sizeof(unsigned long long) == 8, "64-bit masks");
+    if (h->P > 64) return fail(h, RLBM_ERR_UNSUPPORTED, "at most 64 populations per warp");
+    std::vector<unsigned long long> masks(size_t(h->G) * 2, 0ull);
+    for (int g = 0; g < h->G; ++g) {
+        const int r = g / h->Gs, qq = g % h->Gs;
+        for (int k = 0; k < h->P; ++k) {
+            const int j = qq * h->P + k;
+            if (j >= K) break;
+            const int i = r * K + j;
+            if (q.vx[i] >= 0.0) masks[2 * g] |= 1ull << k;
+            if (q.vy[i] >= 0.0) masks[2 * g + 1] |= 1ull << k;
+        }
+    }
+
     const bool r64 = (h->prec == RLBM_FP64);
     const bool l64 = r64 || h->site_fp64;
     const size_t rs = r64 ? 8 : 4, ls = l64 ? 8 : 4;
     const size_t o_pop = 0;
     const size_t o_shell = align256(pop.size() * rs);
     const size_t o_rt = o_shell + align256(shell.size() * ls);
-    const size_t total = o_rt + align256(rt.size() * ls);
+    const size_t o_mask = o_rt + align256(rt.size() * ls);
+    const size_t total = o_mask + align256(masks.size() * sizeof(unsigned long long));
     std::vector<unsigned char> blob(total, 0);
     if (r64) put<double>(blob, o_pop, pop); else put<float>(blob, o_pop, pop);
     if (l64) { put<double>(blob, o_shell, shell); put<double>(blob, o_rt, rt); }
     else { put<float>(blob, o_shell, shell); put<float>(blob, o_rt, rt); }
+    std::memcpy(blob.data() + o_mask, masks.data(), masks.size() * sizeof(unsigned long long));
 
     RLBM_CUDA(h, cudaMalloc(&h->d_tabs, total));
-    RLBM_CUDA(h, cudaMalloc(&h->d_status, sizeof(int)));
+    RLBM_CUDA(h, cudaMalloc(&h->d_status, 4 * sizeof(int))); // status, launch counter, CTAs done
     RLBM_CUDA(h, cudaMemcpyAsync(h->d_tabs, blob.data(), total, cudaMemcpyHostToDevice, h->stream));
-    RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, 4 * sizeof(int), h->stream));
     RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
 
     rlbmk::KernelArgs &a = h->base;
@@ -356,16 +387,26 @@ rlbm_status build_tables(rlbm_t *h)
     a.collide = std::isinf(h->tau) ? 0 : 1;
     a.inv_tau = std::isinf(h->tau) ? 0.0 : 1.0 / h->tau;
     a.beta = beta;
-    for (int t = 0; t < 8; ++t) a.off[t] = off[t];
+    a.inv_tau_f = float(a.inv_tau);
+    a.feq_off = scaled ? beta / (2.0 * kPi) : 0.0;
+    a.feq_off_f = float(a.feq_off);
+    for (int t = 0; t < 8; ++t) {
+        a.off[t] = off[t];
+        a.off_f[t] = float(off[t]);
+    }
     for (int j = 0; j <= N; ++j) {
         const double ph = 2.0 * kPi * j / (N + 1);
         a.smp_c[j] = std::cos(ph);
         a.smp_s[j] = std::sin(ph);
+        a.smp_cf[j] = float(a.smp_c[j]);
+        a.smp_sf[j] = float(a.smp_s[j]);
     }
     a.poptab = (const unsigned char *)h->d_tabs + o_pop;
     a.shelltab = (const unsigned char *)h->d_tabs + o_shell;
     a.rtab = (const unsigned char *)h->d_tabs + o_rt;
+    a.masks = reinterpret_cast<const unsigned long long *>((const unsigned char *)h->d_tabs + o_mask);
     a.status = h->d_status;
+    a.ctr = reinterpret_cast<unsigned *>(h->d_status + 1);
     return RLBM_OK;
 }
 
@@ -373,9 +414,8 @@ void *buffer(rlbm_t *h, int which) { return (unsigned char *)h->buf + size_t(whi
 
 size_t smem_bytes(const rlbm_t *h)
 {
-    const int N = h->N;
     const size_t ls = (h->prec == RLBM_FP64 || h->site_fp64) ? 8 : 4;
-    return ls * (5 * size_t(h->G) * 32 + size_t(N + 1) * (2 * N + 1) * 32 + 3 * 32);
+    return ls * 5 * size_t(h->G) * 32;
 }
 
 cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
@@ -390,19 +430,125 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     case RLBM_FP32:
         e = rlbmk::launch_f32(mode, h->N, h->P, two_d, h->site_fp64, grid, block, smem, h->stream, a);
         break;
-    case RLBM_FP16_DEV: e = rlbmk::launch_f16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    case RLBM_FP16_DEV:
+    case RLBM_FP16_NORM: e = rlbmk::launch_f16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
     default: e = rlbmk::launch_bf16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
     }
     if (e == cudaSuccess) ++h->launches;
     return e;
 }
 
+cudaError_t launch_tma(rlbm_t *h, const rlbmk::TmaArgs &ta, int grid, int *bps)
+{
+    const dim3 block(32, h->G);
+    const bool two_d = h->grid.ny > 1;
+    switch (h->prec) {
+    case RLBM_FP64: return rlbmk::launch_tma_f64(h->N, h->P, two_d, false, grid, block, h->tma_smem, h->stream, ta, bps);
+    case RLBM_FP32: return rlbmk::launch_tma_f32(h->N, h->P, two_d, h->site_fp64, grid, block, h->tma_smem, h->stream, ta, bps);
+    case RLBM_FP16_DEV:
+    case RLBM_FP16_NORM: return rlbmk::launch_tma_f16(h->N, h->P, two_d, false, grid, block, h->tma_smem, h->stream, ta, bps);
+    default: return rlbmk::launch_tma_bf16(h->N, h->P, two_d, false, grid, block, h->tma_smem, h->stream, ta, bps);
+    }
+}
+
 cudaError_t launch_step(rlbm_t *h, int from)
 {
+    if (h->use_tma) {
+        rlbmk::TmaArgs &ta = h->tma[from];
+        ta.a.fin = buffer(h, from);
+        ta.a.fout = buffer(h, 1 - from);
+        ta.extra_tx = h->stall_next ? 16u : 0u;
+        h->stall_next = false;
+        cudaError_t e = launch_tma(h, ta, h->tma_grid, nullptr);
+        ta.extra_tx = 0;
+        if (e == cudaSuccess) ++h->launches;
+        return e;
+    }
     rlbmk::KernelArgs a = h->base;
     a.fin = buffer(h, from);
     a.fout = buffer(h, 1 - from);
     return launch(h, rlbmk::MODE_STEP, a);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Set up the persistent TMA-staged step kernel if the grid satisfies the
+// tensor-map rules (16-byte row pitch, at least one box wide); otherwise the
+// per-tile kernel is used.
+rlbm_status setup_tma(rlbm_t *h)
+{
+    const char *off = std::getenv("RLBM_NO_TMA");
+    if (off && off[0] == '1') return RLBM_OK;
+    const size_t es = storage_size(h->prec);
+    const int HX = int(16 / es), BW = 32 + 2 * HX;
+    const int nx = h->grid.nx, ny = h->grid.ny, npop = h->npop;
+    if ((size_t(nx) * es) % 16 != 0 || nx < BW) return RLBM_OK;
+    int nbox = (npop + 255) / 256;
+    int BP = (npop + nbox - 1) / nbox;
+    BP = (BP + 3) / 4 * 4;
+    if (BP > 256 || (npop <= 256 && BP != npop)) return RLBM_OK; // keep every box inside the tensor
+    const int BR = ny > 1 ? 3 : 1;
+    const size_t box_bytes = size_t(BP) * BW * es;
+    const size_t stage = rlbmk::align_up(size_t(BR) * nbox * box_bytes, 1024);
+    const size_t ls = (h->prec == RLBM_FP64 || h->site_fp64) ? 8 : 4;
+    const size_t rs = (h->prec == RLBM_FP64) ? 8 : 4;
+    const rlbmk::TmaSmem L(stage, h->G, h->P, h->N, rs, ls);
+    int dev = 0, max_smem = 0;
+    RLBM_CUDA(h, cudaGetDevice(&dev));
+    RLBM_CUDA(h, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    RLBM_CUDA(h, cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    if (L.total > size_t(max_smem)) return RLBM_OK;
+
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qres;
+    RLBM_CUDA(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &qres));
+    if (!fn || qres != cudaDriverEntryPointSuccess)
+        return fail(h, RLBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+    CUtensorMapDataType dt;
+    switch (h->prec) {
+    case RLBM_FP64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+    case RLBM_FP32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case RLBM_FP16_DEV:
+    case RLBM_FP16_NORM: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    default: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    }
+    h->tma = new (std::nothrow) rlbmk::TmaArgs[2];
+    if (!h->tma) return fail(h, RLBM_ERR_OOM, "host allocation failed");
+    const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(npop)};
+    const cuuint64_t strides[2] = {cuuint64_t(nx) * es, cuuint64_t(nx) * ny * es};
+    const cuuint32_t box[3] = {cuuint32_t(BW), 1u, cuuint32_t(BP)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const int ntiles_x = (nx + 31) / 32;
+    for (int b = 0; b < 2; ++b) {
+        rlbmk::TmaArgs &ta = h->tma[b];
+        std::memset(&ta, 0, sizeof(ta));
+        CUresult r = encode(&ta.tmap, dt, 3, buffer(h, b), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, RLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+        ta.a = h->base;
+        ta.BP = BP;
+        ta.nbox = nbox;
+        ta.ntiles_x = ntiles_x;
+        ta.ntiles = ntiles_x * ny;
+        ta.stage_bytes = (long long)stage;
+        ta.wait_cycles = 4000000000LL; // about 2 s at the maximum SM clock
+        ta.extra_tx = 0;
+    }
+    h->tma_smem = L.total;
+    int bps = 0;
+    cudaError_t e = launch_tma(h, h->tma[0], 0, &bps);
+    if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query of the TMA step kernel");
+    if (bps < 1) return RLBM_OK;
+    const long long ntiles = (long long)ntiles_x * ny;
+    h->tma_grid = int(std::min<long long>(ntiles, (long long)bps * h->sm_count));
+    h->use_tma = true;
+    return RLBM_OK;
 }
 
 rlbm_status check_status(rlbm_t *h)
@@ -412,6 +558,10 @@ rlbm_status check_status(rlbm_t *h)
     RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
     if (st) {
         RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+        RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (st & 2)
+            return fail(h, RLBM_ERR_TIMEOUT,
+                        "a bounded wait in the step kernel ran out (its copies did not complete in time)");
         return fail(h, RLBM_ERR_UNPHYSICAL,
                     "a cell had no physical Landau frame (non-positive n or eps, or no timelike eigenvector)");
     }
@@ -511,6 +661,16 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
         delete h;
         return fail(nullptr, RLBM_ERR_UNSUPPORTED, "no compiled tiling for K=%d", angles_K);
     }
+    if (const char *ep = std::getenv("RLBM_TILE_P")) { // experiment hook: force P if it fits
+        const int P = std::atoi(ep);
+        const int gs = (angles_K + P - 1) / P;
+        if ((P == 8 || P == 12 || P == 16 || P == 24 || P == 32 || P == 48 || P == 64) &&
+            gs * (order_N + 1) <= rlbmk::kMaxWarps &&
+            (gs - 1) * P < angles_K) {
+            h->P = P;
+            h->Gs = gs;
+        }
+    }
     h->G = h->Gs * (order_N + 1);
     h->pop_bytes = rlbm_population_bytes(grid, order_N, angles_K, precision);
 
@@ -538,6 +698,7 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
         }
     }
     if (st == RLBM_OK) st = build_tables(h);
+    if (st == RLBM_OK) st = setup_tma(h);
     if (st != RLBM_OK) {
         g_create_error = h->err;
         rlbm_destroy(h);
@@ -557,6 +718,7 @@ void rlbm_destroy(rlbm_t *h)
     if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->d_status) cudaFree(h->d_status);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete[] h->tma;
     delete h;
 }
 
@@ -578,6 +740,8 @@ rlbm_status rlbm_init_device(rlbm_t *h, const double *d_n, const double *d_T, co
     a.in_T = d_T;
     a.in_bx = d_bx;
     a.in_by = d_by;
+    // the launch counter seeds the stochastic rounding of 16-bit storage: restart it
+    RLBM_CUDA(h, cudaMemsetAsync(h->d_status + 1, 0, 2 * sizeof(int), h->stream));
     cudaError_t e = launch(h, rlbmk::MODE_INIT, a);
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
     h->cur = 0;
@@ -687,6 +851,8 @@ rlbm_status rlbm_set_populations(rlbm_t *h, const void *host, size_t bytes, long
     if (!host || bytes != h->pop_bytes)
         return fail(h, RLBM_ERR_ARG, "need a host buffer of exactly %zu bytes", h->pop_bytes);
     RLBM_CUDA(h, cudaMemcpyAsync(buffer(h, 0), host, bytes, cudaMemcpyHostToDevice, h->stream));
+    const unsigned ctr[2] = {unsigned(step), 0u};
+    RLBM_CUDA(h, cudaMemcpyAsync(h->d_status + 1, ctr, sizeof(ctr), cudaMemcpyHostToDevice, h->stream));
     RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->cur = 0;
     h->steps = step;
@@ -704,5 +870,24 @@ rlbm_status rlbm_sync(rlbm_t *h)
 }
 
 long long rlbm_kernel_launches(const rlbm_t *h) { return h ? h->launches : -1; }
+
+int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? (h->use_tma ? 1 : 0) : -1; }
+
+rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (cycles < 1000) return fail(h, RLBM_ERR_ARG, "wait limit must be >= 1000 cycles");
+    if (h->tma)
+        for (int b = 0; b < 2; ++b) h->tma[b].wait_cycles = cycles;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_test_stall_next_step(rlbm_t *h)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (!h->use_tma) return fail(h, RLBM_ERR_UNSUPPORTED, "the per-tile step kernel has no device waits");
+    h->stall_next = true;
+    return RLBM_OK;
+}
 
 } // extern "C"

@@ -37,6 +37,8 @@ static cudaError_t launch_n(int mode, int P, bool two_d, dim3 grid, dim3 block, 
     case 16: return launch_np<St, R, LR, N, 16>(mode, two_d, grid, block, smem, st, a);
     case 24: return launch_np<St, R, LR, N, 24>(mode, two_d, grid, block, smem, st, a);
     case 32: return launch_np<St, R, LR, N, 32>(mode, two_d, grid, block, smem, st, a);
+    case 48: return launch_np<St, R, LR, N, 48>(mode, two_d, grid, block, smem, st, a);
+    case 64: return launch_np<St, R, LR, N, 64>(mode, two_d, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -17,8 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librlbm.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_UNPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
-STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+# fp16 / bf16: s = f / f^rest - 1 (deviation from the rest equilibrium at n = 1, T = 1);
+# fp16n / bf16n: s = f / f^rest (normalised); f^rest_i = w_i / (2 pi).
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "fp16n": 4, "bf16n": 5}
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "fp16n": 2, "bf16n": 2}
 BC_PERIODIC, BC_COPYOUT = 0, 1
 
 # Symbols declared in include/rlbm.h (checked by the CPU test suite).
@@ -27,6 +30,7 @@ EXPORTS = [
     "rlbm_last_error", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
+    "rlbm_step_kernel_variant", "rlbm_set_wait_limit", "rlbm_test_stall_next_step",
 ]
 
 
@@ -37,6 +41,10 @@ class RLBMError(RuntimeError):
 
 
 class Unphysical(RLBMError):
+    pass
+
+
+class DeviceTimeout(RLBMError):
     pass
 
 
@@ -92,6 +100,12 @@ def lib(path: str = LIB_PATH):
     L.rlbm_sync.argtypes = [_vp]
     L.rlbm_kernel_launches.restype = ctypes.c_longlong
     L.rlbm_kernel_launches.argtypes = [_vp]
+    L.rlbm_step_kernel_variant.restype = ctypes.c_int
+    L.rlbm_step_kernel_variant.argtypes = [_vp]
+    L.rlbm_set_wait_limit.restype = st
+    L.rlbm_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
+    L.rlbm_test_stall_next_step.restype = st
+    L.rlbm_test_stall_next_step.argtypes = [_vp]
     _lib = L
     return L
 
@@ -100,7 +114,7 @@ def _check(status: int, handle=None):
     if status == OK:
         return
     msg = lib().rlbm_last_error(handle).decode(errors="replace")
-    cls = Unphysical if status == ERR_UNPHYSICAL else RLBMError
+    cls = {ERR_UNPHYSICAL: Unphysical, ERR_TIMEOUT: DeviceTimeout}.get(status, RLBMError)
     raise cls(status, msg)
 
 
@@ -211,8 +225,8 @@ class Simulation:
 
     def get_populations(self) -> np.ndarray:
         """Raw stored populations, shape (npop, ny, nx), storage dtype."""
-        dt = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16}[
-            self.precision]
+        dt = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16,
+              "fp16n": np.float16, "bf16n": np.uint16}[self.precision]
         out = np.empty((self.npop, self.ny, self.nx), dtype=dt)
         _check(lib().rlbm_get_populations(self._h, _vp(out.ctypes.data), out.nbytes), self._h)
         return out
@@ -236,13 +250,26 @@ class Simulation:
     def current_buffer_ptr(self) -> int:
         return lib().rlbm_current_buffer(self._h)
 
+    @property
+    def uses_tma(self) -> bool:
+        """True when steps run the persistent TMA-staged kernel."""
+        return lib().rlbm_step_kernel_variant(self._h) == 1
+
+    def set_wait_limit(self, cycles: int):
+        _check(lib().rlbm_set_wait_limit(self._h, int(cycles)), self._h)
+
+    def test_stall_next_step(self):
+        _check(lib().rlbm_test_stall_next_step(self._h), self._h)
+
 
 def decode_populations(raw: np.ndarray, precision: str, w: np.ndarray) -> np.ndarray:
-    """Stored values -> f_i: identity for fp64/fp32; f = w (h + 1/(2 pi)) for 16-bit storage."""
+    """Stored values -> f_i: identity for fp64/fp32; f = f^rest (s + beta) for
+    16-bit storage, f^rest_i = w_i / (2 pi), beta = 1 (deviation) or 0 (normalised)."""
     if precision in ("fp64", "fp32"):
         return raw.astype(np.float64)
-    if precision == "fp16":
-        h = raw.astype(np.float64)
+    if precision.startswith("fp16"):
+        s = raw.astype(np.float64)
     else:
-        h = (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
-    return w[:, None, None] * (h + 1.0 / (2.0 * math.pi))
+        s = (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    beta = 0.0 if precision.endswith("n") else 1.0
+    return (w / (2.0 * math.pi))[:, None, None] * (s + beta)
