@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shock1d_8192x4_N3K64", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16", "bf16", "fp16n", "bf16n"])
     ap.add_argument("--timesteps", type=int, default=None,
                     help="override time steps per problem (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -247,6 +247,13 @@ def main():
                          stream=stream) for kn in kn_list]
     out = torch.empty((6, w.ny, w.nx), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    # tiling chosen by the library's autotuner (cached per problem shape)
+    with torch.cuda.stream(stream):
+        for sim in sims:
+            sim.init_device(*d_fields)
+            sim.autotune(8)
+    tiling = {"populations_per_warp": sims[0].tile_populations,
+              "kernel": "persistent TMA-staged" if sims[0].uses_tma else "per-tile"}
 
     def one_step():
         for sim in sims:
@@ -329,7 +336,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32",
-                      "bf16": "bf16-storage/f32"}[precision],
+                      "bf16": "bf16-storage/f32", "fp16n": "f16-storage/f32",
+                      "bf16n": "bf16-storage/f32"}[precision],
             "data": "synthetic",
             "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
                        "npop": w.npop, "kn": kn_list, "time_steps_per_problem": steps_pp,
@@ -338,11 +346,12 @@ def main():
                        "l2": f"flushed between timed steps (256 MB write); working set "
                              f"{working_set / 1e6:.0f} MB {'fits' if working_set < 129e6 else 'exceeds'} "
                              f"the 129 MB L2 within a step",
-                       "parallelism": f"replicas x{world} (independent problems)"},
+                       "parallelism": f"replicas x{world} (independent problems)",
+                       "tiling": tiling},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": profiled_traffic(w.name, precision),
-                         "kernel": "rlbmk::rlbm_kernel<MODE_STEP>",
+                         "kernel": "rlbm_step_tma" if sims[0].uses_tma else "rlbm_kernel<MODE_STEP>",
                          "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes},
             "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": METRIC,

@@ -156,6 +156,21 @@ long long rlbm_kernel_launches(const rlbm_t *h);
  * (row pitch a multiple of 16 bytes and nx >= one box), 0 = per-tile kernel. */
 int rlbm_step_kernel_variant(const rlbm_t *h);
 
+/* Populations per warp of the handle's current tiling (the tile is 32 sites
+ * of one row x all populations; G = ceil(K / P) (N+1) warps per CTA). */
+int rlbm_tile_populations(const rlbm_t *h);
+
+/* Autotuner: time every compiled tiling of the step kernel (P populations per
+ * warp in {8,12,16,24,32,48,64} that fits K and N, each with the persistent
+ * TMA-staged kernel where possible and with the per-tile kernel) on this
+ * handle's own problem, launches_per_trial launches each, and keep the
+ * fastest.  The populations of the current state are not modified (trials
+ * read the current buffer and write the other one).  Results are cached per
+ * (grid, N, K, precision, boundary conditions) for the life of the process.
+ * best_ms (may be NULL) receives the time of one step launch with the chosen
+ * tiling.  Synchronises the stream. */
+rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms);
+
 /* Bound, in SM clock cycles, of every mbarrier wait in the TMA-staged step
  * kernel (default 4e9, about 2 s).  A wait that runs out makes the kernel
  * record RLBM_ERR_TIMEOUT, drain its own copies (bounded) and return; the next
@@ -166,6 +181,69 @@ rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles);
  * than its copies deliver, so its waits run out after the wait limit.
  * RLBM_ERR_UNSUPPORTED when the handle uses the per-tile kernel. */
 rlbm_status rlbm_test_stall_next_step(rlbm_t *h);
+
+/* ------------------------------------------------------------------ */
+/* Batched persistent form: many independent problems, one launch       */
+/* ------------------------------------------------------------------ */
+
+typedef struct rlbm_batch rlbm_batch_t; /* opaque, owned by the library */
+
+/* One problem of a batch: grid, boundary conditions, K angles, tau. */
+typedef struct {
+    int nx, ny;
+    int bc_x, bc_y;
+    int angles_K;
+    double tau;
+} rlbm_problem;
+
+/* Bytes of device memory holding both population buffers of every problem
+ * (each problem's pair starts on a 256-byte boundary). */
+size_t rlbm_batch_arena_bytes(const rlbm_problem *problems, int count, int order_N, int precision);
+
+/* Create a batch of `count` independent problems sharing the order N and the
+ * storage precision (RLBM_FP64 or RLBM_FP32).  Every problem needs a tiling
+ * whose warps per tile divide the 6-warp CTA: N = 2 with K <= 64 (N = 3 has
+ * none: RLBM_ERR_UNSUPPORTED).  dev_arena: caller-owned device memory of
+ * rlbm_batch_arena_bytes() bytes, 256-byte aligned, or NULL (the library
+ * allocates).  The problems are also reachable as single handles through
+ * rlbm_batch_problem() for init, moments and checkpoints. */
+rlbm_status rlbm_batch_create(rlbm_batch_t **out, const rlbm_problem *problems, int count,
+                              int order_N, int precision, void *cuda_stream, void *dev_arena,
+                              size_t arena_bytes);
+void rlbm_batch_destroy(rlbm_batch_t *b);
+const char *rlbm_batch_last_error(const rlbm_batch_t *b);
+int rlbm_batch_count(const rlbm_batch_t *b);
+
+/* Handle of problem i (owned by the batch; do not destroy).  Use rlbm_init,
+ * rlbm_init_device, rlbm_moments, rlbm_get/set_populations on it; do not call
+ * rlbm_step on it while the batch is in use. */
+rlbm_t *rlbm_batch_problem(rlbm_batch_t *b, int i);
+
+/* Advance every problem nsteps time steps (Sec. 2.2, the same fused step as
+ * rlbm_step) with ONE persistent cooperative kernel launch, replayed from a
+ * CUDA graph captured per nsteps.  Work units (tiles of 32 sites of one row
+ * of one problem) are taken dynamically from a counter; time steps are
+ * separated by a grid barrier whose waits are bounded (RLBM_ERR_TIMEOUT at
+ * the next rlbm_batch_sync).  Asynchronous. */
+rlbm_status rlbm_batch_step(rlbm_batch_t *b, int nsteps);
+
+/* Wait for the stream; reports a barrier timeout or a non-physical cell. */
+rlbm_status rlbm_batch_sync(rlbm_batch_t *b);
+long long rlbm_batch_kernel_launches(const rlbm_batch_t *b);
+
+/* Autotuner of the batched tile shapes: for each class of problems with the
+ * same K, time the batched kernel with one and with two warps per energy
+ * shell (P populations per warp, 1 or 2 tiles per CTA), steps_per_trial
+ * steps each, and keep the faster.  It initialises every problem with a
+ * uniform rest state first, so call it before rlbm_init.  best_ms (may be
+ * NULL): time of one batched step with the chosen shapes. */
+rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *best_ms);
+
+/* Bound of each grid-barrier wait in SM cycles (default 4e9) and a test hook
+ * making the next rlbm_batch_step's barrier wait for one CTA too many, so
+ * that every wait runs out and RLBM_ERR_TIMEOUT is reported. */
+rlbm_status rlbm_batch_set_wait_limit(rlbm_batch_t *b, long long cycles);
+rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b);
 
 #ifdef __cplusplus
 }

@@ -91,4 +91,30 @@ cudaError_t launch_f16(int mode, int N, int P, bool two_d, dim3 grid, dim3 block
 cudaError_t launch_bf16(int mode, int N, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
                         cudaStream_t st, const KernelArgs &a);
 
+// Batched persistent form (rlbm_batch.cuh).
+constexpr int kBatchWarps = 6;
+
+struct BatchUnit {
+    int prob;  // problem index
+    int tile0; // first tile (row-major: y * ntiles_x + xt)
+};
+
+struct BatchArgs {
+    const KernelArgs *probs; // per problem: fin = buffer 0, fout = buffer 1
+    const int *ntiles_x;     // per problem
+    const int *ntiles;       // per problem
+    const int *tiles_per_unit;
+    const BatchUnit *units;
+    int nunits;
+    int nsteps;
+    const int *parity0;      // per problem: buffer holding the current state (0 / 1)
+    unsigned *sync;          // [0] arrivals, [1] generation, [2], [3] work counters (by step parity)
+    int *status;             // bit 1: a barrier wait ran out
+    long long wait_cycles;
+    unsigned barrier_extra;  // test hook: arrivals the barrier waits for beyond the grid (0)
+};
+
+cudaError_t launch_batch(int prec, int N, const BatchArgs &b, int grid, cudaStream_t st,
+                         int *blocks_per_sm);
+
 } // namespace rlbmk

@@ -36,11 +36,13 @@ template <class St, class R> struct Io;
 template <> struct Io<double, double> {
     static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
     static __device__ __forceinline__ double lds(const double *p) { return *p; }
+    static __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <> struct Io<float, float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float lds(const float *p) { return *p; }
+    static __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Io<__half, float> {
@@ -49,6 +51,10 @@ template <> struct Io<__half, float> {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
     static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ float ldcg(const __half *p)
+    {
+        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Io<__nv_bfloat16, float> {
@@ -58,6 +64,11 @@ template <> struct Io<__nv_bfloat16, float> {
             __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
     static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float ldcg(const __nv_bfloat16 *p)
+    {
+        return __bfloat162float(
+            __ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v)
     {
         *p = __float2bfloat16_rn(v);

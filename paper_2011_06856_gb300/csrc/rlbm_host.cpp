@@ -15,6 +15,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -205,6 +207,7 @@ struct rlbm {
     size_t tma_smem = 0;
     int sm_count = 0;
     bool stall_next = false; // test hook: next launch waits for bytes that never arrive
+    bool no_tma = false;     // tiling choice: per-tile kernel even where TMA is possible
     std::string err;
 };
 
@@ -368,10 +371,17 @@ rlbm_status build_tables(rlbm_t *h)
     else { put<float>(blob, o_shell, shell); put<float>(blob, o_rt, rt); }
     std::memcpy(blob.data() + o_mask, masks.data(), masks.size() * sizeof(unsigned long long));
 
+    if (h->d_tabs) { // re-tiling: replace the tables
+        RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_tabs);
+        h->d_tabs = nullptr;
+    }
     RLBM_CUDA(h, cudaMalloc(&h->d_tabs, total));
-    RLBM_CUDA(h, cudaMalloc(&h->d_status, 4 * sizeof(int))); // status, launch counter, CTAs done
+    if (!h->d_status) {
+        RLBM_CUDA(h, cudaMalloc(&h->d_status, 4 * sizeof(int))); // status, launch counter, CTAs done
+        RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, 4 * sizeof(int), h->stream));
+    }
     RLBM_CUDA(h, cudaMemcpyAsync(h->d_tabs, blob.data(), total, cudaMemcpyHostToDevice, h->stream));
-    RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, 4 * sizeof(int), h->stream));
     RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
 
     rlbmk::KernelArgs &a = h->base;
@@ -480,8 +490,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // per-tile kernel is used.
 rlbm_status setup_tma(rlbm_t *h)
 {
+    h->use_tma = false;
+    delete[] h->tma;
+    h->tma = nullptr;
     const char *off = std::getenv("RLBM_NO_TMA");
-    if (off && off[0] == '1') return RLBM_OK;
+    if ((off && off[0] == '1') || h->no_tma) return RLBM_OK;
     const size_t es = storage_size(h->prec);
     const int HX = int(16 / es), BW = 32 + 2 * HX;
     const int nx = h->grid.nx, ny = h->grid.ny, npop = h->npop;
@@ -595,6 +608,37 @@ rlbm_status validate_fields_ptrs(rlbm_t *h, const void *a, const void *b, const 
     if (!a || !b || !c || !d) return fail(h, RLBM_ERR_ARG, "NULL field pointer");
     return RLBM_OK;
 }
+
+// Switch the handle to another tiling (P populations per warp, TMA or not).
+rlbm_status retile(rlbm_t *h, int P, bool tma)
+{
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto &g : h->graph)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    h->P = P;
+    h->Gs = (h->K + P - 1) / P;
+    h->G = h->Gs * (h->N + 1);
+    h->no_tma = !tma;
+    rlbm_status st = build_tables(h);
+    if (st) return st;
+    return setup_tma(h);
+}
+
+struct TuneKey {
+    int nx, ny, N, K, prec, bcx, bcy, site64;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::memcmp(this, &o, sizeof(TuneKey)) < 0;
+    }
+};
+struct TuneChoice { int P; bool tma; float ms; };
+
+std::map<TuneKey, TuneChoice> &tune_cache()
+{
+    static std::map<TuneKey, TuneChoice> m;
+    return m;
+}
+std::mutex g_tune_mutex;
 
 } // namespace
 
@@ -873,6 +917,68 @@ long long rlbm_kernel_launches(const rlbm_t *h) { return h ? h->launches : -1; }
 
 int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? (h->use_tma ? 1 : 0) : -1; }
 
+int rlbm_tile_populations(const rlbm_t *h) { return h ? h->P : -1; }
+
+rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (launches_per_trial < 1) return fail(h, RLBM_ERR_ARG, "launches_per_trial must be >= 1");
+    const TuneKey key{h->grid.nx, h->grid.ny, h->N, h->K, h->prec, h->grid.bc_x, h->grid.bc_y,
+                      h->site_fp64 ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            if (best_ms) *best_ms = it->second.ms;
+            if (it->second.P == h->P && it->second.tma == h->use_tma) return RLBM_OK;
+            return retile(h, it->second.P, it->second.tma);
+        }
+    }
+    static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
+    cudaEvent_t e0, e1;
+    RLBM_CUDA(h, cudaEventCreate(&e0));
+    RLBM_CUDA(h, cudaEventCreate(&e1));
+    TuneChoice best{h->P, h->use_tma, 1e30f};
+    const long long launches0 = h->launches;
+    rlbm_status st = RLBM_OK;
+    for (int P : sizes) {
+        const int gs = (h->K + P - 1) / P;
+        if (gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K) continue;
+        if (P > 2 * h->K) continue;
+        for (int tma = 1; tma >= 0 && st == RLBM_OK; --tma) {
+            st = retile(h, P, tma != 0);
+            if (st) break;
+            if (tma && !h->use_tma) continue; // TMA not possible for this tiling
+            // time cur -> other launches (the state in buffer cur is not modified)
+            cudaError_t e = launch_step(h, h->cur);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < launches_per_trial && e == cudaSuccess; ++k) e = launch_step(h, h->cur);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) { st = cuda_fail(h, e, "autotune trial"); break; }
+            ms /= launches_per_trial;
+            if (ms < best.ms) best = TuneChoice{P, h->use_tma, ms};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->launches = launches0; // trial launches are not steps
+    if (st) return st;
+    st = retile(h, best.P, best.tma);
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        tune_cache()[key] = best;
+    }
+    if (best_ms) *best_ms = best.ms;
+    // trial launches may flag cells of a state that was never stepped: clear
+    RLBM_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RLBM_OK;
+}
+
 rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles)
 {
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
@@ -887,6 +993,427 @@ rlbm_status rlbm_test_stall_next_step(rlbm_t *h)
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
     if (!h->use_tma) return fail(h, RLBM_ERR_UNSUPPORTED, "the per-tile step kernel has no device waits");
     h->stall_next = true;
+    return RLBM_OK;
+}
+
+} // extern "C"
+
+// ============================================================== batched form
+
+struct rlbm_batch {
+    std::vector<rlbm_t *> probs;
+    int N = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *arena = nullptr;
+    bool own_arena = false;
+    std::vector<size_t> offs;
+    std::vector<int> tpu;       // tiles per unit (per problem)
+    std::vector<int> ntiles_x, ntiles;
+    int nunits = 0, grid = 0;
+    // device arrays
+    rlbmk::KernelArgs *d_args = nullptr;
+    int *d_ints = nullptr;                // ntiles_x | ntiles | tpu | parity
+    rlbmk::BatchUnit *d_units = nullptr;
+    unsigned *d_sync = nullptr;           // 4 words
+    int *d_status = nullptr;
+    long long wait_cycles = 4000000000LL;
+    bool stall_next = false;
+    std::map<int, cudaGraphExec_t> graphs; // by nsteps
+    long long launches = 0, steps = 0;
+    std::string err;
+};
+
+namespace {
+
+rlbm_status bfail(rlbm_batch *b, rlbm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf; else g_create_error = buf;
+    return st;
+}
+
+#define BATCH_CUDA(b, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? RLBM_ERR_OOM : RLBM_ERR_CUDA,        \
+                         "%s: %s", #call, cudaGetErrorString(e_));                               \
+    } while (0)
+
+// Tiling of one problem in a 6-warp CTA: G = gs (N+1) warps per tile must divide 6.
+bool batch_tiling(int N, int K, int gs, int &P)
+{
+    static const int sizes[] = {8, 12, 16, 24, 32};
+    if (rlbmk::kBatchWarps % (gs * (N + 1)) != 0) return false;
+    const int need = (K + gs - 1) / gs;
+    for (int s : sizes)
+        if (s >= need) {
+            if ((gs - 1) * s >= K) return false;
+            P = s;
+            return true;
+        }
+    return false;
+}
+
+rlbm_status batch_build_units(rlbm_batch *b)
+{
+    const int n = int(b->probs.size());
+    b->tpu.assign(n, 1);
+    b->ntiles_x.assign(n, 0);
+    b->ntiles.assign(n, 0);
+    std::vector<rlbmk::KernelArgs> args(n);
+    std::vector<std::pair<double, int>> order;
+    for (int i = 0; i < n; ++i) {
+        rlbm_t *h = b->probs[i];
+        b->tpu[i] = rlbmk::kBatchWarps / h->G;
+        b->ntiles_x[i] = (h->grid.nx + 31) / 32;
+        b->ntiles[i] = b->ntiles_x[i] * h->grid.ny;
+        args[i] = h->base;
+        args[i].fin = buffer(h, 0);
+        args[i].fout = buffer(h, 1);
+        order.push_back({-double(h->npop) * h->grid.nx * h->grid.ny, i}); // largest first
+    }
+    std::sort(order.begin(), order.end());
+    std::vector<rlbmk::BatchUnit> units;
+    for (auto &o : order) {
+        const int i = o.second;
+        for (int t = 0; t < b->ntiles[i]; t += b->tpu[i]) units.push_back({i, t});
+    }
+    b->nunits = int(units.size());
+    if (b->d_units) { cudaFree(b->d_units); b->d_units = nullptr; }
+    BATCH_CUDA(b, cudaMalloc(&b->d_units, sizeof(rlbmk::BatchUnit) * std::max<size_t>(1, units.size())));
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_units, units.data(), sizeof(rlbmk::BatchUnit) * units.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_args, args.data(), sizeof(rlbmk::KernelArgs) * n,
+                                  cudaMemcpyHostToDevice, b->stream));
+    std::vector<int> ints(4 * size_t(n));
+    for (int i = 0; i < n; ++i) {
+        ints[i] = b->ntiles_x[i];
+        ints[n + i] = b->ntiles[i];
+        ints[2 * n + i] = b->tpu[i];
+        ints[3 * n + i] = b->probs[i]->cur;
+    }
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_ints, ints.data(), sizeof(int) * ints.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    return RLBM_OK;
+}
+
+rlbmk::BatchArgs batch_args(rlbm_batch *b, int nsteps)
+{
+    const int n = int(b->probs.size());
+    rlbmk::BatchArgs a{};
+    a.probs = b->d_args;
+    a.ntiles_x = b->d_ints;
+    a.ntiles = b->d_ints + n;
+    a.tiles_per_unit = b->d_ints + 2 * n;
+    a.parity0 = b->d_ints + 3 * n;
+    a.units = b->d_units;
+    a.nunits = b->nunits;
+    a.nsteps = nsteps;
+    a.sync = b->d_sync;
+    a.status = b->d_status;
+    a.wait_cycles = b->wait_cycles;
+    a.barrier_extra = 0;
+    return a;
+}
+
+rlbm_status batch_launch(rlbm_batch *b, int nsteps, bool use_graph)
+{
+    const bool stall = b->stall_next;
+    b->stall_next = false;
+    if (use_graph && !stall) {
+        auto it = b->graphs.find(nsteps);
+        if (it == b->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            BATCH_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaMemsetAsync(b->d_sync, 0, 4 * sizeof(unsigned), b->stream);
+            if (e == cudaSuccess)
+                e = rlbmk::launch_batch(b->prec, b->N, batch_args(b, nsteps), b->grid, b->stream, nullptr);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); BATCH_CUDA(b, e); }
+            BATCH_CUDA(b, e2);
+            cudaGraphExec_t ge = nullptr;
+            cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            BATCH_CUDA(b, e3);
+            it = b->graphs.emplace(nsteps, ge).first;
+        }
+        BATCH_CUDA(b, cudaGraphLaunch(it->second, b->stream));
+    } else {
+        BATCH_CUDA(b, cudaMemsetAsync(b->d_sync, 0, 4 * sizeof(unsigned), b->stream));
+        rlbmk::BatchArgs a = batch_args(b, nsteps);
+        if (stall) a.barrier_extra = 1;
+        BATCH_CUDA(b, rlbmk::launch_batch(b->prec, b->N, a, b->grid, b->stream, nullptr));
+    }
+    ++b->launches;
+    return RLBM_OK;
+}
+
+rlbm_status batch_check(rlbm_batch *b)
+{
+    int st = 0;
+    BATCH_CUDA(b, cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (st) {
+        BATCH_CUDA(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+        BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+        return bfail(b, RLBM_ERR_TIMEOUT, "a grid-barrier wait in the batched kernel ran out");
+    }
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        rlbm_status s2 = check_status(b->probs[i]);
+        if (s2) return bfail(b, s2, "problem %zu: %s", i, b->probs[i]->err.c_str());
+    }
+    return RLBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+size_t rlbm_batch_arena_bytes(const rlbm_problem *p, int count, int order_N, int precision)
+{
+    if (!p || count < 1) return 0;
+    size_t tot = 0;
+    for (int i = 0; i < count; ++i) {
+        const rlbm_grid g{p[i].nx, p[i].ny, p[i].bc_x, p[i].bc_y};
+        tot += align256(2 * rlbm_population_bytes(g, order_N, p[i].angles_K, precision));
+    }
+    return tot;
+}
+
+rlbm_status rlbm_batch_create(rlbm_batch_t **out, const rlbm_problem *p, int count, int order_N,
+                              int precision, void *cuda_stream, void *dev_arena, size_t arena_bytes)
+{
+    if (!out) return bfail(nullptr, RLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || count < 1) return bfail(nullptr, RLBM_ERR_ARG, "need at least one problem");
+    if (precision != RLBM_FP64 && precision != RLBM_FP32)
+        return bfail(nullptr, RLBM_ERR_UNSUPPORTED, "the batched kernel is built for FP64 and FP32 storage");
+    if (order_N != 2 && order_N != 3)
+        return bfail(nullptr, RLBM_ERR_UNSUPPORTED, "the batched kernel is built for N = 2, 3");
+    for (int i = 0; i < count; ++i) {
+        int P;
+        if (!batch_tiling(order_N, p[i].angles_K, 1, P) && !batch_tiling(order_N, p[i].angles_K, 2, P))
+            return bfail(nullptr, RLBM_ERR_UNSUPPORTED,
+                         "problem %d: K=%d has no batched tiling (6 warps per CTA; N=2: K <= 64, N=3: none)",
+                         i, p[i].angles_K);
+        if (p[i].nx < 1 || p[i].ny < 1 || !(p[i].tau > 0.0) || p[i].angles_K < 2 * order_N + 1 ||
+            p[i].bc_x < 0 || p[i].bc_x > 1 || p[i].bc_y < 0 || p[i].bc_y > 1)
+            return bfail(nullptr, RLBM_ERR_ARG, "problem %d: invalid grid, K, tau or boundary condition", i);
+    }
+    const size_t need = rlbm_batch_arena_bytes(p, count, order_N, precision);
+    if (dev_arena && (arena_bytes < need || ((uintptr_t)dev_arena) % 256))
+        return bfail(nullptr, RLBM_ERR_ARG, "dev_arena must be 256-byte aligned and hold %zu bytes", need);
+    rlbm_batch *b = new (std::nothrow) rlbm_batch();
+    if (!b) return bfail(nullptr, RLBM_ERR_OOM, "host allocation failed");
+    b->N = order_N;
+    b->prec = precision;
+    rlbm_status st = RLBM_OK;
+    auto bail = [&](rlbm_status s) {
+        g_create_error = b->err;
+        rlbm_batch_destroy(b);
+        return s;
+    };
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(bfail(b, RLBM_ERR_CUDA, "cudaStreamCreate failed"));
+        b->own_stream = true;
+    }
+    if (dev_arena) {
+        b->arena = dev_arena;
+    } else {
+        if (cudaMalloc(&b->arena, need) != cudaSuccess)
+            return bail(bfail(b, RLBM_ERR_OOM, "cudaMalloc of a %zu-byte arena failed", need));
+        b->own_arena = true;
+    }
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        const rlbm_grid g{p[i].nx, p[i].ny, p[i].bc_x, p[i].bc_y};
+        const size_t bytes = 2 * rlbm_population_bytes(g, order_N, p[i].angles_K, precision);
+        rlbm_t *h = nullptr;
+        st = rlbm_create(&h, g, order_N, p[i].angles_K, p[i].tau, precision, b->stream,
+                         (unsigned char *)b->arena + off, bytes);
+        if (st) return bail(bfail(b, st, "problem %d: %s", i, g_create_error.c_str()));
+        b->probs.push_back(h);
+        b->offs.push_back(off);
+        int P = 0;
+        const int gs = batch_tiling(order_N, p[i].angles_K, 1, P) ? 1 : 2;
+        batch_tiling(order_N, p[i].angles_K, gs, P);
+        h->no_tma = true;
+        st = retile(h, P, false);
+        if (st) return bail(bfail(b, st, "problem %d: %s", i, h->err.c_str()));
+        off += align256(bytes);
+    }
+    const int n = count;
+    if (cudaMalloc(&b->d_args, sizeof(rlbmk::KernelArgs) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_ints, sizeof(int) * 4 * n) != cudaSuccess ||
+        cudaMalloc(&b->d_sync, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess)
+        return bail(bfail(b, RLBM_ERR_OOM, "device allocation of batch tables failed"));
+    if (cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess)
+        return bail(bfail(b, RLBM_ERR_CUDA, "cudaMemsetAsync failed"));
+    st = batch_build_units(b);
+    if (st) return bail(st);
+    int bps = 0, dev = 0, sms = 0;
+    if (rlbmk::launch_batch(precision, order_N, batch_args(b, 0), 0, b->stream, &bps) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || bps < 1)
+        return bail(bfail(b, RLBM_ERR_CUDA, "occupancy query of the batched kernel failed"));
+    b->grid = bps * sms;
+    *out = b;
+    return RLBM_OK;
+}
+
+void rlbm_batch_destroy(rlbm_batch_t *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    for (rlbm_t *h : b->probs) rlbm_destroy(h);
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->d_ints) cudaFree(b->d_ints);
+    if (b->d_units) cudaFree(b->d_units);
+    if (b->d_sync) cudaFree(b->d_sync);
+    if (b->d_status) cudaFree(b->d_status);
+    if (b->own_arena && b->arena) cudaFree(b->arena);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char *rlbm_batch_last_error(const rlbm_batch_t *b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int rlbm_batch_count(const rlbm_batch_t *b) { return b ? int(b->probs.size()) : -1; }
+
+rlbm_t *rlbm_batch_problem(rlbm_batch_t *b, int i)
+{
+    if (!b || i < 0 || i >= int(b->probs.size())) return nullptr;
+    return b->probs[i];
+}
+
+rlbm_status rlbm_batch_step(rlbm_batch_t *b, int nsteps)
+{
+    if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    if (nsteps < 0) return bfail(b, RLBM_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return RLBM_OK;
+    // current buffer parity of every problem (problems can be re-initialised one by one)
+    const int n = int(b->probs.size());
+    std::vector<int> par(n);
+    for (int i = 0; i < n; ++i) par[i] = b->probs[i]->cur;
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_ints + 3 * n, par.data(), sizeof(int) * n,
+                                  cudaMemcpyHostToDevice, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream)); // par is a stack buffer
+    rlbm_status st = batch_launch(b, nsteps, true);
+    if (st) return st;
+    for (rlbm_t *h : b->probs) {
+        h->cur = (h->cur + nsteps) & 1;
+        h->steps += nsteps;
+    }
+    b->steps += nsteps;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_sync(rlbm_batch_t *b)
+{
+    if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    return batch_check(b);
+}
+
+long long rlbm_batch_kernel_launches(const rlbm_batch_t *b) { return b ? b->launches : -1; }
+
+rlbm_status rlbm_batch_set_wait_limit(rlbm_batch_t *b, long long cycles)
+{
+    if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    if (cycles < 1000) return bfail(b, RLBM_ERR_ARG, "wait limit must be >= 1000 cycles");
+    b->wait_cycles = cycles;
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b)
+{
+    if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    b->stall_next = true;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *best_ms)
+{
+    if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    if (steps_per_trial < 1) return bfail(b, RLBM_ERR_ARG, "steps_per_trial must be >= 1");
+    const int n = int(b->probs.size());
+    // a uniform rest state (n = 1, T = 1) in every problem: realistic timing, no NaNs
+    for (int i = 0; i < n; ++i) {
+        rlbm_t *h = b->probs[i];
+        const size_t S = size_t(h->grid.nx) * h->grid.ny;
+        std::vector<double> one(S, 1.0), zero(S, 0.0);
+        rlbm_status st = rlbm_init(h, one.data(), one.data(), zero.data(), zero.data());
+        if (st) return bfail(b, st, "problem %d: %s", i, h->err.c_str());
+    }
+    cudaEvent_t e0, e1;
+    BATCH_CUDA(b, cudaEventCreate(&e0));
+    BATCH_CUDA(b, cudaEventCreate(&e1));
+    auto trial = [&](float &ms) -> rlbm_status {
+        rlbm_status st = batch_build_units(b);
+        if (st) return st;
+        BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+        st = batch_launch(b, steps_per_trial, false);
+        if (st) return st;
+        BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+        BATCH_CUDA(b, cudaEventSynchronize(e1));
+        BATCH_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+        return RLBM_OK;
+    };
+    // greedy over classes of K: warps per tile gs (N+1) in {N+1, 2 (N+1)}
+    std::map<int, std::vector<int>> classes;
+    for (int i = 0; i < n; ++i) classes[b->probs[i]->K].push_back(i);
+    float best = 0.f;
+    rlbm_status st = trial(best);
+    for (auto &c : classes) {
+        if (st) break;
+        const int K = c.first;
+        const int cur_gs = b->probs[c.second[0]]->Gs;
+        int best_gs = cur_gs;
+        for (int gs = 1; gs <= 2 && !st; ++gs) {
+            int P;
+            if (gs == cur_gs || !batch_tiling(b->N, K, gs, P)) continue;
+            for (int i : c.second) {
+                st = retile(b->probs[i], P, false);
+                if (st) break;
+            }
+            float ms = 0.f;
+            if (!st) st = trial(ms);
+            if (!st && ms < best) { best = ms; best_gs = gs; }
+        }
+        if (!st && best_gs != b->probs[c.second[0]]->Gs) {
+            int P;
+            batch_tiling(b->N, K, best_gs, P);
+            for (int i : c.second)
+                if (!st) st = retile(b->probs[i], P, false);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!st) st = batch_build_units(b);
+    if (st) return st;
+    b->launches = 0;
+    if (best_ms) *best_ms = best / steps_per_trial;
+    BATCH_CUDA(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+    for (rlbm_t *h : b->probs) {
+        BATCH_CUDA(b, cudaMemsetAsync(h->d_status, 0, sizeof(int), b->stream));
+        h->steps = 0;
+    }
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
     return RLBM_OK;
 }
 

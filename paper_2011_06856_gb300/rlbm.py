@@ -31,6 +31,11 @@ EXPORTS = [
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
     "rlbm_step_kernel_variant", "rlbm_set_wait_limit", "rlbm_test_stall_next_step",
+    "rlbm_tile_populations", "rlbm_autotune",
+    "rlbm_batch_arena_bytes", "rlbm_batch_create", "rlbm_batch_destroy", "rlbm_batch_last_error",
+    "rlbm_batch_count", "rlbm_batch_problem", "rlbm_batch_step", "rlbm_batch_sync",
+    "rlbm_batch_kernel_launches", "rlbm_batch_autotune", "rlbm_batch_set_wait_limit",
+    "rlbm_batch_test_stall_next_step",
 ]
 
 
@@ -46,6 +51,11 @@ class Unphysical(RLBMError):
 
 class DeviceTimeout(RLBMError):
     pass
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc_x", ctypes.c_int),
+                ("bc_y", ctypes.c_int), ("angles_K", ctypes.c_int), ("tau", ctypes.c_double)]
 
 
 class Grid(ctypes.Structure):
@@ -106,6 +116,36 @@ def lib(path: str = LIB_PATH):
     L.rlbm_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
     L.rlbm_test_stall_next_step.restype = st
     L.rlbm_test_stall_next_step.argtypes = [_vp]
+    L.rlbm_tile_populations.restype = ctypes.c_int
+    L.rlbm_tile_populations.argtypes = [_vp]
+    L.rlbm_autotune.restype = st
+    L.rlbm_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+    _pp = ctypes.POINTER(Problem)
+    L.rlbm_batch_arena_bytes.restype = ctypes.c_size_t
+    L.rlbm_batch_arena_bytes.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.rlbm_batch_create.restype = st
+    L.rlbm_batch_create.argtypes = [ctypes.POINTER(_vp), _pp, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, _vp, _vp, ctypes.c_size_t]
+    L.rlbm_batch_destroy.restype = None
+    L.rlbm_batch_destroy.argtypes = [_vp]
+    L.rlbm_batch_last_error.restype = ctypes.c_char_p
+    L.rlbm_batch_last_error.argtypes = [_vp]
+    L.rlbm_batch_count.restype = ctypes.c_int
+    L.rlbm_batch_count.argtypes = [_vp]
+    L.rlbm_batch_problem.restype = _vp
+    L.rlbm_batch_problem.argtypes = [_vp, ctypes.c_int]
+    L.rlbm_batch_step.restype = st
+    L.rlbm_batch_step.argtypes = [_vp, ctypes.c_int]
+    L.rlbm_batch_sync.restype = st
+    L.rlbm_batch_sync.argtypes = [_vp]
+    L.rlbm_batch_kernel_launches.restype = ctypes.c_longlong
+    L.rlbm_batch_kernel_launches.argtypes = [_vp]
+    L.rlbm_batch_autotune.restype = st
+    L.rlbm_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+    L.rlbm_batch_set_wait_limit.restype = st
+    L.rlbm_batch_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
+    L.rlbm_batch_test_stall_next_step.restype = st
+    L.rlbm_batch_test_stall_next_step.argtypes = [_vp]
     _lib = L
     return L
 
@@ -255,6 +295,17 @@ class Simulation:
         """True when steps run the persistent TMA-staged kernel."""
         return lib().rlbm_step_kernel_variant(self._h) == 1
 
+    @property
+    def tile_populations(self) -> int:
+        return lib().rlbm_tile_populations(self._h)
+
+    def autotune(self, launches_per_trial: int = 8) -> float:
+        """Pick the fastest compiled tiling for this problem (see rlbm_autotune);
+        returns the time of one step launch in ms.  Call after init."""
+        ms = ctypes.c_float(0.0)
+        _check(lib().rlbm_autotune(self._h, int(launches_per_trial), ctypes.byref(ms)), self._h)
+        return ms.value
+
     def set_wait_limit(self, cycles: int):
         _check(lib().rlbm_set_wait_limit(self._h, int(cycles)), self._h)
 
@@ -273,3 +324,112 @@ def decode_populations(raw: np.ndarray, precision: str, w: np.ndarray) -> np.nda
         s = (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     beta = 0.0 if precision.endswith("n") else 1.0
     return (w / (2.0 * math.pi))[:, None, None] * (s + beta)
+
+
+def _bcheck(status: int, b=None):
+    if status == OK:
+        return
+    msg = lib().rlbm_batch_last_error(b).decode(errors="replace")
+    cls = {ERR_UNPHYSICAL: Unphysical, ERR_TIMEOUT: DeviceTimeout}.get(status, RLBMError)
+    raise cls(status, msg)
+
+
+def problems_array(problems):
+    """ctypes array of Problem from (nx, ny, bc_x, bc_y, K, tau) tuples or Problem objects."""
+    arr = (Problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = p if isinstance(p, Problem) else Problem(*p)
+    return arr
+
+
+def batch_arena_bytes(problems, N: int, precision: str = "fp32") -> int:
+    arr = problems_array(problems)
+    return lib().rlbm_batch_arena_bytes(arr, len(problems), N, PRECISIONS[precision])
+
+
+class _View(Simulation):
+    """A problem of a batch: the Simulation API on a handle the batch owns."""
+
+    def __init__(self, handle, nx, ny, N, K, tau, precision, stream):
+        self._h = handle
+        self.nx, self.ny, self.N, self.K = nx, ny, N, K
+        self.npop = K * (N + 1)
+        self.precision = precision
+        self.tau = tau
+        self.stream = stream
+        self._buf = None
+
+    def close(self):
+        self._h = None  # owned by the batch
+
+    def step(self, nsteps: int = 1):
+        raise RuntimeError("step a batch with Batch.step")
+
+
+class Batch:
+    """Many independent problems (N shared) advanced by one persistent launch."""
+
+    def __init__(self, problems, N: int = 2, precision: str = "fp32", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("librlbm needs a CUDA GPU")
+        self.N = int(N)
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = problems_array(problems)
+        self.specs = [(p.nx, p.ny, p.bc_x, p.bc_y, p.angles_K, p.tau) for p in arr]
+        nbytes = lib().rlbm_batch_arena_bytes(arr, len(arr), self.N, PRECISIONS[precision])
+        self._arena = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+        h = _vp()
+        _bcheck(lib().rlbm_batch_create(ctypes.byref(h), arr, len(arr), self.N,
+                                        PRECISIONS[precision], _vp(self.stream.cuda_stream),
+                                        _vp(self._arena.data_ptr()), nbytes))
+        self._b = h
+        self.problems = []
+        for i, (nx, ny, bcx, bcy, K, tau) in enumerate(self.specs):
+            ph = lib().rlbm_batch_problem(self._b, i)
+            self.problems.append(_View(_vp(ph), nx, ny, self.N, K, tau, precision, self.stream))
+
+    def __len__(self):
+        return len(self.problems)
+
+    def __getitem__(self, i) -> Simulation:
+        return self.problems[i]
+
+    def step(self, nsteps: int = 1):
+        _bcheck(lib().rlbm_batch_step(self._b, int(nsteps)), self._b)
+
+    def sync(self):
+        _bcheck(lib().rlbm_batch_sync(self._b), self._b)
+
+    def autotune(self, steps_per_trial: int = 4) -> float:
+        ms = ctypes.c_float(0.0)
+        _bcheck(lib().rlbm_batch_autotune(self._b, int(steps_per_trial), ctypes.byref(ms)), self._b)
+        return ms.value
+
+    def set_wait_limit(self, cycles: int):
+        _bcheck(lib().rlbm_batch_set_wait_limit(self._b, int(cycles)), self._b)
+
+    def test_stall_next_step(self):
+        _bcheck(lib().rlbm_batch_test_stall_next_step(self._b), self._b)
+
+    @property
+    def kernel_launches(self) -> int:
+        return lib().rlbm_batch_kernel_launches(self._b)
+
+    @property
+    def population_updates_per_step(self) -> int:
+        return sum(nx * ny * K * (self.N + 1) for (nx, ny, _, _, K, _) in self.specs)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for p in self.problems:
+                p.close()
+            lib().rlbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

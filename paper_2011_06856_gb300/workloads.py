@@ -149,7 +149,7 @@ WORKLOADS = {
                                      (0.01, 0.1, 1.0, 10.0), 4000, "fp32"),
     # 2D Riemann problem 2048^2, 3 radial x 48 angles, Kn 0.05, 2000 steps, 16-bit storage
     "riemann2d_2048_N2K48": Workload("riemann2d_2048_N2K48", 2048, 2048, 2, 48, (0.05,), 2000,
-                                     "fp16", BC_COPYOUT, BC_COPYOUT,
+                                     "fp16n", BC_COPYOUT, BC_COPYOUT,
                                      {"states": [(1.0, 1.0, 0.0, 0.0), (0.5, 0.8, 0.0, 0.0),
                                                  (0.25, 0.6, 0.0, 0.0), (0.5, 0.8, 0.0, 0.0)],
                                       "jitter": 0.01}),

@@ -111,3 +111,19 @@ def test_binding_fails_loudly_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         R.Simulation(8, 1, 2, 16, 1.0)
+
+
+def test_batch_arena_and_validation(lib):
+    probs = [(100, 1, 1, 0, 16, 4.0), (64, 3, 1, 1, 48, 2.0)]
+    arr = R.problems_array(probs)
+    want = sum((2 * K * 3 * nx * ny * 4 + 255) // 256 * 256 for (nx, ny, _, _, K, _) in probs)
+    assert lib.rlbm_batch_arena_bytes(arr, 2, 2, 1) == want
+    h = R._vp()
+    # N = 3 has no 6-warp batched tiling; K > 64 neither; bad tau is an argument error
+    assert lib.rlbm_batch_create(R.ctypes.byref(h), arr, 2, 3, 1, None, None, 0) == R.ERR_UNSUPPORTED
+    bad = R.problems_array([(100, 1, 1, 0, 96, 4.0)])
+    assert lib.rlbm_batch_create(R.ctypes.byref(h), bad, 1, 2, 1, None, None, 0) == R.ERR_UNSUPPORTED
+    bad = R.problems_array([(100, 1, 1, 0, 16, -1.0)])
+    assert lib.rlbm_batch_create(R.ctypes.byref(h), bad, 1, 2, 1, None, None, 0) == R.ERR_ARG
+    assert lib.rlbm_batch_create(R.ctypes.byref(h), arr, 2, 2, 2, None, None, 0) == R.ERR_UNSUPPORTED
+    assert not h.value

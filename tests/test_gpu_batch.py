@@ -1,0 +1,93 @@
+"""Batched persistent form: every problem of a mixed batch stepped by one
+persistent launch equals the FP64 oracle run of that problem alone."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_2011_06856_gb300 import build as B  # noqa: E402
+from paper_2011_06856_gb300 import rlbm as R  # noqa: E402
+from paper_2011_06856_gb300 import workloads as W  # noqa: E402
+
+B.build()
+
+MIXED = [  # nx, ny, bc_x, bc_y, K, tau
+    (100, 1, 1, 0, 16, 4.0), (70, 3, 1, 1, 48, 2.5), (33, 1, 0, 0, 64, math.inf),
+    (64, 5, 1, 0, 32, 1.5), (130, 2, 0, 1, 24, 3.0), (40, 1, 1, 0, 48, 6.0),
+    (96, 4, 0, 0, 16, 2.0), (31, 2, 1, 1, 64, 2.2),
+]
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def run_oracle(spec, fl, steps):
+    nx, ny, bcx, bcy, K, tau = spec
+    q = O.Quadrature(2, K)
+    f = q.init(fl.n, fl.T, fl.bx, fl.by)
+    return q.run(f, tau, steps, bcx, bcy)[0]
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_mixed_batch_matches_oracle_per_problem(autotune):
+    b = R.Batch(MIXED, N=2, precision="fp64")
+    if autotune:
+        b.autotune(2)
+    fields = [W.random_fields(s[0], s[1], seed=40 + i) for i, s in enumerate(MIXED)]
+    for p, fl in zip(b.problems, fields):
+        p.init_fields(fl)
+    steps = 7
+    b.step(3)
+    b.step(4)  # two launches: the buffer parity carries over
+    b.sync()
+    assert b.kernel_launches >= 2
+    for i, (p, fl) in enumerate(zip(b.problems, fields)):
+        ref = run_oracle(MIXED[i], fl, steps)
+        assert p.steps_done == steps
+        assert relerr(p.get_populations(), ref) < 1e-12, i
+
+
+def test_batch_fp32_matches_oracle():
+    b = R.Batch(MIXED[:4], N=2, precision="fp32")
+    fields = [W.random_fields(s[0], s[1], seed=7 + i) for i, s in enumerate(MIXED[:4])]
+    for p, fl in zip(b.problems, fields):
+        p.init_fields(fl)
+    b.step(20)
+    b.sync()
+    for i, (p, fl) in enumerate(zip(b.problems, fields)):
+        ref = run_oracle(MIXED[i], fl, 20)
+        assert relerr(p.get_populations().astype(np.float64), ref) < 2e-5, i
+
+
+def test_batch_reinit_one_problem_midway():
+    b = R.Batch(MIXED[:3], N=2, precision="fp64")
+    fields = [W.random_fields(s[0], s[1], seed=3 + i) for i, s in enumerate(MIXED[:3])]
+    for p, fl in zip(b.problems, fields):
+        p.init_fields(fl)
+    b.step(5)
+    b.problems[1].init_fields(fields[1])  # back to step 0 on buffer 0 for this one
+    b.step(4)
+    b.sync()
+    assert relerr(b.problems[0].get_populations(), run_oracle(MIXED[0], fields[0], 9)) < 1e-12
+    assert relerr(b.problems[1].get_populations(), run_oracle(MIXED[1], fields[1], 4)) < 1e-12
+
+
+def test_batch_barrier_timeout_is_reported():
+    b = R.Batch(MIXED[:2], N=2, precision="fp32")
+    for i, p in enumerate(b.problems):
+        p.init_fields(W.random_fields(MIXED[i][0], MIXED[i][1], seed=i))
+    b.set_wait_limit(2_000_000)
+    b.test_stall_next_step()
+    b.step(3)  # the barrier waits for one CTA more than the grid: every wait runs out
+    with pytest.raises(R.DeviceTimeout):
+        b.sync()
+    b.step(2)  # the context and the batch still work
+    b.sync()

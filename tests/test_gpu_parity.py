@@ -417,3 +417,25 @@ def test_both_kernels_agree_for_every_storage(precision):
             os.environ.pop("RLBM_NO_TMA", None)
     # same formulas; 16-bit stores may round one unit apart where contraction differs
     assert relerr(out["tma"], out["per_tile"]) < (1e-6 if precision == "fp32" else 2e-3)
+
+
+def test_autotuned_tiling_matches_oracle():
+    """The autotuner may pick any compiled tiling; the result stays at parity
+    and the state it was tuned on is unchanged."""
+    nx, ny, N, K, steps, tau = 128, 6, 2, 48, 7, 2.0
+    fl = W.random_fields(nx, ny, seed=12)
+    sim = R.Simulation(nx, ny, N, K, tau, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    sim.init_fields(fl)
+    f0 = sim.get_populations()
+    ms = sim.autotune(3)
+    assert ms > 0 and sim.tile_populations in (8, 12, 16, 24, 32, 48, 64)
+    np.testing.assert_array_equal(sim.get_populations(), f0)
+    sim.step(steps)
+    q = O.Quadrature(N, K)
+    ref, _ = q.run(f0, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert relerr(sim.get_populations(), ref) < TOL["fp64"]
+    # a second handle of the same problem reuses the cached choice
+    sim2 = R.Simulation(nx, ny, N, K, tau, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    sim2.init_fields(fl)
+    sim2.autotune(3)
+    assert (sim2.tile_populations, sim2.uses_tma) == (sim.tile_populations, sim.uses_tma)
