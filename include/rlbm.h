@@ -245,6 +245,31 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *bes
 rlbm_status rlbm_batch_set_wait_limit(rlbm_batch_t *b, long long cycles);
 rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free single step                                          */
+/* ------------------------------------------------------------------ */
+
+/* One fused time step (the same step as rlbm_step) from d_fin to d_fout,
+ * caller-owned device buffers of N_pop * nx * ny elements each (FP64 or FP32
+ * storage, f[i][y][x]), on cuda_stream (NULL: the default stream).  This entry
+ * point has no counterpart in the paper: it exists for callers that cannot
+ * let a library allocate device memory -- their memory comes from their own
+ * pool or framework allocator, or they run under a fixed budget -- so it calls
+ * no cudaMalloc, cudaFree or other allocating routine.  Its constant tables
+ * and status word live in one file-scope __device__ array of 32 KB that every
+ * GPU loading the library holds until the process exits; the first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current, so make the first call on each device before any stream
+ * capture.  Limits: N in {2, 3}, K (N+1) <= 256 populations; larger sizes
+ * return RLBM_ERR_ARG.  Every call rewrites the array and clears its status
+ * word, so calls that overlap on the GPU race: serialise them.  The call
+ * synchronises the stream and returns RLBM_ERR_UNPHYSICAL if a cell had no
+ * physical Landau frame.  rlbm_noalloc_last_error() gives the message of the
+ * calling thread's latest failure. */
+rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles_K, double tau, int precision,
+                              const void *d_fin, void *d_fout, void *cuda_stream);
+const char *rlbm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ EXPORTS = [
     "rlbm_batch_arena_bytes", "rlbm_batch_create", "rlbm_batch_destroy", "rlbm_batch_last_error",
     "rlbm_batch_count", "rlbm_batch_problem", "rlbm_batch_step", "rlbm_batch_sync",
     "rlbm_batch_kernel_launches", "rlbm_batch_autotune", "rlbm_batch_set_wait_limit",
-    "rlbm_batch_test_stall_next_step",
+    "rlbm_batch_test_stall_next_step", "rlbm_step_noalloc", "rlbm_noalloc_last_error",
 ]
 
 
@@ -146,6 +146,11 @@ def lib(path: str = LIB_PATH):
     L.rlbm_batch_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
     L.rlbm_batch_test_stall_next_step.restype = st
     L.rlbm_batch_test_stall_next_step.argtypes = [_vp]
+    L.rlbm_step_noalloc.restype = st
+    L.rlbm_step_noalloc.argtypes = [Grid, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    _vp, _vp, _vp]
+    L.rlbm_noalloc_last_error.restype = ctypes.c_char_p
+    L.rlbm_noalloc_last_error.argtypes = []
     _lib = L
     return L
 
@@ -433,3 +438,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def step_noalloc(nx, ny, N, K, tau, precision, fin, fout, bcx=BC_COPYOUT, bcy=BC_PERIODIC,
+                 stream=None):
+    """One step from device tensor fin to device tensor fout through the
+    allocation-free entry point (the library allocates no device memory)."""
+    st = lib().rlbm_step_noalloc(Grid(nx, ny, bcx, bcy), int(N), int(K), float(tau),
+                                 PRECISIONS[precision], _vp(fin.data_ptr()), _vp(fout.data_ptr()),
+                                 _vp(stream.cuda_stream if stream is not None else 0))
+    if st != OK:
+        msg = lib().rlbm_noalloc_last_error().decode(errors="replace")
+        cls = {ERR_UNPHYSICAL: Unphysical}.get(st, RLBMError)
+        raise cls(st, msg)
