@@ -246,6 +246,63 @@ rlbm_status rlbm_batch_set_wait_limit(rlbm_batch_t *b, long long cycles);
 rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b);
 
 /* ------------------------------------------------------------------ */
+/* Learned angular closure (an extension; the paper has no counterpart)  */
+/* ------------------------------------------------------------------ */
+/* A small MLP corrects a coarse-angle run toward the fine-angle solution.
+ * Per site: features x = (N^a, T^ab)/N^0 (9 values), Kn, f_i/(w_i N^0)
+ * (N_pop values); y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3 with hidden
+ * width 64 and N_pop outputs; the correction d_i = y_i w_i N^0 minus its
+ * weighted least-squares component along p^0, p^0 p^0, p^0 p^x, p^0 p^y is
+ * added to the post-collision populations, so N^0, T^00, T^0x, T^0y of every
+ * site are kept.  Weights are BF16 in the forward passes (FP32 master copy,
+ * Adam), products accumulate in FP32.  Activations are feature-major
+ * [feature][column] device arrays with leading dimension ld; coarse
+ * populations are FP32 [i][site].  Parameters are one flat FP32 array:
+ * W1 [F][64], b1 [64], W2 [64][64], b2 [64], W3 [64][N_pop], b3 [N_pop],
+ * F = 10 + N_pop (input-major matrices). */
+typedef struct rlbm_closure rlbm_closure_t;
+
+rlbm_status rlbm_closure_create(rlbm_closure_t **out, int order_N, int angles_K,
+                                unsigned long long seed, void *cuda_stream);
+void rlbm_closure_destroy(rlbm_closure_t *c);
+const char *rlbm_closure_last_error(const rlbm_closure_t *c);
+size_t rlbm_closure_param_count(const rlbm_closure_t *c);
+rlbm_status rlbm_closure_get_params(rlbm_closure_t *c, float *host, size_t n);
+rlbm_status rlbm_closure_set_params(rlbm_closure_t *c, const float *host, size_t n);
+
+/* Features of `sites` sites of coarse FP32 populations d_f into columns
+ * [off, off + sites) of d_x (F rows, leading dimension ld). */
+rlbm_status rlbm_closure_features(rlbm_closure_t *c, const float *d_f, long long sites, double kn,
+                                  float *d_x, long long ld, long long off);
+/* Training target (d_fr - d_fc) / (w_i N^0(d_fc)) into columns of d_t. */
+rlbm_status rlbm_closure_target(rlbm_closure_t *c, const float *d_fr, const float *d_fc,
+                                long long sites, float *d_t, long long ld, long long off);
+/* Angular restriction of fine FP32 populations (fine_K angles per shell) to
+ * the closure's coarse rule: per shell, the angular function f / w is cut to
+ * its Fourier modes |m| <= (K - 1) / 2 and evaluated at the coarse angles
+ * (exact for equilibria; keeps N^a, T^00, T^0x, T^0y). */
+rlbm_status rlbm_closure_restrict(rlbm_closure_t *c, int fine_K, const float *d_ff,
+                                  long long sites, float *d_fc);
+/* Network output for columns [off, off + count) of d_x into d_y (N_pop rows,
+ * leading dimension ld, columns from 0). */
+rlbm_status rlbm_closure_forward(rlbm_closure_t *c, const float *d_x, long long ld, long long off,
+                                 int count, float *d_y);
+/* Device work array size (floats) for gradient / training on ld columns. */
+size_t rlbm_closure_work_floats(const rlbm_closure_t *c, long long ld);
+/* Mean-squared-error gradient over columns [off, off + count); host_grad
+ * (param_count floats, may be NULL) and loss (may be NULL). */
+rlbm_status rlbm_closure_gradient(rlbm_closure_t *c, const float *d_x, const float *d_t,
+                                  long long ld, long long off, int count, float *d_work,
+                                  float *host_grad, float *loss);
+/* One Adam step (beta 0.9, 0.999) on the same loss. */
+rlbm_status rlbm_closure_train_step(rlbm_closure_t *c, const float *d_x, const float *d_t,
+                                    long long ld, long long off, int count, float lr,
+                                    float *d_work, float *loss);
+/* Features + network + conservative projection + update of `sites` sites of
+ * coarse FP32 populations d_f, in place (one fused kernel). */
+rlbm_status rlbm_closure_apply_buffer(rlbm_closure_t *c, float *d_f, long long sites, double kn);
+
+/* ------------------------------------------------------------------ */
 /* Allocation-free single step                                          */
 /* ------------------------------------------------------------------ */
 

@@ -36,6 +36,11 @@ EXPORTS = [
     "rlbm_batch_count", "rlbm_batch_problem", "rlbm_batch_step", "rlbm_batch_sync",
     "rlbm_batch_kernel_launches", "rlbm_batch_autotune", "rlbm_batch_set_wait_limit",
     "rlbm_batch_test_stall_next_step", "rlbm_step_noalloc", "rlbm_noalloc_last_error",
+    "rlbm_closure_create", "rlbm_closure_destroy", "rlbm_closure_last_error",
+    "rlbm_closure_param_count", "rlbm_closure_get_params", "rlbm_closure_set_params",
+    "rlbm_closure_features", "rlbm_closure_target", "rlbm_closure_restrict",
+    "rlbm_closure_forward", "rlbm_closure_work_floats", "rlbm_closure_gradient",
+    "rlbm_closure_train_step", "rlbm_closure_apply_buffer",
 ]
 
 
@@ -151,6 +156,37 @@ def lib(path: str = LIB_PATH):
                                     _vp, _vp, _vp]
     L.rlbm_noalloc_last_error.restype = ctypes.c_char_p
     L.rlbm_noalloc_last_error.argtypes = []
+    ll, fp = ctypes.c_longlong, ctypes.POINTER(ctypes.c_float)
+    L.rlbm_closure_create.restype = st
+    L.rlbm_closure_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_ulonglong, _vp]
+    L.rlbm_closure_destroy.restype = None
+    L.rlbm_closure_destroy.argtypes = [_vp]
+    L.rlbm_closure_last_error.restype = ctypes.c_char_p
+    L.rlbm_closure_last_error.argtypes = [_vp]
+    L.rlbm_closure_param_count.restype = ctypes.c_size_t
+    L.rlbm_closure_param_count.argtypes = [_vp]
+    L.rlbm_closure_get_params.restype = st
+    L.rlbm_closure_get_params.argtypes = [_vp, fp, ctypes.c_size_t]
+    L.rlbm_closure_set_params.restype = st
+    L.rlbm_closure_set_params.argtypes = [_vp, fp, ctypes.c_size_t]
+    L.rlbm_closure_features.restype = st
+    L.rlbm_closure_features.argtypes = [_vp, _vp, ll, ctypes.c_double, _vp, ll, ll]
+    L.rlbm_closure_target.restype = st
+    L.rlbm_closure_target.argtypes = [_vp, _vp, _vp, ll, _vp, ll, ll]
+    L.rlbm_closure_restrict.restype = st
+    L.rlbm_closure_restrict.argtypes = [_vp, ctypes.c_int, _vp, ll, _vp]
+    L.rlbm_closure_forward.restype = st
+    L.rlbm_closure_forward.argtypes = [_vp, _vp, ll, ll, ctypes.c_int, _vp]
+    L.rlbm_closure_work_floats.restype = ctypes.c_size_t
+    L.rlbm_closure_work_floats.argtypes = [_vp, ll]
+    L.rlbm_closure_gradient.restype = st
+    L.rlbm_closure_gradient.argtypes = [_vp, _vp, _vp, ll, ll, ctypes.c_int, _vp, fp, fp]
+    L.rlbm_closure_train_step.restype = st
+    L.rlbm_closure_train_step.argtypes = [_vp, _vp, _vp, ll, ll, ctypes.c_int, ctypes.c_float,
+                                          _vp, fp]
+    L.rlbm_closure_apply_buffer.restype = st
+    L.rlbm_closure_apply_buffer.argtypes = [_vp, _vp, ll, ctypes.c_double]
     _lib = L
     return L
 
@@ -451,3 +487,114 @@ def step_noalloc(nx, ny, N, K, tau, precision, fin, fout, bcx=BC_COPYOUT, bcy=BC
         msg = lib().rlbm_noalloc_last_error().decode(errors="replace")
         cls = {ERR_UNPHYSICAL: Unphysical}.get(st, RLBMError)
         raise cls(st, msg)
+
+
+class Closure:
+    """Learned angular closure (MLP) for a coarse FP32 problem of order N with K angles.
+
+    Arrays are torch CUDA float32 tensors: populations (npop, sites), features
+    (F, ld), targets and outputs (npop, ld)."""
+
+    HIDDEN = 64
+
+    def __init__(self, N: int, K: int, seed: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("librlbm needs a CUDA GPU")
+        self.N, self.K = int(N), int(K)
+        self.npop = self.K * (self.N + 1)
+        self.F = 10 + self.npop
+        # one explicit stream for the closure and the simulations it works with
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = _vp()
+        st = lib().rlbm_closure_create(ctypes.byref(h), self.N, self.K, int(seed),
+                                       _vp(self.stream.cuda_stream))
+        self._c = h
+        self._check(st)
+
+    def _check(self, status: int):
+        if status != OK:
+            msg = lib().rlbm_closure_last_error(self._c if self._c else None).decode(errors="replace")
+            raise RLBMError(status, msg)
+
+    def close(self):
+        if getattr(self, "_c", None):
+            lib().rlbm_closure_destroy(self._c)
+            self._c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self) -> int:
+        return lib().rlbm_closure_param_count(self._c)
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count, dtype=np.float32)
+        self._check(lib().rlbm_closure_get_params(self._c, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  out.size))
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(lib().rlbm_closure_set_params(self._c, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  p.size))
+
+    def split_params(self, p: np.ndarray):
+        """(W1 [F][64], b1, W2 [64][64], b2, W3 [64][npop], b3) views of a flat array."""
+        H, F, O = self.HIDDEN, self.F, self.npop
+        sizes = [F * H, H, H * H, H, H * O, O]
+        shapes = [(F, H), (H,), (H, H), (H,), (H, O), (O,)]
+        out, o = [], 0
+        for n, shp in zip(sizes, shapes):
+            out.append(p[o:o + n].reshape(shp))
+            o += n
+        return out
+
+    def features(self, f, kn: float, X, off: int = 0):
+        self._check(lib().rlbm_closure_features(self._c, _vp(f.data_ptr()), f.shape[1], float(kn),
+                                                _vp(X.data_ptr()), X.shape[1], int(off)))
+
+    def target(self, fr, fc, T, off: int = 0):
+        self._check(lib().rlbm_closure_target(self._c, _vp(fr.data_ptr()), _vp(fc.data_ptr()),
+                                              fr.shape[1], _vp(T.data_ptr()), T.shape[1], int(off)))
+
+    def restrict(self, fine_K: int, ff, fc):
+        self._check(lib().rlbm_closure_restrict(self._c, int(fine_K), _vp(ff.data_ptr()), ff.shape[1],
+                                                _vp(fc.data_ptr())))
+
+    def forward(self, X, off: int, count: int, Y):
+        self._check(lib().rlbm_closure_forward(self._c, _vp(X.data_ptr()), X.shape[1], int(off),
+                                               int(count), _vp(Y.data_ptr())))
+
+    def work(self, ld: int):
+        import torch
+        n = lib().rlbm_closure_work_floats(self._c, int(ld))
+        return torch.empty(n, dtype=torch.float32, device="cuda")
+
+    def gradient(self, X, T, off: int, count: int, work):
+        g = np.zeros(self.param_count, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        self._check(lib().rlbm_closure_gradient(self._c, _vp(X.data_ptr()), _vp(T.data_ptr()),
+                                                X.shape[1], int(off), int(count), _vp(work.data_ptr()),
+                                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, X, T, off: int, count: int, lr: float, work) -> float:
+        loss = ctypes.c_float(0.0)
+        self._check(lib().rlbm_closure_train_step(self._c, _vp(X.data_ptr()), _vp(T.data_ptr()),
+                                                  X.shape[1], int(off), int(count), float(lr),
+                                                  _vp(work.data_ptr()), ctypes.byref(loss)))
+        return loss.value
+
+    def apply_buffer(self, f_ptr: int, sites: int, kn: float):
+        self._check(lib().rlbm_closure_apply_buffer(self._c, _vp(f_ptr), int(sites), float(kn)))
+
+    def apply(self, sim, kn: float):
+        """Correct the current populations of a coarse FP32 Simulation in place."""
+        assert sim.precision == "fp32" and sim.K == self.K and sim.N == self.N
+        self.apply_buffer(sim.current_buffer_ptr(), sim.sites, kn)

@@ -1,0 +1,141 @@
+"""Learned-closure kernels against the FP64 reference (oracle/closure.py)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from oracle import closure as C  # noqa: E402
+from paper_2011_06856_gb300 import build as B  # noqa: E402
+from paper_2011_06856_gb300 import closure as CL  # noqa: E402
+from paper_2011_06856_gb300 import rlbm as R  # noqa: E402
+from paper_2011_06856_gb300 import workloads as W  # noqa: E402
+
+B.build()
+N, K, KF = 2, 24, 128
+
+
+def bf16(a):
+    """Round to BF16 (nearest even), as the device copy of the weights."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def ref_params(cl):
+    p = cl.split_params(cl.get_params().astype(np.float64))
+    return [bf16(p[0]), p[1], bf16(p[2]), p[3], bf16(p[4]), p[5]]
+
+
+def random_coarse_populations(sites, seed):
+    q = O.Quadrature(N, K)
+    g = np.random.default_rng(seed)
+    f = np.stack([q.feq(g.uniform(0.3, 1), g.uniform(0.5, 1.1), g.uniform(-0.2, 0.2),
+                        g.uniform(-0.2, 0.2)) for _ in range(sites)], axis=1)
+    f *= g.uniform(0.9, 1.1, f.shape)  # off equilibrium
+    return q, f
+
+
+def test_features_restriction_target_match_reference():
+    cl = R.Closure(N, K, seed=1)
+    q, f = random_coarse_populations(300, 0)
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    X = torch.zeros((cl.F, 300), dtype=torch.float32, device="cuda")
+    cl.features(fd, 0.37, X)
+    cl.stream.synchronize()
+    ref = C.features(f.astype(np.float32).astype(np.float64), q.p0, q.vx, q.vy, q.w, 0.37).T
+    np.testing.assert_allclose(X.cpu().numpy(), ref, rtol=2e-5, atol=2e-6)
+    # restriction of fine populations
+    qf = O.Quadrature(N, KF)
+    ff = np.random.default_rng(4).uniform(0.1, 1, (qf.npop, 50)) * qf.w[:, None]
+    ffd = torch.tensor(ff, dtype=torch.float32, device="cuda")
+    fcd = torch.zeros((cl.npop, 50), dtype=torch.float32, device="cuda")
+    cl.restrict(KF, ffd, fcd)
+    np.testing.assert_allclose(fcd.cpu().numpy(), C.restrict(ff.astype(np.float32).astype(np.float64), N, KF, K),
+                               rtol=2e-5, atol=1e-9)
+    # target
+    T = torch.zeros((cl.npop, 50), dtype=torch.float32, device="cuda")
+    fc2 = fcd * 1.01
+    cl.target(fcd, fc2, T)
+    cl.stream.synchronize()
+    a, b = fcd.double().cpu().numpy(), fc2.double().cpu().numpy()
+    n0 = q.p0 @ b
+    np.testing.assert_allclose(T.cpu().numpy(), (a - b) / (q.w[:, None] * n0[None, :]), rtol=1e-4, atol=1e-6)
+
+
+def test_forward_and_gradient_match_reference():
+    cl = R.Closure(N, K, seed=2)
+    g = np.random.default_rng(5)
+    S = 700
+    X = g.normal(0, 0.5, (cl.F, S)).astype(np.float32)
+    T = g.normal(0, 0.1, (cl.npop, S)).astype(np.float32)
+    Xd = torch.tensor(X, device="cuda")
+    Td = torch.tensor(T, device="cuda")
+    Y = torch.zeros((cl.npop, S), dtype=torch.float32, device="cuda")
+    cl.forward(Xd, 0, S, Y)
+    cl.stream.synchronize()
+    params = ref_params(cl)
+    yref, _ = C.mlp_forward(params, X.T.astype(np.float64))
+    np.testing.assert_allclose(Y.cpu().numpy(), yref.T, rtol=1e-4, atol=1e-5)
+    work = cl.work(S)
+    grad, loss = cl.gradient(Xd, Td, 100, 500, work)
+    lref, gref = C.mlp_loss_and_grad(params, X[:, 100:600].T.astype(np.float64),
+                                     T[:, 100:600].T.astype(np.float64))
+    assert abs(loss - lref) < 1e-4 * lref
+    flat = np.concatenate([a.ravel() for a in gref])
+    assert np.abs(grad - flat).max() < 1e-3 * np.abs(flat).max()
+
+
+def test_apply_conserves_and_matches_reference():
+    cl = R.Closure(N, K, seed=3)
+    sites = 333
+    q, f = random_coarse_populations(sites, 6)
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda").contiguous()
+    f32 = fd.double().cpu().numpy()
+    cl.apply_buffer(fd.data_ptr(), sites, 0.3)
+    cl.stream.synchronize()
+    got = fd.double().cpu().numpy()
+    # reference: features -> network -> denormalise -> projection -> add
+    params = ref_params(cl)
+    X = C.features(f32, q.p0, q.vx, q.vy, q.w, 0.3)
+    y, _ = C.mlp_forward(params, X)
+    n0 = q.p0 @ f32
+    d = y.T * q.w[:, None] * n0[None, :]
+    ref = f32 + C.conservative_projection(d, q.p0, q.vx, q.vy, q.w)
+    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-7 * np.abs(f32).max())
+    Cm = np.stack([q.p0, q.p0 ** 2, q.p0 ** 2 * q.vx, q.p0 ** 2 * q.vy])
+    before, after = Cm @ f32, Cm @ got
+    assert np.abs(after - before).max() < 2e-6 * np.abs(before).max()
+
+
+def test_training_on_method_data_reduces_loss():
+    cl = R.Closure(N, K, seed=4)
+    X, T = CL.generate(cl, 32, KF, kns=(0.05, 0.5), steps=12)
+    assert X.shape[1] == 2 * 12 * 32 * 32
+    assert torch.isfinite(X).all() and torch.isfinite(T).all()
+    losses = CL.train(cl, X, T, iters=120, batch=2048, lr=3e-3)
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5]), (losses[:5], losses[-20:])
+
+
+def test_trained_closure_reduces_coarse_error_vs_fine():
+    """Gain test: trained on runs of the method itself (K = 128 fine, K = 24 coarse),
+    the corrected coarse run is closer to the fine run than the plain coarse run
+    (relative L2, Eq. rel_err, of n and eps) on a Riemann problem not in the
+    training set, at Kn = 0.3 and Kn = 1."""
+    cl = R.Closure(N, K, seed=7)
+    X, T = CL.generate(cl, 64, KF, kns=(0.02, 0.1, 0.5, 2.0), steps=48, every=2)
+    CL.train(cl, X, T, iters=1500, batch=8192, lr=2e-3)
+    plain, learned = [], []
+    for kn in (0.3, 1.0):
+        mf, mc, ml = CL.deploy(cl, 64, KF, kn, 48)
+        for i in (0, 1):
+            plain.append(CL.rel_l2(mc[i], mf[i]))
+            learned.append(CL.rel_l2(ml[i], mf[i]))
+    print("plain", plain, "learned", learned)
+    assert np.mean(learned) < 0.95 * np.mean(plain)
