@@ -75,21 +75,22 @@ struct TmaSmem {
 // Persistent TMA-staged step launchers; grid <= 0 with blocks_per_sm set only
 // queries the occupancy.
 #define RLBM_DECLARE_TMA(t)                                                                       \
-    cudaError_t launch_tma_##t(int N, int P, bool two_d, bool site_fp64, int grid, dim3 block,     \
-                               size_t smem, cudaStream_t st, const TmaArgs &a, int *bps);
+    cudaError_t launch_tma_##t(int N, int P, bool two_d, bool full, bool site_fp64, int grid,      \
+                               dim3 block, size_t smem, cudaStream_t st, const TmaArgs &a, int *bps);
 RLBM_DECLARE_TMA(f64)
 RLBM_DECLARE_TMA(f32)
 RLBM_DECLARE_TMA(f16)
 RLBM_DECLARE_TMA(bf16)
 #undef RLBM_DECLARE_TMA
-cudaError_t launch_f64(int mode, int N, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
-                       cudaStream_t st, const KernelArgs &a);
-cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool site_fp64, dim3 grid, dim3 block,
+// full: K is a multiple of P (every warp owns exactly P populations)
+cudaError_t launch_f64(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
-cudaError_t launch_f16(int mode, int N, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
-                       cudaStream_t st, const KernelArgs &a);
-cudaError_t launch_bf16(int mode, int N, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
-                        cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool full, bool site_fp64, dim3 grid,
+                       dim3 block, size_t smem, cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_f16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_bf16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                        size_t smem, cudaStream_t st, const KernelArgs &a);
 
 // Batched persistent form (rlbm_batch.cuh).
 constexpr int kBatchWarps = 6;

@@ -346,8 +346,9 @@ __device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, L
 
 // St: storage type; R: per-population arithmetic; LR: per-site arithmetic
 // (moment sums, Landau frame, equilibrium coefficients); N: quadrature order;
-// P: populations per thread (compile-time upper bound); TWO_D: ny > 1.
-template <class St, class R, class LR, int N, int P, bool TWO_D, int MODE>
+// P: populations per thread (compile-time upper bound); TWO_D: ny > 1;
+// FULL: every warp owns exactly P populations (no per-population guard).
+template <class St, class R, class LR, int N, int P, bool TWO_D, int MODE, bool FULL>
 __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a)
 {
     constexpr int NC = 2 * N + 1;
@@ -360,7 +361,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     const int y = blockIdx.y;
     const int r = g / a.Gs, q = g % a.Gs;
     const int i0 = r * a.K + q * a.P;
-    const int pc = min(a.P, a.K - q * a.P); // populations of this warp
+    // populations of this warp (FULL: K is a multiple of P, every warp owns P)
+    const int pc = FULL ? P : min(a.P, a.K - q * a.P);
     const long long S = a.S;
     const long long site = (long long)y * a.nx + x;
     const R *tab = reinterpret_cast<const R *>(a.poptab) + (long long)i0 * TW;

@@ -434,15 +434,16 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     const dim3 block(32, h->G);
     const size_t smem = smem_bytes(h);
     const bool two_d = h->grid.ny > 1;
+    const bool full = (h->K % h->P) == 0;
     cudaError_t e;
     switch (h->prec) {
-    case RLBM_FP64: e = rlbmk::launch_f64(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    case RLBM_FP64: e = rlbmk::launch_f64(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
     case RLBM_FP32:
-        e = rlbmk::launch_f32(mode, h->N, h->P, two_d, h->site_fp64, grid, block, smem, h->stream, a);
+        e = rlbmk::launch_f32(mode, h->N, h->P, two_d, full, h->site_fp64, grid, block, smem, h->stream, a);
         break;
     case RLBM_FP16_DEV:
-    case RLBM_FP16_NORM: e = rlbmk::launch_f16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
-    default: e = rlbmk::launch_bf16(mode, h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    case RLBM_FP16_NORM: e = rlbmk::launch_f16(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
+    default: e = rlbmk::launch_bf16(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
     }
     if (e == cudaSuccess) ++h->launches;
     return e;
@@ -452,12 +453,13 @@ cudaError_t launch_tma(rlbm_t *h, const rlbmk::TmaArgs &ta, int grid, int *bps)
 {
     const dim3 block(32, h->G);
     const bool two_d = h->grid.ny > 1;
+    const bool full = (h->K % h->P) == 0;
     switch (h->prec) {
-    case RLBM_FP64: return rlbmk::launch_tma_f64(h->N, h->P, two_d, false, grid, block, h->tma_smem, h->stream, ta, bps);
-    case RLBM_FP32: return rlbmk::launch_tma_f32(h->N, h->P, two_d, h->site_fp64, grid, block, h->tma_smem, h->stream, ta, bps);
+    case RLBM_FP64: return rlbmk::launch_tma_f64(h->N, h->P, two_d, full, false, grid, block, h->tma_smem, h->stream, ta, bps);
+    case RLBM_FP32: return rlbmk::launch_tma_f32(h->N, h->P, two_d, full, h->site_fp64, grid, block, h->tma_smem, h->stream, ta, bps);
     case RLBM_FP16_DEV:
-    case RLBM_FP16_NORM: return rlbmk::launch_tma_f16(h->N, h->P, two_d, false, grid, block, h->tma_smem, h->stream, ta, bps);
-    default: return rlbmk::launch_tma_bf16(h->N, h->P, two_d, false, grid, block, h->tma_smem, h->stream, ta, bps);
+    case RLBM_FP16_NORM: return rlbmk::launch_tma_f16(h->N, h->P, two_d, full, false, grid, block, h->tma_smem, h->stream, ta, bps);
+    default: return rlbmk::launch_tma_bf16(h->N, h->P, two_d, full, false, grid, block, h->tma_smem, h->stream, ta, bps);
     }
 }
 

@@ -2,11 +2,11 @@
 // folding, Landau frame, equilibrium coefficients) in FP32 or FP64.
 #include "rlbm_launch.cuh"
 namespace rlbmk {
-cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool site_fp64, dim3 grid, dim3 block,
+cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool full, bool site_fp64, dim3 grid, dim3 block,
                        size_t smem, cudaStream_t st, const KernelArgs &a)
 {
     if (site_fp64)
-        return launch_t<float, float, double>(mode, N, P, two_d, grid, block, smem, st, a);
-    return launch_t<float, float, float>(mode, N, P, two_d, grid, block, smem, st, a);
+        return launch_t<float, float, double>(mode, N, P, two_d, full, grid, block, smem, st, a);
+    return launch_t<float, float, float>(mode, N, P, two_d, full, grid, block, smem, st, a);
 }
 } // namespace rlbmk

@@ -7,17 +7,22 @@
 namespace rlbmk {
 
 template <class St, class R, class LR, int N, int P>
-static cudaError_t launch_np(int mode, bool two_d, dim3 grid, dim3 block, size_t smem,
+static cudaError_t launch_np(int mode, bool two_d, bool full, dim3 grid, dim3 block, size_t smem,
                             cudaStream_t st, const KernelArgs &a)
 {
     void (*k)(const KernelArgs);
-    if (mode == MODE_STEP)
-        k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP>
-                  : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP>;
-    else if (mode == MODE_INIT)
-        k = rlbm_kernel<St, R, LR, N, P, false, MODE_INIT>;
-    else
-        k = rlbm_kernel<St, R, LR, N, P, false, MODE_MOMENTS>;
+    if (mode == MODE_STEP) {
+        if (full)
+            k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP, true>
+                      : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP, true>;
+        else
+            k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP, false>
+                      : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP, false>;
+    } else if (mode == MODE_INIT) {
+        k = rlbm_kernel<St, R, LR, N, P, false, MODE_INIT, false>;
+    } else {
+        k = rlbm_kernel<St, R, LR, N, P, false, MODE_MOMENTS, false>;
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -28,28 +33,28 @@ static cudaError_t launch_np(int mode, bool two_d, dim3 grid, dim3 block, size_t
 }
 
 template <class St, class R, class LR, int N>
-static cudaError_t launch_n(int mode, int P, bool two_d, dim3 grid, dim3 block, size_t smem,
-                           cudaStream_t st, const KernelArgs &a)
+static cudaError_t launch_n(int mode, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t st, const KernelArgs &a)
 {
     switch (P) {
-    case 8: return launch_np<St, R, LR, N, 8>(mode, two_d, grid, block, smem, st, a);
-    case 12: return launch_np<St, R, LR, N, 12>(mode, two_d, grid, block, smem, st, a);
-    case 16: return launch_np<St, R, LR, N, 16>(mode, two_d, grid, block, smem, st, a);
-    case 24: return launch_np<St, R, LR, N, 24>(mode, two_d, grid, block, smem, st, a);
-    case 32: return launch_np<St, R, LR, N, 32>(mode, two_d, grid, block, smem, st, a);
-    case 48: return launch_np<St, R, LR, N, 48>(mode, two_d, grid, block, smem, st, a);
-    case 64: return launch_np<St, R, LR, N, 64>(mode, two_d, grid, block, smem, st, a);
+    case 8: return launch_np<St, R, LR, N, 8>(mode, two_d, full, grid, block, smem, st, a);
+    case 12: return launch_np<St, R, LR, N, 12>(mode, two_d, full, grid, block, smem, st, a);
+    case 16: return launch_np<St, R, LR, N, 16>(mode, two_d, full, grid, block, smem, st, a);
+    case 24: return launch_np<St, R, LR, N, 24>(mode, two_d, full, grid, block, smem, st, a);
+    case 32: return launch_np<St, R, LR, N, 32>(mode, two_d, full, grid, block, smem, st, a);
+    case 48: return launch_np<St, R, LR, N, 48>(mode, two_d, full, grid, block, smem, st, a);
+    case 64: return launch_np<St, R, LR, N, 64>(mode, two_d, full, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <class St, class R, class LR>
-static cudaError_t launch_t(int mode, int N, int P, bool two_d, dim3 grid, dim3 block,
-                           size_t smem, cudaStream_t st, const KernelArgs &a)
+static cudaError_t launch_t(int mode, int N, int P, bool two_d, bool full, dim3 grid,
+                           dim3 block, size_t smem, cudaStream_t st, const KernelArgs &a)
 {
     switch (N) {
-    case 2: return launch_n<St, R, LR, 2>(mode, P, two_d, grid, block, smem, st, a);
-    case 3: return launch_n<St, R, LR, 3>(mode, P, two_d, grid, block, smem, st, a);
+    case 2: return launch_n<St, R, LR, 2>(mode, P, two_d, full, grid, block, smem, st, a);
+    case 3: return launch_n<St, R, LR, 3>(mode, P, two_d, full, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
     }
 }

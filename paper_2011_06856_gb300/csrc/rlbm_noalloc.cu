@@ -284,10 +284,11 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
 
     const dim3 gridd((grid.nx + 31) / 32, grid.ny), block(32, G);
     const size_t smem = es * 5 * size_t(G) * 32;
-    const cudaError_t e = r64 ? rlbmk::launch_f64(rlbmk::MODE_STEP, N, P, grid.ny > 1, gridd, block,
-                                                  smem, stream, a)
-                              : rlbmk::launch_f32(rlbmk::MODE_STEP, N, P, grid.ny > 1, false, gridd,
-                                                  block, smem, stream, a);
+    const bool full = (K % P) == 0;
+    const cudaError_t e = r64 ? rlbmk::launch_f64(rlbmk::MODE_STEP, N, P, grid.ny > 1, full, gridd,
+                                                  block, smem, stream, a)
+                              : rlbmk::launch_f32(rlbmk::MODE_STEP, N, P, grid.ny > 1, full, false,
+                                                  gridd, block, smem, stream, a);
     if (e != cudaSuccess) return fail(RLBM_ERR_CUDA, cudaGetErrorString(e));
     int status = 0;
     if (cudaMemcpyAsync(&status, base + o_status, sizeof(int), cudaMemcpyDeviceToHost, stream) !=

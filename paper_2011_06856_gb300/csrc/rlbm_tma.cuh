@@ -126,7 +126,7 @@ __device__ __forceinline__ void lds4<float>(const float *p, float &x, float &y, 
     x = v.x; y = v.y; z = v.z; w = v.w;
 }
 
-template <class St, class R, class LR, int N, int P, bool TWO_D>
+template <class St, class R, class LR, int N, int P, bool TWO_D, bool FULL>
 __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_step_tma(const __grid_constant__ TmaArgs ta)
 {
     constexpr int NC = 2 * N + 1;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_step_tma(const __grid_con
     const int npop = a.K * (N + 1);
     const int r = g / a.Gs, q = g % a.Gs;
     const int i0 = r * a.K + q * a.P;
-    const int pc = min(a.P, a.K - q * a.P);
+    const int pc = FULL ? P : min(a.P, a.K - q * a.P);
     const long long S = a.S;
 
     // shared memory carve-up (the host sizes it with the same TmaSmem)
