@@ -301,6 +301,10 @@ rlbm_status rlbm_closure_train_step(rlbm_closure_t *c, const float *d_x, const f
 /* Features + network + conservative projection + update of `sites` sites of
  * coarse FP32 populations d_f, in place (one fused kernel). */
 rlbm_status rlbm_closure_apply_buffer(rlbm_closure_t *c, float *d_f, long long sites, double kn);
+/* Choose the kernel of rlbm_closure_apply_buffer: tensor cores (BF16
+ * mma.sync, activations rounded to BF16; the default when N_pop <= 80) or one
+ * thread per site with FP32 activations (tensor_cores = 0). */
+rlbm_status rlbm_closure_set_apply_path(rlbm_closure_t *c, int tensor_cores);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free single step                                          */

@@ -384,6 +384,381 @@ __global__ void __launch_bounds__(128) apply_kernel(Net net, CoarseTab q, float 
     }
 }
 
+// ---------------------------------------------------------------- tensor-core apply
+// The fused correction with the three layers on BF16 tensor cores
+// (mma.sync.m16n8k16, FP32 accumulation), specialised for the coarse rule
+// (N, K).  A CTA of TC_WARPS warps works on tiles of 16 TC_WARPS sites; the
+// populations of the next tile stream into shared memory (cp.async, double
+// buffered) while the current one is processed.
+//
+// * Conservation folded into the last layer.  With d = n0 W y (W = diag w) the
+//   projection d - W C^T A^-1 C d equals n0 W Q y, Q = I - C^T A^-1 C W, a
+//   constant matrix (C rows p^0, p^0 p^0, p^0 p^x, p^0 p^y; A = C W C^T).  So
+//   y' = Q y = h2 (W3 Q^T) + Q b3: each CTA forms W3' = W3 - (W3 V^T) U^T with
+//   V = C W and U = C^T A^-1 (FP32) and keeps it as a BF16 pair hi + lo
+//   (relative error 2^-17), so that C W y' vanishes to FP32 rounding.  The
+//   update is then f += n0 w_i y'_i.
+// * Features.  Warp w owns sites 16w..16w+15 of the tile; lane (site, half)
+//   sums half of every shell's angles (per-shell angular sums S0, Sc, Ss,
+//   Scc, Scs, Sss folded with p_r, p_r^2), the halves are joined by a shuffle,
+//   and the lane writes its populations / (w_i n0) as BF16 pairs into the
+//   warp's input row.
+// * Layers: [16 x K] x [K x N] products, fragments by ldmatrix from
+//   transposed, padded BF16 weights; GELU between them (gelu_as below).
+constexpr int TC_WARPS = 12;
+constexpr int TC_SITES = 16 * TC_WARPS; // sites per CTA tile
+constexpr int LDF = TC_SITES + 4;       // population-row stride of the tile (bank spread)
+constexpr int SH = 72;                  // row stride of hidden tiles and of W2^T, W3'^T
+
+__device__ __forceinline__ void mma_bf16(float *d, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(const void *p, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2(const void *p, unsigned &r0, unsigned &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&v);
+}
+
+// GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2 with erf from Abramowitz &
+// Stegun 7.1.26 (Hastings' rational approximation, |error| <= 1.5e-7):
+// erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z),
+// z >= 0, extended to z < 0 by symmetry.  The layers' inputs are BF16, so
+// this accuracy is far below their rounding.
+__device__ __forceinline__ float gelu_as(float x)
+{
+    const float z = fabsf(x) * 0.70710678118654752f;
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, z, 1.0f)));
+    float q = fmaf(1.061405429f, t, -1.453152027f);
+    q = fmaf(q, t, 1.421413741f);
+    q = fmaf(q, t, -0.284496736f);
+    q = fmaf(q, t, 0.254829592f);
+    q *= t;
+    float e; // exp(-z^2)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.4426950408889634f * z * z));
+    const float h = 0.5f * q * e;                          // (1 - erf(z)) / 2
+    return x * (x >= 0.f ? 1.f - h : h);
+}
+
+// acc[nt][4] += A[16 x 16 KS] (row stride sa) x Bt[8 NT x 16 KS]^T (row stride sb)
+template <int KS, int NT>
+__device__ __forceinline__ void warp_gemm(const __nv_bfloat16 *A, int sa, const __nv_bfloat16 *Bt, int sb,
+                                          float (*acc)[4], int lane)
+{
+    const int mi = lane >> 3, r8 = lane & 7;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        unsigned a0, a1, a2, a3;
+        // matrices: rows 0-7 | rows 8-15 at k0, then the same at k0 + 8
+        ldsm_x4(A + ((mi & 1) * 8 + r8) * sa + ks * 16 + (mi >> 1) * 8, a0, a1, a2, a3);
+#pragma unroll
+        for (int np = 0; np < NT / 2; ++np) {
+            unsigned b0, b1, b2, b3;
+            // matrices: n-tile 2np at k0 | k0 + 8, n-tile 2np+1 at k0 | k0 + 8
+            ldsm_x4(Bt + (np * 16 + (mi >> 1) * 8 + r8) * sb + ks * 16 + (mi & 1) * 8, b0, b1, b2, b3);
+            mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
+            mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+        }
+        if (NT & 1) {
+            unsigned b0, b1;
+            ldsm_x2(Bt + ((NT - 1) * 8 + r8) * sb + ks * 16 + (mi & 1) * 8, b0, b1);
+            mma_bf16(acc[NT - 1], a0, a1, a2, a3, b0, b1);
+        }
+    }
+}
+
+__device__ __forceinline__ void bias_init(float (*acc)[4], const float *b, int nts, int lane)
+{
+    const int t = lane & 3;
+    for (int nt = 0; nt < nts; ++nt) {
+        const float2 v = *reinterpret_cast<const float2 *>(b + nt * 8 + 2 * t);
+        acc[nt][0] = v.x; acc[nt][1] = v.y; acc[nt][2] = v.x; acc[nt][3] = v.y;
+    }
+}
+
+__device__ __forceinline__ void gelu_rows(float (*acc)[4], __nv_bfloat16 *h, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int c = nt * 8 + t * 2;
+        *reinterpret_cast<unsigned *>(h + g * SH + c) = pack_bf16(gelu_as(acc[nt][0]), gelu_as(acc[nt][1]));
+        *reinterpret_cast<unsigned *>(h + (g + 8) * SH + c) =
+            pack_bf16(gelu_as(acc[nt][2]), gelu_as(acc[nt][3]));
+    }
+}
+
+// Populations of the tile at site0 into the shared tile (rows of LDF floats);
+// sites >= S read as zero.  VEC = 4: 16-byte copies (S % 4 == 0, f 16-byte
+// aligned); VEC = 1: 4-byte copies.
+template <int VEC>
+__device__ __forceinline__ void load_tile(float *tile, const float *f, long long S, long long site0, int npop)
+{
+    constexpr int CH = TC_SITES / VEC;
+    for (int e = threadIdx.x; e < npop * CH; e += blockDim.x) {
+        const int i = e / CH, c = e % CH;
+        const long long site = site0 + c * VEC;
+        const bool ok = site < S;
+        const float *src = ok ? f + (long long)i * S + site : f;
+        const unsigned dst = smem_addr(tile + i * LDF + c * VEC);
+        if (VEC == 4)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
+                         : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_tile(const float *tile, float *f, long long S, long long site0, int npop)
+{
+    constexpr int CH = TC_SITES / VEC;
+    for (int e = threadIdx.x; e < npop * CH; e += blockDim.x) {
+        const int i = e / CH, c = e % CH;
+        const long long site = site0 + c * VEC;
+        if (site >= S) continue;
+        if (VEC == 4)
+            *reinterpret_cast<float4 *>(f + (long long)i * S + site) =
+                *reinterpret_cast<const float4 *>(tile + i * LDF + c * 4);
+        else
+            f[(long long)i * S + site] = tile[i * LDF + c];
+    }
+}
+
+template <int N, int K>
+struct TcGeom {
+    static constexpr int NPOP = (N + 1) * K;
+    static constexpr int F = 10 + NPOP;
+    static constexpr int KS1 = (F + 15) / 16; // k-steps of layer 1
+    static constexpr int SX = 16 * KS1 + 8;   // input row stride: odd number of 16-byte units
+    static constexpr int NT3 = NPOP / 8;      // n-tiles of layer 3
+    // shared memory carve-up, bytes
+    static constexpr size_t W1 = 0, W2 = W1 + size_t(64) * SX * 2, W3H = W2 + size_t(64) * SH * 2,
+                            W3L = W3H + size_t(NPOP) * SH * 2, BIAS = W3L + size_t(NPOP) * SH * 2,
+                            TAB = BIAS + size_t(128 + NPOP) * 4,
+                            WV = TAB + size_t(4 * NPOP + 8) * 4, // cs (2 NPOP), invw, wq, p_r (<= 8)
+                            FT = (WV + 64 * 4 * 4 + 8 * 4 + 15) / 16 * 16,
+                            WARP = FT + size_t(2) * NPOP * LDF * 4, TOTAL = WARP + size_t(TC_WARPS) * 16 * SX * 2;
+};
+
+template <int N, int K, int VEC>
+__global__ void __launch_bounds__(TC_WARPS * 32, 1) apply_tc_kernel(Net net, CoarseTab q, float *__restrict__ f,
+                                                                    long long S, float kn)
+{
+    using Gm = TcGeom<N, K>;
+    constexpr int NPOP = Gm::NPOP, F = Gm::F, SX = Gm::SX, KH = K / 2;
+    static_assert(K % 4 == 0 && NPOP % 8 == 0 && NPOP <= 2 * 64, "tile geometry");
+    extern __shared__ __align__(16) unsigned char sm[];
+    __nv_bfloat16 *w1t = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W1);  // [64][SX]
+    __nv_bfloat16 *w2t = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W2);  // [64][SH]
+    __nv_bfloat16 *w3h = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W3H); // [NPOP][SH]
+    __nv_bfloat16 *w3l = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W3L); // [NPOP][SH]
+    float *bias = reinterpret_cast<float *>(sm + Gm::BIAS);               // b1[64] b2[64] b3'[NPOP]
+    float2 *cs = reinterpret_cast<float2 *>(sm + Gm::TAB);                // (v_x, v_y) per population
+    float *invw = reinterpret_cast<float *>(cs + NPOP);
+    float *wq = invw + NPOP;
+    float *pr = wq + NPOP;                                                // p_r per shell
+    float *wv = reinterpret_cast<float *>(sm + Gm::WV);                   // (W3 V^T)[64][4], V b3 [4]
+    float *ftile = reinterpret_cast<float *>(sm + Gm::FT);                // [2][NPOP][LDF]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __nv_bfloat16 *xa = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::WARP) + size_t(wid) * 16 * SX;
+    const long long ntile = (S + TC_SITES - 1) / TC_SITES;
+    long long tile = blockIdx.x;
+    if (tile < ntile) load_tile<VEC>(ftile, f, S, tile * TC_SITES, NPOP);
+
+    // ---- per-CTA setup: weights, tables, the folded last layer
+    for (int e = tid; e < 64 * SX; e += blockDim.x) {
+        const int n = e / SX, k = e % SX;
+        w1t[e] = (k < F) ? net.W1[k * H + n] : __float2bfloat16_rn(0.f);
+    }
+    for (int e = tid; e < 64 * SH; e += blockDim.x) {
+        const int n = e / SH, k = e % SH;
+        w2t[e] = (k < H) ? net.W2[k * H + n] : __float2bfloat16_rn(0.f);
+    }
+    for (int e = tid; e < 64; e += blockDim.x) { bias[e] = net.b1[e]; bias[64 + e] = net.b2[e]; }
+    for (int e = tid; e < NPOP; e += blockDim.x) {
+        cs[e] = make_float2(q.c[e], q.s[e]);
+        invw[e] = 1.f / q.w[e];
+        wq[e] = q.w[e];
+    }
+    for (int e = tid; e <= N; e += blockDim.x) pr[e] = q.p0[e * K];
+    // C[a][j] for a = 0..3: p, p^2, p^2 c, p^2 s
+    auto Cm = [&](int a0, int j) {
+        const float p = q.p0[j];
+        return a0 == 0 ? p : a0 == 1 ? p * p : a0 == 2 ? p * p * q.c[j] : p * p * q.s[j];
+    };
+    // (W3 V^T)[k][a] = sum_j W3[k][j] C[a][j] w_j, and (V b3)[a]
+    for (int e = tid; e < 64 * 4 + 4; e += blockDim.x) {
+        float acc = 0.f;
+        if (e < 256) {
+            const int k = e >> 2, a0 = e & 3;
+            for (int j = 0; j < NPOP; ++j) acc += __bfloat162float(net.W3[k * NPOP + j]) * Cm(a0, j) * q.w[j];
+        } else {
+            const int a0 = e - 256;
+            for (int j = 0; j < NPOP; ++j) acc += net.b3[j] * Cm(a0, j) * q.w[j];
+        }
+        wv[e] = acc;
+    }
+    __syncthreads();
+    // W3'[k][i] = W3[k][i] - sum_a (W3 V^T)[k][a] U[i][a], U = C^T A^-1; b3' likewise
+    for (int e = tid; e < NPOP * SH; e += blockDim.x) {
+        const int i = e / SH, k = e % SH;
+        float u[4];
+#pragma unroll
+        for (int a0 = 0; a0 < 4; ++a0)
+            u[a0] = Cm(0, i) * q.Ainv[0 * 4 + a0] + Cm(1, i) * q.Ainv[1 * 4 + a0] + Cm(2, i) * q.Ainv[2 * 4 + a0] +
+                    Cm(3, i) * q.Ainv[3 * 4 + a0];
+        if (k < H) {
+            const float v = __bfloat162float(net.W3[k * NPOP + i]) -
+                            (wv[k * 4] * u[0] + wv[k * 4 + 1] * u[1] + wv[k * 4 + 2] * u[2] + wv[k * 4 + 3] * u[3]);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            w3h[e] = hi;
+            w3l[e] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        } else {
+            w3h[e] = __float2bfloat16_rn(0.f);
+            w3l[e] = __float2bfloat16_rn(0.f);
+        }
+        if (k == 0)
+            bias[128 + i] = net.b3[i] - (wv[256] * u[0] + wv[257] * u[1] + wv[258] * u[2] + wv[259] * u[3]);
+    }
+    for (int e = lane; e < 16 * SX; e += 32) xa[e] = __float2bfloat16_rn(0.f);
+    __syncthreads();
+
+    const int g = lane >> 2, t = lane & 3;
+    const int ls = lane & 15, half = lane >> 4;
+    for (int k = 0; tile < ntile; ++k, tile += gridDim.x) {
+        float *cur = ftile + (k & 1) * NPOP * LDF;
+        const long long site0 = tile * TC_SITES;
+        if (tile + gridDim.x < ntile)
+            load_tile<VEC>(ftile + ((k + 1) & 1) * NPOP * LDF, f, S, (tile + gridDim.x) * TC_SITES, NPOP);
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        // ---- features of the warp's 16 sites: this lane takes angles [half K/2, (half+1) K/2) of every shell
+        const int col = wid * 16 + ls;
+        const bool valid = site0 + col < S;
+        float v[N + 1][KH];
+        float m[9];
+#pragma unroll
+        for (int a0 = 0; a0 < 9; ++a0) m[a0] = 0.f;
+#pragma unroll
+        for (int r = 0; r <= N; ++r) {
+            float s0 = 0.f, sc = 0.f, ss = 0.f, scc = 0.f, scs = 0.f, sss = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < KH; ++jj) {
+                const int i = r * K + half * KH + jj;
+                const float x = cur[i * LDF + col];
+                const float2 d = cs[i];
+                v[r][jj] = x;
+                const float cx = d.x * x, sx = d.y * x;
+                s0 += x; sc += cx; ss += sx;
+                scc = fmaf(d.x, cx, scc); scs = fmaf(d.x, sx, scs); sss = fmaf(d.y, sx, sss);
+            }
+            const float p = pr[r], p2 = p * p;
+            m[0] = fmaf(p, s0, m[0]); m[1] = fmaf(p, sc, m[1]); m[2] = fmaf(p, ss, m[2]);
+            m[3] = fmaf(p2, s0, m[3]); m[4] = fmaf(p2, sc, m[4]); m[5] = fmaf(p2, ss, m[5]);
+            m[6] = fmaf(p2, scc, m[6]); m[7] = fmaf(p2, scs, m[7]); m[8] = fmaf(p2, sss, m[8]);
+        }
+#pragma unroll
+        for (int a0 = 0; a0 < 9; ++a0) m[a0] += __shfl_xor_sync(0xffffffffu, m[a0], 16);
+        const float n0 = m[0], inv = valid ? __frcp_rn(n0) : 0.f;
+        __nv_bfloat16 *xr = xa + ls * SX;
+        if (half == 0) {
+#pragma unroll
+            for (int a0 = 0; a0 < 8; a0 += 2)
+                *reinterpret_cast<unsigned *>(xr + a0) = pack_bf16(m[a0] * inv, m[a0 + 1] * inv);
+            *reinterpret_cast<unsigned *>(xr + 8) = pack_bf16(m[8] * inv, kn);
+        }
+#pragma unroll
+        for (int r = 0; r <= N; ++r)
+#pragma unroll
+            for (int jj = 0; jj < KH; jj += 2) {
+                const int i = r * K + half * KH + jj;
+                const float2 iw = *reinterpret_cast<const float2 *>(invw + i);
+                *reinterpret_cast<unsigned *>(xr + 10 + i) =
+                    pack_bf16(v[r][jj] * iw.x * inv, v[r][jj + 1] * iw.y * inv);
+            }
+        // zero padding of layer 1's k range (the hidden tile of the previous tile overlaps it)
+        constexpr int PADP = (16 * Gm::KS1 - F) / 2;
+        for (int e = lane; e < 16 * PADP; e += 32)
+            *reinterpret_cast<unsigned *>(xa + (e / PADP) * SX + F + 2 * (e % PADP)) = 0u;
+        __syncwarp();
+        // ---- layer 1: [16 x 16 KS1] x [16 KS1 x 64]; the hidden tile reuses the input rows
+        float acc[Gm::NT3 > 8 ? Gm::NT3 : 8][4];
+        bias_init(acc, bias, 8, lane);
+        warp_gemm<Gm::KS1, 8>(xa, SX, w1t, SX, acc, lane);
+        __syncwarp();
+        gelu_rows(acc, xa, lane);
+        __syncwarp();
+        // ---- layer 2
+        bias_init(acc, bias + 64, 8, lane);
+        warp_gemm<4, 8>(xa, SH, w2t, SH, acc, lane);
+        __syncwarp();
+        gelu_rows(acc, xa, lane);
+        __syncwarp();
+        // ---- layer 3 with the folded projection (hi + lo)
+        bias_init(acc, bias + 128, Gm::NT3, lane);
+        warp_gemm<4, Gm::NT3>(xa, SH, w3h, SH, acc, lane);
+        warp_gemm<4, Gm::NT3>(xa, SH, w3l, SH, acc, lane);
+        // ---- update: f_i += n0 w_i y'_i; rows g (u = 0, 1) and g + 8 (u = 2, 3)
+        const float na = __shfl_sync(0xffffffffu, n0, g), nb = __shfl_sync(0xffffffffu, n0, g + 8);
+        float *fa = cur + wid * 16 + g;
+#pragma unroll
+        for (int nt = 0; nt < Gm::NT3; ++nt) {
+            const int c = nt * 8 + 2 * t;
+            const float2 w2 = *reinterpret_cast<const float2 *>(wq + c);
+            fa[c * LDF] = fmaf(na * w2.x, acc[nt][0], fa[c * LDF]);
+            fa[(c + 1) * LDF] = fmaf(na * w2.y, acc[nt][1], fa[(c + 1) * LDF]);
+            fa[c * LDF + 8] = fmaf(nb * w2.x, acc[nt][2], fa[c * LDF + 8]);
+            fa[(c + 1) * LDF + 8] = fmaf(nb * w2.y, acc[nt][3], fa[(c + 1) * LDF + 8]);
+        }
+        __syncthreads();
+        store_tile<VEC>(cur, f, S, site0, NPOP);
+        __syncthreads(); // the buffer is refilled by the next iteration's copy
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+using TcKernel = void (*)(Net, CoarseTab, float *, long long, float);
+
+// the specialisations: (N, K) with N_pop a multiple of 8 and at most 80 outputs
+template <int VEC>
+TcKernel tc_kernel(int N, int K, size_t *smem)
+{
+    if (N == 2 && K == 24) { *smem = TcGeom<2, 24>::TOTAL; return apply_tc_kernel<2, 24, VEC>; }
+    if (N == 2 && K == 16) { *smem = TcGeom<2, 16>::TOTAL; return apply_tc_kernel<2, 16, VEC>; }
+    if (N == 3 && K == 16) { *smem = TcGeom<3, 16>::TOTAL; return apply_tc_kernel<3, 16, VEC>; }
+    return nullptr;
+}
+
 } // namespace
 
 // ==================================================================== host side
@@ -398,6 +773,7 @@ struct rlbm_closure {
     float *d_tab = nullptr;         // p0 | c | s | w | Ainv
     float *d_loss = nullptr;
     int adam_t = 0;
+    bool simt_apply = false;
     std::string err;
     size_t off_W1, off_b1, off_W2, off_b2, off_W3, off_b3;
 };
@@ -459,6 +835,17 @@ size_t fwd_smem(const rlbm_closure *c, bool with_x)
 }
 
 size_t bwd_smem(const rlbm_closure *c) { return (size_t(MAXO) + 2 * H + c->F) * TS * 4; }
+
+bool tc_attributes(const rlbm_closure *c)
+{
+    for (int v = 0; v < 2; ++v) {
+        size_t smem = 0;
+        TcKernel k = v ? tc_kernel<4>(c->N, c->K, &smem) : tc_kernel<1>(c->N, c->K, &smem);
+        if (k && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return false;
+    }
+    return true;
+}
 
 rlbm_status refresh_bf16(rlbm_closure *c)
 {
@@ -578,7 +965,8 @@ rlbm_status rlbm_closure_create(rlbm_closure_t **out, int order_N, int angles_K,
     if (cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(c, false)) != cudaSuccess ||
         cudaFuncSetAttribute(mlp_forward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(c, false)) != cudaSuccess ||
         cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(c, true)) != cudaSuccess ||
-        cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(c)) != cudaSuccess)
+        cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(c)) != cudaSuccess ||
+        !tc_attributes(c))
         return bail(cfail(c, RLBM_ERR_CUDA, "shared-memory attribute failed"));
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(cfail(c, RLBM_ERR_CUDA, "sync failed"));
     *out = c;
@@ -754,9 +1142,30 @@ rlbm_status rlbm_closure_train_step(rlbm_closure_t *c, const float *d_x, const f
 rlbm_status rlbm_closure_apply_buffer(rlbm_closure_t *c, float *d_f, long long sites, double kn)
 {
     if (!c || !d_f || sites < 1) return cfail(c, RLBM_ERR_ARG, "bad arguments");
+    size_t smem = 0;
+    const bool vec = sites % 4 == 0 && reinterpret_cast<uintptr_t>(d_f) % 16 == 0;
+    TcKernel k = c->simt_apply ? nullptr : vec ? tc_kernel<4>(c->N, c->K, &smem) : tc_kernel<1>(c->N, c->K, &smem);
+    if (k) {
+        // tensor-core path: a persistent grid of one CTA per SM
+        int dev = 0, sms = 0;
+        CL_CUDA(c, cudaGetDevice(&dev));
+        CL_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long tiles = (sites + TC_SITES - 1) / TC_SITES;
+        const int grid = int(std::min<long long>(sms, tiles));
+        k<<<grid, TC_WARPS * 32, smem, c->stream>>>(net_of(c), tab_of(c), d_f, sites, float(kn));
+        CL_CUDA(c, cudaGetLastError());
+        return RLBM_OK;
+    }
     const int grid = int(std::min<long long>(4096, (sites + 127) / 128));
     apply_kernel<<<grid, 128, fwd_smem(c, true), c->stream>>>(net_of(c), tab_of(c), d_f, sites, float(kn));
     CL_CUDA(c, cudaGetLastError());
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_closure_set_apply_path(rlbm_closure_t *c, int tensor_cores)
+{
+    if (!c) return cfail(nullptr, RLBM_ERR_ARG, "NULL closure");
+    c->simt_apply = !tensor_cores;
     return RLBM_OK;
 }
 

@@ -40,7 +40,7 @@ EXPORTS = [
     "rlbm_closure_param_count", "rlbm_closure_get_params", "rlbm_closure_set_params",
     "rlbm_closure_features", "rlbm_closure_target", "rlbm_closure_restrict",
     "rlbm_closure_forward", "rlbm_closure_work_floats", "rlbm_closure_gradient",
-    "rlbm_closure_train_step", "rlbm_closure_apply_buffer",
+    "rlbm_closure_train_step", "rlbm_closure_apply_buffer", "rlbm_closure_set_apply_path",
 ]
 
 
@@ -187,6 +187,8 @@ def lib(path: str = LIB_PATH):
                                           _vp, fp]
     L.rlbm_closure_apply_buffer.restype = st
     L.rlbm_closure_apply_buffer.argtypes = [_vp, _vp, ll, ctypes.c_double]
+    L.rlbm_closure_set_apply_path.restype = st
+    L.rlbm_closure_set_apply_path.argtypes = [_vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -593,6 +595,9 @@ class Closure:
 
     def apply_buffer(self, f_ptr: int, sites: int, kn: float):
         self._check(lib().rlbm_closure_apply_buffer(self._c, _vp(f_ptr), int(sites), float(kn)))
+
+    def set_apply_path(self, tensor_cores: bool):
+        self._check(lib().rlbm_closure_set_apply_path(self._c, 1 if tensor_cores else 0))
 
     def apply(self, sim, kn: float):
         """Correct the current populations of a coarse FP32 Simulation in place."""

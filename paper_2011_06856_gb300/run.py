@@ -2,10 +2,13 @@
 
     python -m paper_2011_06856_gb300.run --nx 8192 --ny 4 --N 3 --K 64 \\
         --precision fp32 --kn 0.01 --steps 100 [--tile-p 32] [--autotune] [--out fields.npz]
+        [--closure]
 
 The initial state is the shock tube of the named workload shape (a 2D
 four-quadrant Riemann problem when --riemann is given).  Prints the tiling
-used and the step count; with --out writes n, eps, T, U^0, U^x, U^y.
+used and the step count; with --out writes n, eps, T, U^0, U^x, U^y.  With
+--closure (FP32) the learned correction, with its initial random weights,
+is applied after every step.
 Used for ncu captures of single kernels.
 """
 from __future__ import annotations
@@ -36,6 +39,7 @@ def main(argv=None):
     ap.add_argument("--per-tile", action="store_true", help="do not use the TMA-staged kernel")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--closure", action="store_true", help="fused learned correction after each step")
     a = ap.parse_args(argv)
     if a.tile_p:
         os.environ["RLBM_TILE_P"] = str(a.tile_p)
@@ -46,11 +50,19 @@ def main(argv=None):
         fl = W.workload_fields(W.WORKLOADS["riemann2d_2048_N2K48"], a.nx, a.ny)
     else:
         fl = W.shock_tube(a.nx, a.ny)
-    sim = R.Simulation(a.nx, a.ny, a.N, a.K, W.tau_from_kn(a.kn, a.nx), a.precision, a.bcx, bcy)
+    cl = R.Closure(a.N, a.K, seed=1) if a.closure else None
+    sim = R.Simulation(a.nx, a.ny, a.N, a.K, W.tau_from_kn(a.kn, a.nx), a.precision, a.bcx, bcy,
+                       stream=cl.stream if cl else None)
     sim.init_fields(fl)
     if a.autotune:
         sim.autotune(8)
-    sim.step(a.steps)
+    if cl:
+        for _ in range(a.steps):
+            sim.step(1)
+            cl.apply(sim, a.kn)
+        cl.stream.synchronize()
+    else:
+        sim.step(a.steps)
     sim.sync()
     print(f"tiling P={sim.tile_populations} kernel={'tma' if sim.uses_tma else 'per-tile'} "
           f"steps={sim.steps_done} launches={sim.kernel_launches}")

@@ -33,8 +33,8 @@ def ref_params(cl):
     return [bf16(p[0]), p[1], bf16(p[2]), p[3], bf16(p[4]), p[5]]
 
 
-def random_coarse_populations(sites, seed):
-    q = O.Quadrature(N, K)
+def random_coarse_populations(sites, seed, n=N, k=K):
+    q = O.Quadrature(n, k)
     g = np.random.default_rng(seed)
     f = np.stack([q.feq(g.uniform(0.3, 1), g.uniform(0.5, 1.1), g.uniform(-0.2, 0.2),
                         g.uniform(-0.2, 0.2)) for _ in range(sites)], axis=1)
@@ -92,10 +92,23 @@ def test_forward_and_gradient_match_reference():
     assert np.abs(grad - flat).max() < 1e-3 * np.abs(flat).max()
 
 
-def test_apply_conserves_and_matches_reference():
-    cl = R.Closure(N, K, seed=3)
-    sites = 333
-    q, f = random_coarse_populations(sites, 6)
+def bf16_forward(params, X):
+    """The network with its layer inputs rounded to BF16, as the tensor-core kernel
+    feeds them (features, GELU outputs); FP64 otherwise."""
+    W1, b1, W2, b2, W3, b3 = params
+    h1 = bf16(C.gelu(bf16(X) @ W1 + b1))
+    h2 = bf16(C.gelu(h1 @ W2 + b2))
+    return h2 @ W3 + b3
+
+
+def apply_case(sites, seed, tensor_cores, n=N, k=K, ref_bf16=None):
+    """Apply the correction to random off-equilibrium populations through the
+    chosen kernel (the tensor-core one falls back to the other for rules it has
+    no specialisation for); returns the reference next to the result."""
+    ref_bf16 = tensor_cores if ref_bf16 is None else ref_bf16
+    cl = R.Closure(n, k, seed=3)
+    cl.set_apply_path(tensor_cores)
+    q, f = random_coarse_populations(sites, seed, n, k)
     fd = torch.tensor(f, dtype=torch.float32, device="cuda").contiguous()
     f32 = fd.double().cpu().numpy()
     cl.apply_buffer(fd.data_ptr(), sites, 0.3)
@@ -104,12 +117,39 @@ def test_apply_conserves_and_matches_reference():
     # reference: features -> network -> denormalise -> projection -> add
     params = ref_params(cl)
     X = C.features(f32, q.p0, q.vx, q.vy, q.w, 0.3)
-    y, _ = C.mlp_forward(params, X)
+    y = bf16_forward(params, X) if ref_bf16 else C.mlp_forward(params, X)[0]
     n0 = q.p0 @ f32
     d = y.T * q.w[:, None] * n0[None, :]
     ref = f32 + C.conservative_projection(d, q.p0, q.vx, q.vy, q.w)
-    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-7 * np.abs(f32).max())
     Cm = np.stack([q.p0, q.p0 ** 2, q.p0 ** 2 * q.vx, q.p0 ** 2 * q.vy])
+    return q, f32, got, ref, d, Cm
+
+
+@pytest.mark.parametrize("n,k", [(2, 24), (2, 20)])
+def test_apply_conserves_and_matches_reference(n, k):
+    """One thread per site, FP32 activations: FP32 rounding only.  (2, 20) has no
+    tensor-core specialisation (60 populations) and takes this kernel by default."""
+    q, f32, got, ref, d, Cm = apply_case(333, 6, k == 20, n, k, ref_bf16=False)
+    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-7 * np.abs(f32).max())
+    before, after = Cm @ f32, Cm @ got
+    assert np.abs(after - before).max() < 2e-6 * np.abs(before).max()
+
+
+@pytest.mark.parametrize("n,k,sites", [(2, 24, 16), (2, 24, 333), (2, 24, 5000), (2, 24, 40000),
+                                       (2, 24, 45001), (2, 16, 3001), (3, 16, 4000)])
+def test_apply_tensor_cores_conserves_and_matches_reference(n, k, sites):
+    """BF16 mma.sync path (192-site CTA tiles; ragged last tile; site counts that
+    are not a multiple of 4 take the 4-byte copy form; above 152 x 192 sites the
+    CTAs loop over tiles through both population buffers; the conservative
+    projection folded into the last layer) against the reference with the same
+    BF16 roundings of the layer inputs.  A rare flip of one BF16 rounding (FP32
+    vs FP64 sums on either side of a rounding boundary) moves an output by about
+    a BF16 ulp of one activation times a weight, hence the absolute term in
+    units of the correction."""
+    q, f32, got, ref, d, Cm = apply_case(sites, 6 + sites, True, n, k)
+    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=2e-3 * np.abs(d).max())
+    med = np.median(np.abs(got - ref)) / np.abs(d).max()
+    assert med < 1e-4
     before, after = Cm @ f32, Cm @ got
     assert np.abs(after - before).max() < 2e-6 * np.abs(before).max()
 
