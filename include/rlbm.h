@@ -153,16 +153,31 @@ rlbm_status rlbm_sync(rlbm_t *h);
 long long rlbm_kernel_launches(const rlbm_t *h);
 
 /* Which step kernel the handle uses: 1 = persistent TMA-staged kernel
- * (row pitch a multiple of 16 bytes and nx >= one box), 0 = per-tile kernel. */
+ * (row pitch a multiple of 16 bytes and nx >= one box), 2 = two sites per
+ * lane (64-site tiles, packed f32x2 arithmetic; FP32 arithmetic, finite tau,
+ * nx even, K a multiple of P in {16, 24, 32}) with its first pass staged
+ * through shared memory by cp.async (row pitch a multiple of 16 bytes),
+ * 3 = the same with plain loads, 0 = per-tile kernel. */
 int rlbm_step_kernel_variant(const rlbm_t *h);
+
+/* Select the tiling and step kernel directly (no counterpart in the paper:
+ * a performance choice that does not change what a step computes beyond
+ * rounding).  P = populations per warp (one of 8, 12, 16, 24, 32, 48, 64 that
+ * fits K and N); kind = 0 per-tile, 1 persistent TMA-staged, 2 two sites per
+ * lane (staged), 3 two sites per lane (plain loads).  RLBM_ERR_UNSUPPORTED if
+ * the kernel is not possible for this handle (the handle then keeps tiling P
+ * with the per-tile kernel); RLBM_ERR_ARG for a kind outside 0..3.
+ * Synchronises the stream; the state is kept. */
+rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind);
 
 /* Populations per warp of the handle's current tiling (the tile is 32 sites
  * of one row x all populations; G = ceil(K / P) (N+1) warps per CTA). */
 int rlbm_tile_populations(const rlbm_t *h);
 
 /* Autotuner: time every compiled tiling of the step kernel (P populations per
- * warp in {8,12,16,24,32,48,64} that fits K and N, each with the persistent
- * TMA-staged kernel where possible and with the per-tile kernel) on this
+ * warp in {8,12,16,24,32,48,64} that fits K and N, each with the two-sites-
+ * per-lane kernel and the persistent TMA-staged kernel where possible and
+ * with the per-tile kernel) on this
  * handle's own problem, launches_per_trial launches each, and keep the
  * fastest.  The populations of the current state are not modified (trials
  * read the current buffer and write the other one).  Results are cached per

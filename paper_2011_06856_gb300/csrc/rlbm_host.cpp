@@ -208,6 +208,8 @@ struct rlbm {
     int sm_count = 0;
     bool stall_next = false; // test hook: next launch waits for bytes that never arrive
     bool no_tma = false;     // tiling choice: per-tile kernel even where TMA is possible
+    bool use_pair = false;   // two-sites-per-lane step kernel (rlbm_pair.cuh)
+    bool pair_plain = false; // ... with plain loads in pass 1 instead of the cp.async staging
     std::string err;
 };
 
@@ -364,12 +366,29 @@ rlbm_status build_tables(rlbm_t *h)
     const size_t o_shell = align256(pop.size() * rs);
     const size_t o_rt = o_shell + align256(shell.size() * ls);
     const size_t o_mask = o_rt + align256(rt.size() * ls);
-    const size_t total = o_mask + align256(masks.size() * sizeof(unsigned long long));
+    // pair table of the two-sites-per-lane kernel (FP32 arithmetic only):
+    // (|c|,|c|,|s|,|s|), (c,c,s,s), (cc,cc,cs,cs), then E_0..E_2N in pairs
+    const int PQ = N + 4;
+    std::vector<double> ptab;
+    if (!r64) {
+        ptab.assign(size_t(npop) * PQ * 4, 0.0);
+        for (int i = 0; i < npop; ++i) {
+            const double *t = &pop[size_t(i) * TW];
+            double *o = &ptab[size_t(i) * PQ * 4];
+            const double v[12] = {std::fabs(t[0]), std::fabs(t[0]), std::fabs(t[1]), std::fabs(t[1]),
+                                  t[0], t[0], t[1], t[1], t[2], t[2], t[3], t[3]};
+            for (int u = 0; u < 12; ++u) o[u] = v[u];
+            for (int e = 0; e <= 2 * N; ++e) o[12 + 2 * e] = o[12 + 2 * e + 1] = t[4 + e];
+        }
+    }
+    const size_t o_pair = o_mask + align256(masks.size() * sizeof(unsigned long long));
+    const size_t total = o_pair + align256(ptab.size() * 4);
     std::vector<unsigned char> blob(total, 0);
     if (r64) put<double>(blob, o_pop, pop); else put<float>(blob, o_pop, pop);
     if (l64) { put<double>(blob, o_shell, shell); put<double>(blob, o_rt, rt); }
     else { put<float>(blob, o_shell, shell); put<float>(blob, o_rt, rt); }
     std::memcpy(blob.data() + o_mask, masks.data(), masks.size() * sizeof(unsigned long long));
+    put<float>(blob, o_pair, ptab);
 
     if (h->d_tabs) { // re-tiling: replace the tables
         RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -415,6 +434,7 @@ rlbm_status build_tables(rlbm_t *h)
     a.shelltab = (const unsigned char *)h->d_tabs + o_shell;
     a.rtab = (const unsigned char *)h->d_tabs + o_rt;
     a.masks = reinterpret_cast<const unsigned long long *>((const unsigned char *)h->d_tabs + o_mask);
+    a.pairtab = ptab.empty() ? nullptr : (const unsigned char *)h->d_tabs + o_pair;
     a.status = h->d_status;
     a.ctr = reinterpret_cast<unsigned *>(h->d_status + 1);
     return RLBM_OK;
@@ -444,6 +464,46 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     case RLBM_FP16_DEV:
     case RLBM_FP16_NORM: e = rlbmk::launch_f16(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
     default: e = rlbmk::launch_bf16(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
+    }
+    if (e == cudaSuccess) ++h->launches;
+    return e;
+}
+
+// The two-sites-per-lane step kernel applies to FP32 arithmetic with a
+// collision, an even row length, K a multiple of P and P in {16, 24, 32}.
+bool pair_possible(const rlbm_t *h, int P)
+{
+    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau)) return false;
+    if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
+    if (!(P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
+    const int G = (h->K / P) * (h->N + 1);
+    return G <= rlbmk::kMaxWarps &&
+           rlbmk::pair_smem_bytes(h->N, G, true, int(storage_size(h->prec)), h->grid.ny > 1) <= 200 * 1024;
+}
+
+// The staged form copies 16-byte chunks: rows must be a whole number of
+// chunks and the buffers 16-byte aligned.
+bool pair_async(const rlbm_t *h)
+{
+    const size_t es = storage_size(h->prec);
+    return !h->pair_plain && (size_t(h->grid.nx) * es) % 16 == 0 &&
+           reinterpret_cast<uintptr_t>(h->buf) % 16 == 0;
+}
+
+cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
+{
+    const dim3 grid((h->grid.nx + rlbmk::kPairSites - 1) / rlbmk::kPairSites, h->grid.ny);
+    const dim3 block(32, h->G);
+    const bool two_d = h->grid.ny > 1, async = pair_async(h);
+    const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G, async, int(storage_size(h->prec)), two_d);
+    cudaError_t e;
+    switch (h->prec) {
+    case RLBM_FP32: e = rlbmk::launch_pair_f32(h->N, h->P, two_d, async, grid, block, smem, h->stream, a); break;
+    case RLBM_FP16_DEV:
+    case RLBM_FP16_NORM:
+        e = rlbmk::launch_pair_f16(h->N, h->P, two_d, async, grid, block, smem, h->stream, a);
+        break;
+    default: e = rlbmk::launch_pair_bf16(h->N, h->P, two_d, async, grid, block, smem, h->stream, a); break;
     }
     if (e == cudaSuccess) ++h->launches;
     return e;
@@ -479,6 +539,7 @@ cudaError_t launch_step(rlbm_t *h, int from)
     rlbmk::KernelArgs a = h->base;
     a.fin = buffer(h, from);
     a.fout = buffer(h, 1 - from);
+    if (h->use_pair) return launch_pair(h, a);
     return launch(h, rlbmk::MODE_STEP, a);
 }
 
@@ -611,8 +672,10 @@ rlbm_status validate_fields_ptrs(rlbm_t *h, const void *a, const void *b, const 
     return RLBM_OK;
 }
 
-// Switch the handle to another tiling (P populations per warp, TMA or not).
-rlbm_status retile(rlbm_t *h, int P, bool tma)
+// Switch the handle to another tiling: P populations per warp and the step
+// kernel kind (0 per-tile, 1 persistent TMA-staged where possible, 2 two
+// sites per lane where possible; otherwise the per-tile kernel).
+rlbm_status retile(rlbm_t *h, int P, int kind)
 {
     RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
     for (auto &g : h->graph)
@@ -620,10 +683,18 @@ rlbm_status retile(rlbm_t *h, int P, bool tma)
     h->P = P;
     h->Gs = (h->K + P - 1) / P;
     h->G = h->Gs * (h->N + 1);
-    h->no_tma = !tma;
+    h->no_tma = kind != 1;
+    h->use_pair = (kind == 2 || kind == 3) && pair_possible(h, P);
+    h->pair_plain = kind == 3;
     rlbm_status st = build_tables(h);
     if (st) return st;
     return setup_tma(h);
+}
+
+int kernel_kind(const rlbm_t *h)
+{
+    if (h->use_pair) return pair_async(h) ? 2 : 3;
+    return h->use_tma ? 1 : 0;
 }
 
 struct TuneKey {
@@ -633,7 +704,7 @@ struct TuneKey {
         return std::memcmp(this, &o, sizeof(TuneKey)) < 0;
     }
 };
-struct TuneChoice { int P; bool tma; float ms; };
+struct TuneChoice { int P; int kind; float ms; };
 
 std::map<TuneKey, TuneChoice> &tune_cache()
 {
@@ -917,7 +988,35 @@ rlbm_status rlbm_sync(rlbm_t *h)
 
 long long rlbm_kernel_launches(const rlbm_t *h) { return h ? h->launches : -1; }
 
-int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? (h->use_tma ? 1 : 0) : -1; }
+int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? kernel_kind(h) : -1; }
+
+rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (kind < 0 || kind > 3) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0..3 (got %d)", kind);
+    static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
+    bool ok = false;
+    for (int v : sizes) ok = ok || v == P;
+    const int gs = ok ? (h->K + P - 1) / P : 0;
+    if (!ok || gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K)
+        return fail(h, RLBM_ERR_UNSUPPORTED, "no compiled tiling with P=%d for N=%d, K=%d", P, h->N, h->K);
+    if ((kind == 2 || kind == 3) && !pair_possible(h, P)) {
+        rlbm_status st0 = retile(h, P, 0);
+        if (st0) return st0;
+        return fail(h, RLBM_ERR_UNSUPPORTED,
+                    "two-sites-per-lane kernel needs FP32 arithmetic, tau finite, nx even, P in {16,24,32} "
+                    "dividing K");
+    }
+    rlbm_status st = retile(h, P, kind);
+    if (st) return st;
+    if (kernel_kind(h) != kind) {
+        st = retile(h, P, 0);
+        if (st) return st;
+        return fail(h, RLBM_ERR_UNSUPPORTED, kind == 1 ? "TMA-staged kernel not possible for this grid and tiling"
+                                                       : "staged form needs rows of whole 16-byte chunks");
+    }
+    return RLBM_OK;
+}
 
 int rlbm_tile_populations(const rlbm_t *h) { return h ? h->P : -1; }
 
@@ -932,25 +1031,25 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
         auto it = tune_cache().find(key);
         if (it != tune_cache().end()) {
             if (best_ms) *best_ms = it->second.ms;
-            if (it->second.P == h->P && it->second.tma == h->use_tma) return RLBM_OK;
-            return retile(h, it->second.P, it->second.tma);
+            if (it->second.P == h->P && it->second.kind == kernel_kind(h)) return RLBM_OK;
+            return retile(h, it->second.P, it->second.kind);
         }
     }
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
     cudaEvent_t e0, e1;
     RLBM_CUDA(h, cudaEventCreate(&e0));
     RLBM_CUDA(h, cudaEventCreate(&e1));
-    TuneChoice best{h->P, h->use_tma, 1e30f};
+    TuneChoice best{h->P, kernel_kind(h), 1e30f};
     const long long launches0 = h->launches;
     rlbm_status st = RLBM_OK;
     for (int P : sizes) {
         const int gs = (h->K + P - 1) / P;
         if (gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K) continue;
         if (P > 2 * h->K) continue;
-        for (int tma = 1; tma >= 0 && st == RLBM_OK; --tma) {
-            st = retile(h, P, tma != 0);
+        for (int kind = 3; kind >= 0 && st == RLBM_OK; --kind) {
+            st = retile(h, P, kind);
             if (st) break;
-            if (tma && !h->use_tma) continue; // TMA not possible for this tiling
+            if (kernel_kind(h) != kind) continue; // kernel kind not possible for this tiling
             // time cur -> other launches (the state in buffer cur is not modified)
             cudaError_t e = launch_step(h, h->cur);
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -961,14 +1060,14 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) { st = cuda_fail(h, e, "autotune trial"); break; }
             ms /= launches_per_trial;
-            if (ms < best.ms) best = TuneChoice{P, h->use_tma, ms};
+            if (ms < best.ms) best = TuneChoice{P, kind, ms};
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->launches = launches0; // trial launches are not steps
     if (st) return st;
-    st = retile(h, best.P, best.tma);
+    st = retile(h, best.P, best.kind);
     if (st) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -1252,7 +1351,7 @@ rlbm_status rlbm_batch_create(rlbm_batch_t **out, const rlbm_problem *p, int cou
         const int gs = batch_tiling(order_N, p[i].angles_K, 1, P) ? 1 : 2;
         batch_tiling(order_N, p[i].angles_K, gs, P);
         h->no_tma = true;
-        st = retile(h, P, false);
+        st = retile(h, P, 0);
         if (st) return bail(bfail(b, st, "problem %d: %s", i, h->err.c_str()));
         off += align256(bytes);
     }
@@ -1390,7 +1489,7 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *bes
             int P;
             if (gs == cur_gs || !batch_tiling(b->N, K, gs, P)) continue;
             for (int i : c.second) {
-                st = retile(b->probs[i], P, false);
+                st = retile(b->probs[i], P, 0);
                 if (st) break;
             }
             float ms = 0.f;
@@ -1401,7 +1500,7 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *bes
             int P;
             batch_tiling(b->N, K, best_gs, P);
             for (int i : c.second)
-                if (!st) st = retile(b->probs[i], P, false);
+                if (!st) st = retile(b->probs[i], P, 0);
         }
     }
     cudaEventDestroy(e0);

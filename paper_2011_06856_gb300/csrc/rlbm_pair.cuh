@@ -1,0 +1,461 @@
+// Two-sites-per-lane form of the fused RLBM step (arXiv 2011.06856, Sec. 2.2)
+// for FP32 arithmetic (FP32, FP16 or BF16 storage).
+//
+// A CTA owns 64 consecutive sites of one grid row and all N_pop populations
+// of them; lane l holds sites x0 + 2l and x0 + 2l + 1 as one packed pair, so
+// that every per-population operation is one Blackwell f32x2 instruction
+// (add / sub / mul / fma .f32x2) for two sites, every population-table load
+// serves two sites, and the centre values of a pair are one 8-byte load.
+// Warp g owns PP populations of energy shell r = g / Gs.
+//
+//   pass 1  bilinear pull (Eqs. streaming, interpolation): the pair pulled
+//           from x - sgn(v_x) is (f[x0+2l-1], f[x0+2l]) or (f[x0+2l+1],
+//           f[x0+2l+2]), i.e. one neighbour value plus one of the centre
+//           pair; five per-shell angular sums S0, Sc, Ss, Scc, Scs of f*;
+//   site    two warps (one site per lane) fold the sums of all warps into
+//           N^a and T^ab (Eq. discrete_sum_moments), solve the Landau frame
+//           (landau_fast), and form the truncated-equilibrium coefficients of
+//           every shell (Eqs. mj-projection-coefficients,
+//           mj-feq-expansion-truncated) once per site, into shared memory;
+//   pass 2  f^eq_i and the relaxation f <- f* + omega_i (f^eq - f*)
+//           (Eq. discrete-rbe), one paired store per population.
+//
+// Per-population constants come from a pair table (each constant twice, so a
+// 16-byte load gives two packed operands): (|c|,|c|,|s|,|s|), (c,c,s,s),
+// (cc,cc,cs,cs), then the 2N+1 equilibrium basis values E_t in pairs.
+#pragma once
+
+#include "rlbm_device.cuh"
+
+namespace rlbmk {
+
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b)
+{
+    unsigned long long ua, ub, ud;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+
+// paired storage access: two consecutive sites (the first at an even index)
+template <class St> struct PIo;
+// Loads are volatile asm so that the compiler issues a chunk's loads in
+// program order before the arithmetic that uses them (many in flight).
+template <> struct PIo<float> {
+    static __device__ __forceinline__ float2 ld2(const float *p)
+    {
+        float2 v;
+        asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ float ld1(const float *p)
+    {
+        float v;
+        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ void st2(float *p, float2 v, unsigned &) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <> struct PIo<__half> {
+    static __device__ __forceinline__ float2 ld2(const __half *p)
+    {
+        unsigned u;
+        asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(p));
+        __half2 h;
+        memcpy(&h, &u, 4);
+        return __half22float2(h);
+    }
+    static __device__ __forceinline__ float ld1(const __half *p)
+    {
+        unsigned short u;
+        asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(u) : "l"(p));
+        return __half2float(__ushort_as_half(u));
+    }
+    static __device__ __forceinline__ void st2(__half *p, float2 v, unsigned &rng)
+    {
+        // stochastic rounding of both values (13 dropped mantissa bits)
+        const __half h0 = __float2half_rz(__uint_as_float(__float_as_uint(v.x) + (lcg_next(rng) >> 19)));
+        const __half h1 = __float2half_rz(__uint_as_float(__float_as_uint(v.y) + (lcg_next(rng) >> 19)));
+        const unsigned u = unsigned(__half_as_ushort(h0)) | (unsigned(__half_as_ushort(h1)) << 16);
+        *reinterpret_cast<unsigned *>(p) = u;
+    }
+};
+template <> struct PIo<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p)
+    {
+        unsigned u;
+        asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(p));
+        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+    }
+    static __device__ __forceinline__ float ld1(const __nv_bfloat16 *p)
+    {
+        unsigned short u;
+        asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(u) : "l"(p));
+        return __uint_as_float(unsigned(u) << 16);
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16 *p, float2 v, unsigned &rng)
+    {
+        // stochastic rounding of both values (16 dropped mantissa bits)
+        const unsigned b0 = __float_as_uint(v.x) + (lcg_next(rng) >> 16);
+        const unsigned b1 = __float_as_uint(v.y) + (lcg_next(rng) >> 16);
+        *reinterpret_cast<unsigned *>(p) = (b0 >> 16) | (b1 & 0xFFFF0000u);
+    }
+};
+
+// The per-site part for site s of the tile (FP32): moments from the warps'
+// angular sums, Landau frame, and the equilibrium coefficients of all N+1
+// shells (the boosted-direction sums acc are shared by the shells), written
+// to sres[(r NC + t) 64 + s]; then U^a / tau at rows (N+1) NC + 0..2.
+template <int N>
+__device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float *red, int G, int s, bool act,
+                                                float *sres)
+{
+    constexpr int NC = 2 * N + 1;
+    const float *sh = reinterpret_cast<const float *>(a.shelltab);
+    float m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = a.off_f[u];
+#pragma unroll
+    for (int rr = 0; rr <= N; ++rr) {
+        float p0 = 0.f, pc = 0.f, ps = 0.f, pcc = 0.f, pcs = 0.f;
+        for (int qq = 0; qq < a.Gs; ++qq) {
+            const int w = rr * a.Gs + qq;
+            p0 += red[(0 * G + w) * kPairSites + s];
+            pc += red[(1 * G + w) * kPairSites + s];
+            ps += red[(2 * G + w) * kPairSites + s];
+            pcc += red[(3 * G + w) * kPairSites + s];
+            pcs += red[(4 * G + w) * kPairSites + s];
+        }
+        const float f1 = __ldg(sh + 2 * rr), f2v = __ldg(sh + 2 * rr + 1);
+        m[0] += f1 * p0;
+        m[1] += f1 * pc;
+        m[2] += f1 * ps;
+        m[3] += f2v * p0;
+        m[4] += f2v * pc;
+        m[5] += f2v * ps;
+        m[6] += f2v * pcc;
+        m[7] += f2v * pcs;
+    }
+    float n, eps, U0, Ux, Uy;
+    const bool ok = landau_fast<float>(m, n, eps, U0, Ux, Uy);
+    const float T = eps / (2.f * n);
+    if (!ok && act) atomicOr(a.status, 1);
+    // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
+    float accr[N + 1][N + 1], acci[N + 1][N + 1];
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+        for (int k = 0; k <= N; ++k) { accr[mm][k] = 0.f; acci[mm][k] = 0.f; }
+    const float inv1g = 1.f / (1.f + U0);
+#pragma unroll
+    for (int j = 0; j <= N; ++j) {
+        const float cj = a.smp_cf[j], sj = a.smp_sf[j];
+        const float un = Ux * cj + Uy * sj;
+        const float q0 = U0 + un;
+        const float h = 1.f + un * inv1g;
+        const float zr = cj + Ux * h, zi = sj + Uy * h;
+        float qp[N + 1], pr[N + 1], pi[N + 1];
+        qp[0] = 1.f;
+        pr[0] = 1.f;
+        pi[0] = 0.f;
+#pragma unroll
+        for (int t = 1; t <= N; ++t) {
+            qp[t] = qp[t - 1] * q0;
+            pr[t] = pr[t - 1] * zr - pi[t - 1] * zi;
+            pi[t] = pr[t - 1] * zi + pi[t - 1] * zr;
+        }
+#pragma unroll
+        for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                accr[mm][k] += qp[k - mm] * pr[mm];
+                acci[mm][k] += qp[k - mm] * pi[mm];
+            }
+    }
+    float tk[N + 1];
+    tk[0] = n / T;
+#pragma unroll
+    for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
+    const float *rtab = reinterpret_cast<const float *>(a.rtab);
+#pragma unroll
+    for (int r = 0; r <= N; ++r) {
+        const float *rt = rtab + r * (N + 1) * (N + 1);
+#pragma unroll
+        for (int mm = 0; mm <= N; ++mm) {
+            float cre = 0.f, cim = 0.f;
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float wgt = __ldg(rt + mm * (N + 1) + k) * tk[k];
+                cre += wgt * accr[mm][k];
+                cim += wgt * acci[mm][k];
+            }
+            if (mm == 0) {
+                sres[(r * NC) * kPairSites + s] = cre - a.feq_off_f;
+            } else {
+                sres[(r * NC + 2 * mm - 1) * kPairSites + s] = cre;
+                sres[(r * NC + 2 * mm) * kPairSites + s] = cim;
+            }
+        }
+    }
+    const float itau = a.inv_tau_f;
+    sres[((N + 1) * NC + 0) * kPairSites + s] = U0 * itau;
+    sres[((N + 1) * NC + 1) * kPairSites + s] = Ux * itau;
+    sres[((N + 1) * NC + 2) * kPairSites + s] = Uy * itau;
+}
+
+// Asynchronous staging of pass 1 (ASYNC): each warp streams its own
+// populations through a ring of kPairDepth slots in shared memory, a slot
+// holding kPairChunk populations x (1 or 2) rows x (64 + 2 HX) sites, HX = one
+// 16-byte chunk of halo on each side; rows are the site row y and, in 2D, the
+// row y - sgn(v_y) the population pulls from (boundary-mapped).  The copies
+// are cp.async 16-byte chunks (zero-filled outside the row), two slots ahead
+// of the arithmetic; the waits are cp.async group waits (no spin loop).  Halo
+// values outside the grid (x0 = 0, or x0 + 64 > nx) are loaded from their
+// boundary-mapped source directly.
+template <class St> struct PairStage {
+    static constexpr int HX = 16 / int(sizeof(St));      // halo elements per side
+    static constexpr int BW = kPairSites + 2 * HX;       // staged row width (elements)
+    static constexpr int C16 = BW * int(sizeof(St)) / 16; // 16-byte chunks per row
+    static constexpr int ROWB = BW * int(sizeof(St));     // bytes per staged row
+};
+
+__device__ __forceinline__ unsigned smem_u32p(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+template <class St> __device__ __forceinline__ float2 lds2(const St *p);
+template <> __device__ __forceinline__ float2 lds2<float>(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+template <> __device__ __forceinline__ float2 lds2<__half>(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+template <> __device__ __forceinline__ float2 lds2<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const unsigned u = *reinterpret_cast<const unsigned *>(p);
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+template <class St> __device__ __forceinline__ float lds1(const St *p);
+template <> __device__ __forceinline__ float lds1<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float lds1<__half>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float lds1<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(*p);
+}
+
+// St: storage type; N: quadrature order; PP: populations per warp (K is a
+// multiple of PP); TWO_D: ny > 1; ASYNC: staged pass 1 (nx a multiple of one
+// 16-byte chunk, buffers 16-byte aligned).  Requires nx even (paired access)
+// and a collision (tau finite).
+template <class St, int N, int PP, bool TWO_D, bool ASYNC>
+__global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelArgs a)
+{
+    constexpr int NC = 2 * N + 1;
+    constexpr int PQ = N + 4; // float4 per population in the pair table
+    constexpr int R = TWO_D ? 2 : 1;
+    using Sg = PairStage<St>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x, g = threadIdx.y, G = blockDim.y;
+    const int x0 = blockIdx.x * kPairSites;
+    const int xl = x0 + 2 * lane;
+    const bool act = xl < a.nx;
+    const int xa = act ? xl : a.nx - 2;
+    const int y = blockIdx.y;
+    const int r = g / a.Gs, q = g % a.Gs;
+    const int i0 = r * a.K + q * PP;
+    const long long S = a.S;
+    const St *fin = reinterpret_cast<const St *>(a.fin);
+    St *fout = reinterpret_cast<St *>(a.fout);
+    float *red = reinterpret_cast<float *>(smem_raw); // [5][G][64]
+    float *sres = red + 5 * G * kPairSites;           // [(N+1) NC + 3][64]
+    const float4 *tb = reinterpret_cast<const float4 *>(a.pairtab) + size_t(i0) * PQ;
+
+    const int xm = bc_index(xa - 1, a.nx, a.bcx), xp = bc_index(xa + 2, a.nx, a.bcx);
+    const int ym = TWO_D ? bc_index(y - 1, a.ny, a.bcy) : y;
+    const int yp = TWO_D ? bc_index(y + 1, a.ny, a.bcy) : y;
+    const unsigned long long mx = __ldg(a.masks + 2 * g), my = __ldg(a.masks + 2 * g + 1);
+    const St *base = fin + (long long)i0 * S + (long long)y * a.nx;
+    const long long dym = (long long)(ym - y) * a.nx, dyp = (long long)(yp - y) * a.nx;
+
+    float2 fs[PP];
+    float2 s0 = f2(0.f, 0.f), sc = f2(0.f, 0.f), ss = f2(0.f, 0.f), scc = f2(0.f, 0.f), scs = f2(0.f, 0.f);
+    // streamed pair of population k from its centre pair C, neighbour e (row 1),
+    // and, in 2D, C2, e2 of the pull row; accumulates the angular sums
+    auto stream_pop = [&](int k, float2 C, float e, float2 C2, float e2) {
+        const float4 t0 = __ldg(tb + k * PQ), t1 = __ldg(tb + k * PQ + 1), t2 = __ldg(tb + k * PQ + 2);
+        const bool px = (mx >> k) & 1ull; // v_x >= 0: pull from x - 1
+        const float2 B = px ? f2(e, C.x) : f2(C.y, e);
+        const float2 ac = f2(t0.x, t0.y);
+        float2 v = __ffma2_rn(ac, f2sub(B, C), C);
+        if (TWO_D) {
+            const float2 B2 = px ? f2(e2, C2.x) : f2(C2.y, e2);
+            const float2 hi = __ffma2_rn(ac, f2sub(B2, C2), C2);
+            v = __ffma2_rn(f2(t0.z, t0.w), f2sub(hi, v), v);
+        }
+        fs[k] = v;
+        s0 = __fadd2_rn(s0, v);
+        sc = __ffma2_rn(f2(t1.x, t1.y), v, sc);
+        ss = __ffma2_rn(f2(t1.z, t1.w), v, ss);
+        scc = __ffma2_rn(f2(t2.x, t2.y), v, scc);
+        scs = __ffma2_rn(f2(t2.z, t2.w), v, scs);
+    };
+
+    if (ASYNC) {
+        constexpr int CHA = kPairChunk, E = CHA * R * Sg::C16, SLOT = CHA * R * Sg::ROWB;
+        unsigned char *stg = smem_raw + pair_stage_offset(N, G) + size_t(g) * kPairDepth * SLOT;
+        const bool left = (x0 == 0) && lane == 0, right = xa + 2 >= a.nx; // halo from outside the grid
+        auto issue = [&](int c) {
+            if (c < PP / CHA) {
+                unsigned char *slot = stg + (c % kPairDepth) * SLOT;
+                for (int e = lane; e < E; e += 32) {
+                    const int kk = e / (R * Sg::C16), rem = e % (R * Sg::C16);
+                    const int row = rem / Sg::C16, j = rem % Sg::C16;
+                    const int k = c * CHA + kk;
+                    const long long dy = row == 0 ? 0 : (((my >> k) & 1ull) ? dym : dyp);
+                    const int x = x0 - Sg::HX + j * (16 / int(sizeof(St)));
+                    const bool ok = x >= 0 && x < a.nx;
+                    const St *src = ok ? base + (long long)k * S + dy + x : fin;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                                     smem_u32p(slot + (kk * R + row) * Sg::ROWB + j * 16)),
+                                 "l"(src), "r"(ok ? 16 : 0)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+#pragma unroll
+        for (int c = 0; c < kPairDepth - 1; ++c) issue(c);
+#pragma unroll
+        for (int c = 0; c < PP / CHA; ++c) {
+            issue(c + kPairDepth - 1);
+            asm volatile("cp.async.wait_group %0;" ::"n"(kPairDepth - 1) : "memory");
+            __syncwarp();
+            const St *slot = reinterpret_cast<const St *>(stg + (c % kPairDepth) * SLOT);
+#pragma unroll
+            for (int kk = 0; kk < CHA; ++kk) {
+                const int k = c * CHA + kk;
+                const bool px = (mx >> k) & 1ull;
+                const St *ra = slot + (kk * R) * Sg::BW + Sg::HX + 2 * lane;
+                const float2 C = lds2<St>(ra);
+                float e = lds1<St>(ra + (px ? -1 : 2));
+                float2 C2 = f2(0.f, 0.f);
+                float e2 = 0.f;
+                if (TWO_D) {
+                    const St *rb = ra + Sg::BW;
+                    C2 = lds2<St>(rb);
+                    e2 = lds1<St>(rb + (px ? -1 : 2));
+                }
+                if ((left && px) || (right && !px)) {
+                    const St *pk = base + (long long)k * S;
+                    const int xs = px ? xm : xp;
+                    e = PIo<St>::ld1(pk + xs);
+                    if (TWO_D) e2 = PIo<St>::ld1(pk + (((my >> k) & 1ull) ? dym : dyp) + xs);
+                }
+                stream_pop(k, C, e, C2, e2);
+            }
+            __syncwarp(); // the slot is refilled by the next issue
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else {
+        constexpr int CH = TWO_D ? 4 : 8;
+        static_assert(PP % CH == 0, "chunking");
+#pragma unroll
+        for (int c0 = 0; c0 < PP; c0 += CH) {
+            float2 ca[CH], cb[TWO_D ? CH : 1];
+            float ea[CH], eb[TWO_D ? CH : 1];
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                const int k = c0 + kk;
+                const St *pk = base + (long long)k * S;
+                const int xs = ((mx >> k) & 1ull) ? xm : xp;
+                ca[kk] = PIo<St>::ld2(pk + xa);
+                ea[kk] = PIo<St>::ld1(pk + xs);
+                if (TWO_D) {
+                    const long long dy = ((my >> k) & 1ull) ? dym : dyp;
+                    cb[kk] = PIo<St>::ld2(pk + dy + xa);
+                    eb[kk] = PIo<St>::ld1(pk + dy + xs);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk)
+                stream_pop(c0 + kk, ca[kk], ea[kk], TWO_D ? cb[kk] : f2(0.f, 0.f), TWO_D ? eb[kk] : 0.f);
+        }
+    }
+    float2 *red2 = reinterpret_cast<float2 *>(red);
+    red2[(0 * G + g) * 32 + lane] = s0;
+    red2[(1 * G + g) * 32 + lane] = sc;
+    red2[(2 * G + g) * 32 + lane] = ss;
+    red2[(3 * G + g) * 32 + lane] = scc;
+    red2[(4 * G + g) * 32 + lane] = scs;
+    __syncthreads();
+    if (g < 2) {
+        const int s = g * 32 + lane;
+        pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
+    }
+    __syncthreads();
+
+    const float2 *sres2 = reinterpret_cast<const float2 *>(sres);
+    float2 cr[NC];
+#pragma unroll
+    for (int t = 0; t < NC; ++t) cr[t] = sres2[(r * NC + t) * 32 + lane];
+    const float2 o0 = sres2[((N + 1) * NC + 0) * 32 + lane];
+    const float2 o1 = sres2[((N + 1) * NC + 1) * 32 + lane];
+    const float2 o2 = sres2[((N + 1) * NC + 2) * 32 + lane];
+    const float2 no1 = f2(-o1.x, -o1.y), no2 = f2(-o2.x, -o2.y);
+    constexpr bool kSR = sizeof(St) == 2;
+    unsigned rng = 0;
+    if (kSR) rng = mix32(unsigned(y * a.nx + xa) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
+    St *ob = fout + (long long)i0 * S + (long long)y * a.nx + xa;
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+        const float4 t1 = __ldg(tb + k * PQ + 1);
+        float2 feq = f2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < NC; t += 2) {
+            const float4 e = __ldg(tb + k * PQ + 3 + t / 2);
+            feq = (t == 0) ? __fmul2_rn(cr[0], f2(e.x, e.y)) : __ffma2_rn(cr[t], f2(e.x, e.y), feq);
+            if (t + 1 < NC) feq = __ffma2_rn(cr[t + 1], f2(e.z, e.w), feq);
+        }
+        const float2 om = __ffma2_rn(no2, f2(t1.z, t1.w), __ffma2_rn(no1, f2(t1.x, t1.y), o0));
+        const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
+        if (act) PIo<St>::st2(ob + (long long)k * S, out, rng);
+    }
+    if (kSR) {
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) advance_launch_counter(a.ctr, gridDim.x * gridDim.y);
+    }
+}
+
+template <class St, int N, int PP>
+static cudaError_t launch_pair_np(bool two_d, bool async, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  const KernelArgs &a)
+{
+    void (*k)(const KernelArgs) =
+        two_d ? (async ? rlbm_pair_kernel<St, N, PP, true, true> : rlbm_pair_kernel<St, N, PP, true, false>)
+              : (async ? rlbm_pair_kernel<St, N, PP, false, true> : rlbm_pair_kernel<St, N, PP, false, false>);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class St>
+static cudaError_t launch_pair_t(int N, int PP, bool two_d, bool async, dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, const KernelArgs &a)
+{
+#define RLBM_PAIR_CASE(n, p)                                                                                 \
+    if (N == n && PP == p) return launch_pair_np<St, n, p>(two_d, async, grid, block, smem, st, a);
+    RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
+    RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
+#undef RLBM_PAIR_CASE
+    return cudaErrorInvalidValue;
+}
+
+} // namespace rlbmk

@@ -31,7 +31,7 @@ EXPORTS = [
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
     "rlbm_step_kernel_variant", "rlbm_set_wait_limit", "rlbm_test_stall_next_step",
-    "rlbm_tile_populations", "rlbm_autotune",
+    "rlbm_tile_populations", "rlbm_autotune", "rlbm_set_tiling",
     "rlbm_batch_arena_bytes", "rlbm_batch_create", "rlbm_batch_destroy", "rlbm_batch_last_error",
     "rlbm_batch_count", "rlbm_batch_problem", "rlbm_batch_step", "rlbm_batch_sync",
     "rlbm_batch_kernel_launches", "rlbm_batch_autotune", "rlbm_batch_set_wait_limit",
@@ -123,6 +123,8 @@ def lib(path: str = LIB_PATH):
     L.rlbm_test_stall_next_step.argtypes = [_vp]
     L.rlbm_tile_populations.restype = ctypes.c_int
     L.rlbm_tile_populations.argtypes = [_vp]
+    L.rlbm_set_tiling.restype = st
+    L.rlbm_set_tiling.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.rlbm_autotune.restype = st
     L.rlbm_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     _pp = ctypes.POINTER(Problem)
@@ -341,6 +343,20 @@ class Simulation:
     @property
     def tile_populations(self) -> int:
         return lib().rlbm_tile_populations(self._h)
+
+    KERNELS = ("per-tile", "tma", "pair", "pair-plain")
+
+    @property
+    def step_kernel(self) -> str:
+        """'per-tile', 'tma', 'pair' (two sites per lane, staged first pass) or
+        'pair-plain' (two sites per lane, plain loads)."""
+        return self.KERNELS[lib().rlbm_step_kernel_variant(self._h)]
+
+    def set_tiling(self, P: int, kind: str):
+        """Select P populations per warp and the step kernel (one of KERNELS);
+        raises RLBMError if that kernel is not possible here."""
+        k = self.KERNELS.index(kind)
+        _check(lib().rlbm_set_tiling(self._h, int(P), k), self._h)
 
     def autotune(self, launches_per_trial: int = 8) -> float:
         """Pick the fastest compiled tiling for this problem (see rlbm_autotune);

@@ -37,6 +37,8 @@ def main(argv=None):
     ap.add_argument("--bcy", type=int, default=None)
     ap.add_argument("--tile-p", type=int, default=None, help="populations per warp")
     ap.add_argument("--per-tile", action="store_true", help="do not use the TMA-staged kernel")
+    ap.add_argument("--kernel", choices=("per-tile", "tma", "pair", "pair-plain"), default=None,
+                    help="step kernel (with --tile-p as its populations per warp)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--out", default=None)
     ap.add_argument("--closure", action="store_true", help="fused learned correction after each step")
@@ -54,6 +56,8 @@ def main(argv=None):
     sim = R.Simulation(a.nx, a.ny, a.N, a.K, W.tau_from_kn(a.kn, a.nx), a.precision, a.bcx, bcy,
                        stream=cl.stream if cl else None)
     sim.init_fields(fl)
+    if a.kernel:
+        sim.set_tiling(a.tile_p or sim.tile_populations, a.kernel)
     if a.autotune:
         sim.autotune(8)
     if cl:
@@ -64,7 +68,7 @@ def main(argv=None):
     else:
         sim.step(a.steps)
     sim.sync()
-    print(f"tiling P={sim.tile_populations} kernel={'tma' if sim.uses_tma else 'per-tile'} "
+    print(f"tiling P={sim.tile_populations} kernel={sim.step_kernel} "
           f"steps={sim.steps_done} launches={sim.kernel_launches}")
     if a.out:
         m = sim.moments()

@@ -1,0 +1,193 @@
+"""GPU parity of the two-sites-per-lane step kernel (packed f32x2 arithmetic,
+64-site tiles, per-site solve once per site) against the FP64 oracle and
+against the per-tile kernel, through the C ABI.
+
+FP32 tolerance as in test_gpu_parity: max(1e-5, 4e-7 omega_max steps);
+16-bit storage: the TOL of test_gpu_parity (stochastic rounding, u of the
+format), and agreement with the per-tile kernel within 2e-3 (the rounding
+draws differ between the kernels).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2011_06856_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2011_06856_gb300 import build as B  # noqa: E402
+from paper_2011_06856_gb300 import rlbm as R  # noqa: E402
+
+B.build()
+
+TOL = {"fp16": 1e-3, "bf16": 8e-3, "fp16n": 1e-3, "bf16n": 8e-3}
+
+
+def fp32_tol(tau, steps, umax=1.2):
+    return max(1e-5, 4e-7 * umax / tau * steps)
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+ES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp16n": 2, "bf16n": 2}
+
+
+def staged_ok(nx, precision):
+    """The staged first pass copies whole 16-byte chunks of a row."""
+    return (nx * ES[precision]) % 16 == 0
+
+
+def pair_sim(nx, ny, N, K, tau, precision, bcx, bcy, P, kind=None):
+    kind = kind or ("pair" if staged_ok(nx, precision) else "pair-plain")
+    sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
+    sim.set_tiling(P, kind)
+    assert sim.step_kernel == kind and sim.tile_populations == P
+    return sim
+
+
+@pytest.mark.parametrize("kind", ["pair", "pair-plain"])
+@pytest.mark.parametrize("nx,ny,N,K,P,bcx,bcy", [
+    (128, 1, 2, 16, 16, W.BC_COPYOUT, W.BC_PERIODIC),   # 1D, two full tiles
+    (100, 1, 3, 64, 32, W.BC_PERIODIC, W.BC_PERIODIC),  # ragged last tile (36 of 64 sites)
+    (2, 3, 2, 24, 24, W.BC_PERIODIC, W.BC_PERIODIC),    # one pair per row: both neighbours wrap
+    (4, 4, 2, 24, 24, W.BC_COPYOUT, W.BC_PERIODIC),     # one 16-byte chunk per row
+    (66, 5, 2, 48, 16, W.BC_COPYOUT, W.BC_COPYOUT),     # 2D copy-out corners, 2 sites in the last tile
+    (68, 5, 2, 48, 16, W.BC_PERIODIC, W.BC_COPYOUT),    # 4 sites in the last tile, halo wraps
+    (70, 6, 3, 32, 32, W.BC_PERIODIC, W.BC_PERIODIC),   # 2D periodic wrap
+    (64, 4, 2, 48, 24, W.BC_PERIODIC, W.BC_COPYOUT),
+    (132, 3, 2, 16, 16, W.BC_COPYOUT, W.BC_COPYOUT),
+    (196, 3, 3, 16, 16, W.BC_COPYOUT, W.BC_PERIODIC),
+])
+def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy, kind):
+    if kind == "pair" and not staged_ok(nx, "fp32"):
+        pytest.skip("row pitch not a whole number of 16-byte chunks")
+    steps, tau = 9, 2.5
+    fl = W.random_fields(nx, ny, seed=nx + 7 * ny + K)
+    q = O.Quadrature(N, K)
+    f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
+    ref, flagged = q.run(f0, tau, steps, bcx, bcy)
+    assert flagged == 0
+    sim = pair_sim(nx, ny, N, K, tau, "fp32", bcx, bcy, P, kind)
+    sim.init_fields(fl)
+    sim.step(steps)
+    got = sim.get_populations().astype(np.float64)
+    assert relerr(got, ref) < fp32_tol(tau, steps)
+    mac, _ = q.macro(ref)
+    m = sim.moments()
+    for k in range(4):
+        assert relerr(m[k], mac[k]) < fp32_tol(tau, steps), k
+
+
+@pytest.mark.parametrize("P,kind", [(16, "pair"), (32, "pair"), (32, "pair-plain")])
+def test_pair_kernel_full_size_8192x4_one_step(P, kind):
+    """The benchmark problem (8192 x 4, N=3, K=64, FP32) one step at full size."""
+    nx, ny, N, K = 8192, 4, 3, 64
+    tau = W.tau_from_kn(0.1, nx)
+    fl = W.shock_tube(nx, ny)
+    sim = pair_sim(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, P, kind)
+    sim.init_fields(fl)
+    sim.step(40)
+    f40 = sim.get_populations().astype(np.float64)
+    sim.step(1)
+    got = sim.get_populations().astype(np.float64)
+    q = O.Quadrature(N, K)
+    ref, _ = q.run(f40, tau, 1, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert relerr(got, ref) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16n", "bf16n", "fp16", "bf16"])
+def test_pair_and_per_tile_kernels_agree(precision):
+    nx, ny, N, K = 96, 7, 2, 48
+    fl = W.random_fields(nx, ny, seed=5)
+    out = {}
+    for kind in ("pair", "pair-plain", "per-tile"):
+        s = R.Simulation(nx, ny, N, K, 3.0, precision, W.BC_COPYOUT, W.BC_COPYOUT)
+        s.set_tiling(24, kind)
+        s.init_fields(fl)
+        s.step(6)
+        out[kind] = s.moments()
+    tol = 1e-6 if precision == "fp32" else 2e-3
+    assert relerr(out["pair"], out["per-tile"]) < tol
+    assert relerr(out["pair-plain"], out["per-tile"]) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp16n", "bf16n"])
+def test_pair_kernel_16bit_riemann_matches_oracle(precision):
+    """Four-quadrant Riemann problem, N=2 x K=48 at 96^2, Kn = 0.05, 150 steps."""
+    nx = ny = 96
+    N, K, steps = 2, 48, 150
+    fl = W.workload_fields(W.WORKLOADS["riemann2d_2048_N2K48"], nx, ny)
+    tau = W.tau_from_kn(0.05, nx)
+    q = O.Quadrature(N, K)
+    ref, flagged = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    assert flagged == 0
+    mac, _ = q.macro(ref)
+    sim = pair_sim(nx, ny, N, K, tau, precision, W.BC_COPYOUT, W.BC_COPYOUT, 24)
+    sim.init_fields(fl)
+    sim.step(steps)
+    m = sim.moments()
+    for k in (0, 1):  # n, eps
+        assert relerr(m[k], mac[k]) <= TOL[precision], (k, relerr(m[k], mac[k]))
+
+
+def test_pair_kernel_graph_replay_and_resume_are_exact():
+    """32-step graph replays equal single launches bit for bit (FP32), and a
+    16-bit run resumed from a checkpoint continues bit-identically (the launch
+    counter that seeds the rounding is restored with the step count)."""
+    nx, ny, N, K = 128, 6, 2, 16
+    fl = W.random_fields(nx, ny, seed=3)
+    a = pair_sim(nx, ny, N, K, 3.0, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, 16)
+    b = pair_sim(nx, ny, N, K, 3.0, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, 16)
+    a.init_fields(fl)
+    b.init_fields(fl)
+    a.step(40)
+    for _ in range(40):
+        b.step(1)
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    c = pair_sim(nx, ny, N, K, 3.0, "fp16n", W.BC_COPYOUT, W.BC_PERIODIC, 16)
+    c.init_fields(fl)
+    c.step(10)
+    ck = c.get_populations()
+    c.step(7)
+    d = pair_sim(nx, ny, N, K, 3.0, "fp16n", W.BC_COPYOUT, W.BC_PERIODIC, 16)
+    d.set_populations(ck, step=10)
+    d.step(7)
+    np.testing.assert_array_equal(c.get_populations(), d.get_populations())
+
+
+def test_pair_kernel_refused_where_it_does_not_apply():
+    cases = [
+        dict(nx=64, ny=2, precision="fp64", tau=2.0, P=16),          # FP64 arithmetic
+        dict(nx=65, ny=2, precision="fp32", tau=2.0, P=16),          # odd row length
+        dict(nx=64, ny=2, precision="fp32", tau=float("inf"), P=16),  # no collision
+        dict(nx=64, ny=2, precision="fp32", tau=2.0, P=12),          # P not compiled for it
+        dict(nx=66, ny=2, precision="fp32", tau=2.0, P=16, kind="pair"),  # row not whole 16-byte chunks
+    ]
+    for c in cases:
+        s = R.Simulation(c["nx"], c["ny"], 2, 48, c["tau"], c["precision"], W.BC_COPYOUT, W.BC_PERIODIC)
+        for kind in ([c["kind"]] if "kind" in c else ["pair", "pair-plain"]):
+            with pytest.raises(R.RLBMError):
+                s.set_tiling(c["P"], kind)
+            assert s.step_kernel == "per-tile"
+        s.close()
+
+
+def test_autotune_with_pair_candidates_stays_at_parity():
+    nx, ny, N, K, steps, tau = 256, 4, 3, 32, 7, 2.0
+    fl = W.random_fields(nx, ny, seed=31)
+    sim = R.Simulation(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC)
+    sim.init_fields(fl)
+    f0 = sim.get_populations()
+    sim.autotune(3)
+    np.testing.assert_array_equal(sim.get_populations(), f0)
+    sim.step(steps)
+    q = O.Quadrature(N, K)
+    ref, _ = q.run(f0.astype(np.float64), tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert relerr(sim.get_populations().astype(np.float64), ref) < fp32_tol(tau, steps)
+    print("autotuned:", sim.step_kernel, sim.tile_populations)
