@@ -155,18 +155,17 @@ long long rlbm_kernel_launches(const rlbm_t *h);
 /* Which step kernel the handle uses: 1 = persistent TMA-staged kernel
  * (row pitch a multiple of 16 bytes and nx >= one box), 2 = two sites per
  * lane (64-site tiles, packed f32x2 arithmetic; FP32 arithmetic, finite tau,
- * nx even, K a multiple of P in {16, 24, 32}) with its first pass staged
- * through shared memory by cp.async (row pitch a multiple of 16 bytes),
- * 3 = the same with plain loads, 0 = per-tile kernel. */
+ * nx even, K a multiple of P in {8, 12, 16, 24, 32}, at most 16 warps),
+ * 0 = per-tile kernel. */
 int rlbm_step_kernel_variant(const rlbm_t *h);
 
 /* Select the tiling and step kernel directly (no counterpart in the paper:
  * a performance choice that does not change what a step computes beyond
  * rounding).  P = populations per warp (one of 8, 12, 16, 24, 32, 48, 64 that
  * fits K and N); kind = 0 per-tile, 1 persistent TMA-staged, 2 two sites per
- * lane (staged), 3 two sites per lane (plain loads).  RLBM_ERR_UNSUPPORTED if
- * the kernel is not possible for this handle (the handle then keeps tiling P
- * with the per-tile kernel); RLBM_ERR_ARG for a kind outside 0..3.
+ * lane.  RLBM_ERR_UNSUPPORTED if the kernel is not possible for this handle
+ * (the handle then keeps tiling P with the per-tile kernel); RLBM_ERR_ARG for
+ * a kind outside 0..2.
  * Synchronises the stream; the state is kept. */
 rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind);
 
@@ -235,28 +234,42 @@ int rlbm_batch_count(const rlbm_batch_t *b);
 rlbm_t *rlbm_batch_problem(rlbm_batch_t *b, int i);
 
 /* Advance every problem nsteps time steps (Sec. 2.2, the same fused step as
- * rlbm_step) with ONE persistent cooperative kernel launch, replayed from a
- * CUDA graph captured per nsteps.  Work units (tiles of 32 sites of one row
- * of one problem) are taken dynamically from a counter; time steps are
- * separated by a grid barrier whose waits are bounded (RLBM_ERR_TIMEOUT at
- * the next rlbm_batch_sync).  Asynchronous. */
+ * rlbm_step).  Mode 0 (the default): ONE persistent cooperative kernel
+ * launch, replayed from a CUDA graph captured per nsteps; work units (tiles
+ * of 32 sites of one row of one problem) are taken dynamically from a
+ * counter; time steps are separated by a grid barrier whose waits are
+ * bounded (RLBM_ERR_TIMEOUT at the next rlbm_batch_sync).  Mode 1: the
+ * problems are independent, so each runs its own single-problem step kernel
+ * (its own tiling), all nsteps steps back to back, on one of 16 streams
+ * forked from and joined back to the batch stream (problems balanced over
+ * the streams by size).  Asynchronous. */
 rlbm_status rlbm_batch_step(rlbm_batch_t *b, int nsteps);
+
+/* Select the execution mode (0 persistent launch, 1 stream pool; no
+ * counterpart in the paper: a scheduling choice that does not change what a
+ * step computes beyond rounding).  Re-tiles every problem; synchronises.
+ * RLBM_ERR_ARG for another value. */
+rlbm_status rlbm_batch_set_mode(rlbm_batch_t *b, int mode);
+int rlbm_batch_mode(const rlbm_batch_t *b);
 
 /* Wait for the stream; reports a barrier timeout or a non-physical cell. */
 rlbm_status rlbm_batch_sync(rlbm_batch_t *b);
 long long rlbm_batch_kernel_launches(const rlbm_batch_t *b);
 
-/* Autotuner of the batched tile shapes: for each class of problems with the
- * same K, time the batched kernel with one and with two warps per energy
- * shell (P populations per warp, 1 or 2 tiles per CTA), steps_per_trial
- * steps each, and keep the faster.  It initialises every problem with a
- * uniform rest state first, so call it before rlbm_init.  best_ms (may be
- * NULL): time of one batched step with the chosen shapes. */
+/* Autotuner of the batched form: for each class of problems with the same K,
+ * time the persistent kernel with one and with two warps per energy shell
+ * (P populations per warp, 1 or 2 tiles per CTA), then the stream-pool mode
+ * with each two-sites-per-lane tiling P in {8, 12, 16, 24, 32} that the
+ * class allows, steps_per_trial steps each; keep the faster mode with its
+ * best tilings.  It initialises every problem with a uniform rest state
+ * first, so call it before rlbm_init.  best_ms (may be NULL): time of one
+ * batched step with the chosen mode and shapes. */
 rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *best_ms);
 
 /* Bound of each grid-barrier wait in SM cycles (default 4e9) and a test hook
  * making the next rlbm_batch_step's barrier wait for one CTA too many, so
- * that every wait runs out and RLBM_ERR_TIMEOUT is reported. */
+ * that every wait runs out and RLBM_ERR_TIMEOUT is reported (mode 0 only:
+ * RLBM_ERR_UNSUPPORTED in mode 1, which has no barrier). */
 rlbm_status rlbm_batch_set_wait_limit(rlbm_batch_t *b, long long cycles);
 rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b);
 

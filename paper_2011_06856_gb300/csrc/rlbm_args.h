@@ -44,21 +44,12 @@ struct KernelArgs {
 
 __host__ __device__ constexpr int tab_width(int N) { return ((2 * N + 5) + 3) / 4 * 4; }
 
-// Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory:
-// angular sums [5][G][64] and per-site coefficients [(N+1)(2N+1) + 3][64]
-// (FP32), then, for the staged form, per warp kPairDepth slots of kPairChunk
-// populations x rows x (64 + 2 x 16 bytes of halo).
+// Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory
+// (angular sums [5][G][64], per-site coefficients [(N+1)(2N+1) + 3][64], FP32).
 constexpr int kPairSites = 64;
-constexpr int kPairChunk = 4;
-constexpr int kPairDepth = 3;
-__host__ __device__ constexpr size_t pair_stage_offset(int N, int G)
+__host__ __device__ constexpr size_t pair_smem_bytes(int N, int G)
 {
-    return ((size_t(5) * G + size_t(N + 1) * (2 * N + 1) + 3) * kPairSites * 4 + 15) / 16 * 16;
-}
-__host__ __device__ constexpr size_t pair_smem_bytes(int N, int G, bool async, int elem_bytes, bool two_d)
-{
-    return pair_stage_offset(N, G) +
-           (async ? size_t(G) * kPairDepth * kPairChunk * (two_d ? 2 : 1) * (kPairSites * elem_bytes + 32) : 0);
+    return (size_t(5) * G + size_t(N + 1) * (2 * N + 1) + 3) * kPairSites * 4;
 }
 
 // Arguments of the persistent TMA-staged step kernel.
@@ -109,11 +100,10 @@ cudaError_t launch_f16(int mode, int N, int P, bool two_d, bool full, dim3 grid,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_bf16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t st, const KernelArgs &a);
-// Two-sites-per-lane step kernel (rlbm_pair.cuh): 64-site tiles, PP in {16, 24, 32};
-// async: pass 1 staged through shared memory with cp.async.
+// Two-sites-per-lane step kernel (rlbm_pair.cuh): 64-site tiles, PP in {8, 12, 16, 24, 32}.
 #define RLBM_DECLARE_PAIR(name)                                                                          \
-    cudaError_t launch_pair_##name(int N, int PP, bool two_d, bool async, dim3 grid, dim3 block,         \
-                                   size_t smem, cudaStream_t st, const KernelArgs &a);
+    cudaError_t launch_pair_##name(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,       \
+                                   cudaStream_t st, const KernelArgs &a);
 RLBM_DECLARE_PAIR(f32)
 RLBM_DECLARE_PAIR(f16)
 RLBM_DECLARE_PAIR(bf16)

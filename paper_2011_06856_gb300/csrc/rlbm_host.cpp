@@ -209,7 +209,6 @@ struct rlbm {
     bool stall_next = false; // test hook: next launch waits for bytes that never arrive
     bool no_tma = false;     // tiling choice: per-tile kernel even where TMA is possible
     bool use_pair = false;   // two-sites-per-lane step kernel (rlbm_pair.cuh)
-    bool pair_plain = false; // ... with plain loads in pass 1 instead of the cp.async staging
     std::string err;
 };
 
@@ -470,40 +469,27 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
 }
 
 // The two-sites-per-lane step kernel applies to FP32 arithmetic with a
-// collision, an even row length, K a multiple of P and P in {16, 24, 32}.
+// collision, an even row length, K a multiple of P and P in {8, 12, 16, 24, 32}.
 bool pair_possible(const rlbm_t *h, int P)
 {
     if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau)) return false;
     if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
-    if (!(P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
-    const int G = (h->K / P) * (h->N + 1);
-    return G <= rlbmk::kMaxWarps &&
-           rlbmk::pair_smem_bytes(h->N, G, true, int(storage_size(h->prec)), h->grid.ny > 1) <= 200 * 1024;
-}
-
-// The staged form copies 16-byte chunks: rows must be a whole number of
-// chunks and the buffers 16-byte aligned.
-bool pair_async(const rlbm_t *h)
-{
-    const size_t es = storage_size(h->prec);
-    return !h->pair_plain && (size_t(h->grid.nx) * es) % 16 == 0 &&
-           reinterpret_cast<uintptr_t>(h->buf) % 16 == 0;
+    if (!(P == 8 || P == 12 || P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
+    return (h->K / P) * (h->N + 1) <= rlbmk::kMaxWarps;
 }
 
 cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
 {
     const dim3 grid((h->grid.nx + rlbmk::kPairSites - 1) / rlbmk::kPairSites, h->grid.ny);
     const dim3 block(32, h->G);
-    const bool two_d = h->grid.ny > 1, async = pair_async(h);
-    const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G, async, int(storage_size(h->prec)), two_d);
+    const bool two_d = h->grid.ny > 1;
+    const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G);
     cudaError_t e;
     switch (h->prec) {
-    case RLBM_FP32: e = rlbmk::launch_pair_f32(h->N, h->P, two_d, async, grid, block, smem, h->stream, a); break;
+    case RLBM_FP32: e = rlbmk::launch_pair_f32(h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
     case RLBM_FP16_DEV:
-    case RLBM_FP16_NORM:
-        e = rlbmk::launch_pair_f16(h->N, h->P, two_d, async, grid, block, smem, h->stream, a);
-        break;
-    default: e = rlbmk::launch_pair_bf16(h->N, h->P, two_d, async, grid, block, smem, h->stream, a); break;
+    case RLBM_FP16_NORM: e = rlbmk::launch_pair_f16(h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    default: e = rlbmk::launch_pair_bf16(h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
     }
     if (e == cudaSuccess) ++h->launches;
     return e;
@@ -684,18 +670,13 @@ rlbm_status retile(rlbm_t *h, int P, int kind)
     h->Gs = (h->K + P - 1) / P;
     h->G = h->Gs * (h->N + 1);
     h->no_tma = kind != 1;
-    h->use_pair = (kind == 2 || kind == 3) && pair_possible(h, P);
-    h->pair_plain = kind == 3;
+    h->use_pair = kind == 2 && pair_possible(h, P);
     rlbm_status st = build_tables(h);
     if (st) return st;
     return setup_tma(h);
 }
 
-int kernel_kind(const rlbm_t *h)
-{
-    if (h->use_pair) return pair_async(h) ? 2 : 3;
-    return h->use_tma ? 1 : 0;
-}
+int kernel_kind(const rlbm_t *h) { return h->use_pair ? 2 : (h->use_tma ? 1 : 0); }
 
 struct TuneKey {
     int nx, ny, N, K, prec, bcx, bcy, site64;
@@ -993,27 +974,26 @@ int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? kernel_kind(h) : -1; 
 rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
 {
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
-    if (kind < 0 || kind > 3) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0..3 (got %d)", kind);
+    if (kind < 0 || kind > 2) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0, 1 or 2 (got %d)", kind);
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
     bool ok = false;
     for (int v : sizes) ok = ok || v == P;
     const int gs = ok ? (h->K + P - 1) / P : 0;
     if (!ok || gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K)
         return fail(h, RLBM_ERR_UNSUPPORTED, "no compiled tiling with P=%d for N=%d, K=%d", P, h->N, h->K);
-    if ((kind == 2 || kind == 3) && !pair_possible(h, P)) {
+    if (kind == 2 && !pair_possible(h, P)) {
         rlbm_status st0 = retile(h, P, 0);
         if (st0) return st0;
         return fail(h, RLBM_ERR_UNSUPPORTED,
-                    "two-sites-per-lane kernel needs FP32 arithmetic, tau finite, nx even, P in {16,24,32} "
-                    "dividing K");
+                    "two-sites-per-lane kernel needs FP32 arithmetic, tau finite, nx even, P in "
+                    "{8,12,16,24,32} dividing K and at most 16 warps");
     }
     rlbm_status st = retile(h, P, kind);
     if (st) return st;
     if (kernel_kind(h) != kind) {
         st = retile(h, P, 0);
         if (st) return st;
-        return fail(h, RLBM_ERR_UNSUPPORTED, kind == 1 ? "TMA-staged kernel not possible for this grid and tiling"
-                                                       : "staged form needs rows of whole 16-byte chunks");
+        return fail(h, RLBM_ERR_UNSUPPORTED, "TMA-staged kernel not possible for this grid and tiling");
     }
     return RLBM_OK;
 }
@@ -1046,7 +1026,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
         const int gs = (h->K + P - 1) / P;
         if (gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K) continue;
         if (P > 2 * h->K) continue;
-        for (int kind = 3; kind >= 0 && st == RLBM_OK; --kind) {
+        for (int kind = 2; kind >= 0 && st == RLBM_OK; --kind) {
             st = retile(h, P, kind);
             if (st) break;
             if (kernel_kind(h) != kind) continue; // kernel kind not possible for this tiling
@@ -1122,6 +1102,14 @@ struct rlbm_batch {
     bool stall_next = false;
     std::map<int, cudaGraphExec_t> graphs; // by nsteps
     long long launches = 0, steps = 0;
+    // execution mode: 0 = one persistent cooperative launch per call (tilings
+    // batch_P); 1 = every problem runs its own step kernel (tilings solo_P /
+    // solo_kind), all its steps back to back, on one of a pool of streams
+    int mode = 0;
+    std::vector<int> batch_P, solo_P, solo_kind, lane_of;
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> pool_ev;
+    cudaEvent_t fork_ev = nullptr;
     std::string err;
 };
 
@@ -1275,6 +1263,101 @@ rlbm_status batch_check(rlbm_batch *b)
     return RLBM_OK;
 }
 
+constexpr int kBatchStreams = 16;
+
+// Smallest two-sites-per-lane tiling of a problem (more, lighter warps per
+// SM), else the per-tile kernel with the default tiling.
+void solo_default(const rlbm_t *h, int &P, int &kind)
+{
+    static const int sizes[] = {8, 12, 16, 24, 32};
+    for (int v : sizes)
+        if (pair_possible(h, v)) { P = v; kind = 2; return; }
+    int gs = 0;
+    choose_tiling(h->N, h->K, P, gs);
+    kind = 0;
+}
+
+rlbm_status batch_sync_all(rlbm_batch *b)
+{
+    for (cudaStream_t s : b->pool) BATCH_CUDA(b, cudaStreamSynchronize(s));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    return RLBM_OK;
+}
+
+// Switch the execution mode, re-tiling every problem accordingly.
+rlbm_status batch_set_mode(rlbm_batch *b, int mode)
+{
+    const int n = int(b->probs.size());
+    rlbm_status st = batch_sync_all(b);
+    if (st) return st;
+    if (mode == 1) {
+        if (b->pool.empty()) {
+            b->pool.resize(kBatchStreams);
+            b->pool_ev.resize(kBatchStreams);
+            for (int s = 0; s < kBatchStreams; ++s) {
+                BATCH_CUDA(b, cudaStreamCreateWithFlags(&b->pool[s], cudaStreamNonBlocking));
+                BATCH_CUDA(b, cudaEventCreateWithFlags(&b->pool_ev[s], cudaEventDisableTiming));
+            }
+            BATCH_CUDA(b, cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+            // longest-processing-time assignment of problems to streams
+            std::vector<std::pair<double, int>> order;
+            for (int i = 0; i < n; ++i)
+                order.push_back({-double(b->probs[i]->npop) * b->probs[i]->grid.nx * b->probs[i]->grid.ny, i});
+            std::sort(order.begin(), order.end());
+            std::vector<double> load(kBatchStreams, 0.0);
+            b->lane_of.assign(n, 0);
+            for (auto &o : order) {
+                const int s = int(std::min_element(load.begin(), load.end()) - load.begin());
+                b->lane_of[o.second] = s;
+                load[s] -= o.first;
+            }
+        }
+        if (b->solo_P.empty()) {
+            b->solo_P.resize(n);
+            b->solo_kind.resize(n);
+            for (int i = 0; i < n; ++i) solo_default(b->probs[i], b->solo_P[i], b->solo_kind[i]);
+        }
+        for (int i = 0; i < n; ++i) {
+            st = retile(b->probs[i], b->solo_P[i], b->solo_kind[i]);
+            if (st) return bfail(b, st, "problem %d: %s", i, b->probs[i]->err.c_str());
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            b->probs[i]->no_tma = true;
+            st = retile(b->probs[i], b->batch_P[i], 0);
+            if (st) return bfail(b, st, "problem %d: %s", i, b->probs[i]->err.c_str());
+        }
+        st = batch_build_units(b);
+        if (st) return st;
+    }
+    b->mode = mode;
+    return RLBM_OK;
+}
+
+// Mode 1: fork the pool from the batch stream, run every problem's nsteps
+// steps on its stream, join back.
+rlbm_status batch_streams_step(rlbm_batch *b, int nsteps)
+{
+    BATCH_CUDA(b, cudaEventRecord(b->fork_ev, b->stream));
+    for (cudaStream_t s : b->pool) BATCH_CUDA(b, cudaStreamWaitEvent(s, b->fork_ev, 0));
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        rlbm_t *h = b->probs[i];
+        cudaStream_t saved = h->stream;
+        h->stream = b->pool[b->lane_of[i]];
+        const long long l0 = h->launches;
+        rlbm_status st = rlbm_step(h, nsteps);
+        h->stream = saved;
+        if (st) return bfail(b, st, "problem %zu: %s", i, h->err.c_str());
+        b->launches += h->launches - l0;
+    }
+    for (size_t s = 0; s < b->pool.size(); ++s) {
+        BATCH_CUDA(b, cudaEventRecord(b->pool_ev[s], b->pool[s]));
+        BATCH_CUDA(b, cudaStreamWaitEvent(b->stream, b->pool_ev[s], 0));
+    }
+    b->steps += nsteps;
+    return RLBM_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -1353,6 +1436,7 @@ rlbm_status rlbm_batch_create(rlbm_batch_t **out, const rlbm_problem *p, int cou
         h->no_tma = true;
         st = retile(h, P, 0);
         if (st) return bail(bfail(b, st, "problem %d: %s", i, h->err.c_str()));
+        b->batch_P.push_back(P);
         off += align256(bytes);
     }
     const int n = count;
@@ -1379,6 +1463,9 @@ void rlbm_batch_destroy(rlbm_batch_t *b)
 {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (cudaStream_t s : b->pool) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    for (cudaEvent_t e : b->pool_ev) cudaEventDestroy(e);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
     for (rlbm_t *h : b->probs) rlbm_destroy(h);
     if (b->d_args) cudaFree(b->d_args);
@@ -1406,6 +1493,7 @@ rlbm_status rlbm_batch_step(rlbm_batch_t *b, int nsteps)
     if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
     if (nsteps < 0) return bfail(b, RLBM_ERR_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return RLBM_OK;
+    if (b->mode == 1) return batch_streams_step(b, nsteps);
     // current buffer parity of every problem (problems can be re-initialised one by one)
     const int n = int(b->probs.size());
     std::vector<int> par(n);
@@ -1444,15 +1532,30 @@ rlbm_status rlbm_batch_set_wait_limit(rlbm_batch_t *b, long long cycles)
 rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b)
 {
     if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    if (b->mode != 0) return bfail(b, RLBM_ERR_UNSUPPORTED, "the stream-pool mode has no grid barrier");
     b->stall_next = true;
     return RLBM_OK;
 }
+
+rlbm_status rlbm_batch_set_mode(rlbm_batch_t *b, int mode)
+{
+    if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
+    if (mode != 0 && mode != 1) return bfail(b, RLBM_ERR_ARG, "mode must be 0 or 1 (got %d)", mode);
+    if (mode == b->mode) return RLBM_OK;
+    return batch_set_mode(b, mode);
+}
+
+int rlbm_batch_mode(const rlbm_batch_t *b) { return b ? b->mode : -1; }
 
 rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *best_ms)
 {
     if (!b) return bfail(nullptr, RLBM_ERR_ARG, "NULL batch");
     if (steps_per_trial < 1) return bfail(b, RLBM_ERR_ARG, "steps_per_trial must be >= 1");
     const int n = int(b->probs.size());
+    if (b->mode != 0) {
+        rlbm_status st0 = batch_set_mode(b, 0);
+        if (st0) return st0;
+    }
     // a uniform rest state (n = 1, T = 1) in every problem: realistic timing, no NaNs
     for (int i = 0; i < n; ++i) {
         rlbm_t *h = b->probs[i];
@@ -1503,17 +1606,67 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *bes
                 if (!st) st = retile(b->probs[i], P, 0);
         }
     }
+    if (!st) st = batch_build_units(b);
+    for (int i = 0; i < n && !st; ++i) b->batch_P[i] = b->probs[i]->P;
+    // stream-pool mode: per class of K, the two-sites-per-lane tilings
+    float best1 = 0.f;
+    auto trial1 = [&](float &ms) -> rlbm_status {
+        BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+        rlbm_status s1 = batch_streams_step(b, steps_per_trial);
+        if (s1) return s1;
+        BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+        BATCH_CUDA(b, cudaEventSynchronize(e1));
+        BATCH_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+        return RLBM_OK;
+    };
+    if (!st) st = batch_set_mode(b, 1);
+    if (!st) st = trial1(best1); // graphs captured on the first call: time the second
+    if (!st) st = trial1(best1);
+    static const int psizes[] = {8, 12, 16, 24, 32};
+    for (auto &c : classes) {
+        if (st) break;
+        for (int P : psizes) {
+            std::vector<int> members;
+            for (int i : c.second)
+                if (pair_possible(b->probs[i], P) && !(b->solo_kind[i] == 2 && b->solo_P[i] == P)) members.push_back(i);
+            if (members.empty()) continue;
+            std::vector<int> oldP, oldK;
+            if (!st) st = batch_sync_all(b);
+            for (int i : members) {
+                oldP.push_back(b->solo_P[i]);
+                oldK.push_back(b->solo_kind[i]);
+                b->solo_P[i] = P;
+                b->solo_kind[i] = 2;
+                if (!st) st = retile(b->probs[i], P, 2);
+            }
+            float ms = 0.f;
+            if (!st) st = trial1(ms);
+            if (!st) st = trial1(ms);
+            if (st) break;
+            if (ms < best1) {
+                best1 = ms;
+            } else {
+                st = batch_sync_all(b);
+                for (size_t m = 0; m < members.size() && !st; ++m) {
+                    b->solo_P[members[m]] = oldP[m];
+                    b->solo_kind[members[m]] = oldK[m];
+                    st = retile(b->probs[members[m]], oldP[m], oldK[m]);
+                }
+            }
+        }
+    }
+    if (!st && best < best1) st = batch_set_mode(b, 0);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!st) st = batch_build_units(b);
     if (st) return st;
     b->launches = 0;
-    if (best_ms) *best_ms = best / steps_per_trial;
+    if (best_ms) *best_ms = std::min(best, best1) / steps_per_trial;
     BATCH_CUDA(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
     for (rlbm_t *h : b->probs) {
         BATCH_CUDA(b, cudaMemsetAsync(h->d_status, 0, sizeof(int), b->stream));
         h->steps = 0;
     }
+    b->steps = 0;
     BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
     return RLBM_OK;
 }

@@ -208,57 +208,14 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
     sres[((N + 1) * NC + 2) * kPairSites + s] = Uy * itau;
 }
 
-// Asynchronous staging of pass 1 (ASYNC): each warp streams its own
-// populations through a ring of kPairDepth slots in shared memory, a slot
-// holding kPairChunk populations x (1 or 2) rows x (64 + 2 HX) sites, HX = one
-// 16-byte chunk of halo on each side; rows are the site row y and, in 2D, the
-// row y - sgn(v_y) the population pulls from (boundary-mapped).  The copies
-// are cp.async 16-byte chunks (zero-filled outside the row), two slots ahead
-// of the arithmetic; the waits are cp.async group waits (no spin loop).  Halo
-// values outside the grid (x0 = 0, or x0 + 64 > nx) are loaded from their
-// boundary-mapped source directly.
-template <class St> struct PairStage {
-    static constexpr int HX = 16 / int(sizeof(St));      // halo elements per side
-    static constexpr int BW = kPairSites + 2 * HX;       // staged row width (elements)
-    static constexpr int C16 = BW * int(sizeof(St)) / 16; // 16-byte chunks per row
-    static constexpr int ROWB = BW * int(sizeof(St));     // bytes per staged row
-};
-
-__device__ __forceinline__ unsigned smem_u32p(const void *p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-template <class St> __device__ __forceinline__ float2 lds2(const St *p);
-template <> __device__ __forceinline__ float2 lds2<float>(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-template <> __device__ __forceinline__ float2 lds2<__half>(const __half *p)
-{
-    return __half22float2(*reinterpret_cast<const __half2 *>(p));
-}
-template <> __device__ __forceinline__ float2 lds2<__nv_bfloat16>(const __nv_bfloat16 *p)
-{
-    const unsigned u = *reinterpret_cast<const unsigned *>(p);
-    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
-}
-template <class St> __device__ __forceinline__ float lds1(const St *p);
-template <> __device__ __forceinline__ float lds1<float>(const float *p) { return *p; }
-template <> __device__ __forceinline__ float lds1<__half>(const __half *p) { return __half2float(*p); }
-template <> __device__ __forceinline__ float lds1<__nv_bfloat16>(const __nv_bfloat16 *p)
-{
-    return __bfloat162float(*p);
-}
-
 // St: storage type; N: quadrature order; PP: populations per warp (K is a
-// multiple of PP); TWO_D: ny > 1; ASYNC: staged pass 1 (nx a multiple of one
-// 16-byte chunk, buffers 16-byte aligned).  Requires nx even (paired access)
-// and a collision (tau finite).
-template <class St, int N, int PP, bool TWO_D, bool ASYNC>
+// multiple of PP); TWO_D: ny > 1.  Requires nx even (paired access) and a
+// collision (tau finite).
+template <class St, int N, int PP, bool TWO_D>
 __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelArgs a)
 {
     constexpr int NC = 2 * N + 1;
     constexpr int PQ = N + 4; // float4 per population in the pair table
-    constexpr int R = TWO_D ? 2 : 1;
-    using Sg = PairStage<St>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x, g = threadIdx.y, G = blockDim.y;
     const int x0 = blockIdx.x * kPairSites;
@@ -284,7 +241,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
 
     float2 fs[PP];
     float2 s0 = f2(0.f, 0.f), sc = f2(0.f, 0.f), ss = f2(0.f, 0.f), scc = f2(0.f, 0.f), scs = f2(0.f, 0.f);
-    // streamed pair of population k from its centre pair C, neighbour e (row 1),
+    // streamed pair of population k from its centre pair C, neighbour e (row y),
     // and, in 2D, C2, e2 of the pull row; accumulates the angular sums
     auto stream_pop = [&](int k, float2 C, float e, float2 C2, float e2) {
         const float4 t0 = __ldg(tb + k * PQ), t1 = __ldg(tb + k * PQ + 1), t2 = __ldg(tb + k * PQ + 2);
@@ -305,86 +262,29 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
         scs = __ffma2_rn(f2(t2.z, t2.w), v, scs);
     };
 
-    if (ASYNC) {
-        constexpr int CHA = kPairChunk, E = CHA * R * Sg::C16, SLOT = CHA * R * Sg::ROWB;
-        unsigned char *stg = smem_raw + pair_stage_offset(N, G) + size_t(g) * kPairDepth * SLOT;
-        const bool left = (x0 == 0) && lane == 0, right = xa + 2 >= a.nx; // halo from outside the grid
-        auto issue = [&](int c) {
-            if (c < PP / CHA) {
-                unsigned char *slot = stg + (c % kPairDepth) * SLOT;
-                for (int e = lane; e < E; e += 32) {
-                    const int kk = e / (R * Sg::C16), rem = e % (R * Sg::C16);
-                    const int row = rem / Sg::C16, j = rem % Sg::C16;
-                    const int k = c * CHA + kk;
-                    const long long dy = row == 0 ? 0 : (((my >> k) & 1ull) ? dym : dyp);
-                    const int x = x0 - Sg::HX + j * (16 / int(sizeof(St)));
-                    const bool ok = x >= 0 && x < a.nx;
-                    const St *src = ok ? base + (long long)k * S + dy + x : fin;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
-                                     smem_u32p(slot + (kk * R + row) * Sg::ROWB + j * 16)),
-                                 "l"(src), "r"(ok ? 16 : 0)
-                                 : "memory");
-                }
+    // populations whose loads are in flight together (registers: 6 per population in 2D)
+    constexpr int CH = TWO_D ? (PP <= 8 ? PP : (PP == 12 ? 6 : 4)) : (PP <= 16 ? PP : 8);
+    static_assert(PP % CH == 0, "chunking");
+#pragma unroll
+    for (int c0 = 0; c0 < PP; c0 += CH) {
+        float2 ca[CH], cb[TWO_D ? CH : 1];
+        float ea[CH], eb[TWO_D ? CH : 1];
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) {
+            const int k = c0 + kk;
+            const St *pk = base + (long long)k * S;
+            const int xs = ((mx >> k) & 1ull) ? xm : xp;
+            ca[kk] = PIo<St>::ld2(pk + xa);
+            ea[kk] = PIo<St>::ld1(pk + xs);
+            if (TWO_D) {
+                const long long dy = ((my >> k) & 1ull) ? dym : dyp;
+                cb[kk] = PIo<St>::ld2(pk + dy + xa);
+                eb[kk] = PIo<St>::ld1(pk + dy + xs);
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-#pragma unroll
-        for (int c = 0; c < kPairDepth - 1; ++c) issue(c);
-#pragma unroll
-        for (int c = 0; c < PP / CHA; ++c) {
-            issue(c + kPairDepth - 1);
-            asm volatile("cp.async.wait_group %0;" ::"n"(kPairDepth - 1) : "memory");
-            __syncwarp();
-            const St *slot = reinterpret_cast<const St *>(stg + (c % kPairDepth) * SLOT);
-#pragma unroll
-            for (int kk = 0; kk < CHA; ++kk) {
-                const int k = c * CHA + kk;
-                const bool px = (mx >> k) & 1ull;
-                const St *ra = slot + (kk * R) * Sg::BW + Sg::HX + 2 * lane;
-                const float2 C = lds2<St>(ra);
-                float e = lds1<St>(ra + (px ? -1 : 2));
-                float2 C2 = f2(0.f, 0.f);
-                float e2 = 0.f;
-                if (TWO_D) {
-                    const St *rb = ra + Sg::BW;
-                    C2 = lds2<St>(rb);
-                    e2 = lds1<St>(rb + (px ? -1 : 2));
-                }
-                if ((left && px) || (right && !px)) {
-                    const St *pk = base + (long long)k * S;
-                    const int xs = px ? xm : xp;
-                    e = PIo<St>::ld1(pk + xs);
-                    if (TWO_D) e2 = PIo<St>::ld1(pk + (((my >> k) & 1ull) ? dym : dyp) + xs);
-                }
-                stream_pop(k, C, e, C2, e2);
-            }
-            __syncwarp(); // the slot is refilled by the next issue
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-    } else {
-        constexpr int CH = TWO_D ? 4 : 8;
-        static_assert(PP % CH == 0, "chunking");
 #pragma unroll
-        for (int c0 = 0; c0 < PP; c0 += CH) {
-            float2 ca[CH], cb[TWO_D ? CH : 1];
-            float ea[CH], eb[TWO_D ? CH : 1];
-#pragma unroll
-            for (int kk = 0; kk < CH; ++kk) {
-                const int k = c0 + kk;
-                const St *pk = base + (long long)k * S;
-                const int xs = ((mx >> k) & 1ull) ? xm : xp;
-                ca[kk] = PIo<St>::ld2(pk + xa);
-                ea[kk] = PIo<St>::ld1(pk + xs);
-                if (TWO_D) {
-                    const long long dy = ((my >> k) & 1ull) ? dym : dyp;
-                    cb[kk] = PIo<St>::ld2(pk + dy + xa);
-                    eb[kk] = PIo<St>::ld1(pk + dy + xs);
-                }
-            }
-#pragma unroll
-            for (int kk = 0; kk < CH; ++kk)
-                stream_pop(c0 + kk, ca[kk], ea[kk], TWO_D ? cb[kk] : f2(0.f, 0.f), TWO_D ? eb[kk] : 0.f);
-        }
+        for (int kk = 0; kk < CH; ++kk)
+            stream_pop(c0 + kk, ca[kk], ea[kk], TWO_D ? cb[kk] : f2(0.f, 0.f), TWO_D ? eb[kk] : 0.f);
     }
     float2 *red2 = reinterpret_cast<float2 *>(red);
     red2[(0 * G + g) * 32 + lane] = s0;
@@ -432,12 +332,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
 }
 
 template <class St, int N, int PP>
-static cudaError_t launch_pair_np(bool two_d, bool async, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+static cudaError_t launch_pair_np(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                   const KernelArgs &a)
 {
-    void (*k)(const KernelArgs) =
-        two_d ? (async ? rlbm_pair_kernel<St, N, PP, true, true> : rlbm_pair_kernel<St, N, PP, true, false>)
-              : (async ? rlbm_pair_kernel<St, N, PP, false, true> : rlbm_pair_kernel<St, N, PP, false, false>);
+    void (*k)(const KernelArgs) = two_d ? rlbm_pair_kernel<St, N, PP, true> : rlbm_pair_kernel<St, N, PP, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -447,13 +345,13 @@ static cudaError_t launch_pair_np(bool two_d, bool async, dim3 grid, dim3 block,
 }
 
 template <class St>
-static cudaError_t launch_pair_t(int N, int PP, bool two_d, bool async, dim3 grid, dim3 block, size_t smem,
-                                 cudaStream_t st, const KernelArgs &a)
+static cudaError_t launch_pair_t(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 const KernelArgs &a)
 {
 #define RLBM_PAIR_CASE(n, p)                                                                                 \
-    if (N == n && PP == p) return launch_pair_np<St, n, p>(two_d, async, grid, block, smem, st, a);
-    RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
-    RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
+    if (N == n && PP == p) return launch_pair_np<St, n, p>(two_d, grid, block, smem, st, a);
+    RLBM_PAIR_CASE(2, 8) RLBM_PAIR_CASE(2, 12) RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
+    RLBM_PAIR_CASE(3, 8) RLBM_PAIR_CASE(3, 12) RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
 #undef RLBM_PAIR_CASE
     return cudaErrorInvalidValue;
 }

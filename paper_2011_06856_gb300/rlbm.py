@@ -40,7 +40,7 @@ EXPORTS = [
     "rlbm_closure_param_count", "rlbm_closure_get_params", "rlbm_closure_set_params",
     "rlbm_closure_features", "rlbm_closure_target", "rlbm_closure_restrict",
     "rlbm_closure_forward", "rlbm_closure_work_floats", "rlbm_closure_gradient",
-    "rlbm_closure_train_step", "rlbm_closure_apply_buffer", "rlbm_closure_set_apply_path",
+    "rlbm_closure_train_step", "rlbm_closure_apply_buffer", "rlbm_closure_set_apply_path", "rlbm_batch_set_mode", "rlbm_batch_mode",
 ]
 
 
@@ -189,6 +189,10 @@ def lib(path: str = LIB_PATH):
                                           _vp, fp]
     L.rlbm_closure_apply_buffer.restype = st
     L.rlbm_closure_apply_buffer.argtypes = [_vp, _vp, ll, ctypes.c_double]
+    L.rlbm_batch_set_mode.restype = st
+    L.rlbm_batch_set_mode.argtypes = [_vp, ctypes.c_int]
+    L.rlbm_batch_mode.restype = ctypes.c_int
+    L.rlbm_batch_mode.argtypes = [_vp]
     L.rlbm_closure_set_apply_path.restype = st
     L.rlbm_closure_set_apply_path.argtypes = [_vp, ctypes.c_int]
     _lib = L
@@ -344,12 +348,11 @@ class Simulation:
     def tile_populations(self) -> int:
         return lib().rlbm_tile_populations(self._h)
 
-    KERNELS = ("per-tile", "tma", "pair", "pair-plain")
+    KERNELS = ("per-tile", "tma", "pair")
 
     @property
     def step_kernel(self) -> str:
-        """'per-tile', 'tma', 'pair' (two sites per lane, staged first pass) or
-        'pair-plain' (two sites per lane, plain loads)."""
+        """'per-tile', 'tma' or 'pair' (two sites per lane)."""
         return self.KERNELS[lib().rlbm_step_kernel_variant(self._h)]
 
     def set_tiling(self, P: int, kind: str):
@@ -465,6 +468,17 @@ class Batch:
         ms = ctypes.c_float(0.0)
         _bcheck(lib().rlbm_batch_autotune(self._b, int(steps_per_trial), ctypes.byref(ms)), self._b)
         return ms.value
+
+    MODES = ("persistent", "streams")
+
+    def set_mode(self, mode: str):
+        """'persistent' (one cooperative launch per call) or 'streams' (each
+        problem's own step kernel on a pool of streams)."""
+        _bcheck(lib().rlbm_batch_set_mode(self._b, self.MODES.index(mode)), self._b)
+
+    @property
+    def mode(self) -> str:
+        return self.MODES[lib().rlbm_batch_mode(self._b)]
 
     def set_wait_limit(self, cycles: int):
         _bcheck(lib().rlbm_batch_set_wait_limit(self._b, int(cycles)), self._b)

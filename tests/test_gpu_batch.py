@@ -1,5 +1,6 @@
-"""Batched persistent form: every problem of a mixed batch stepped by one
-persistent launch equals the FP64 oracle run of that problem alone."""
+"""Batched form: every problem of a mixed batch, stepped by one persistent
+launch (mode 'persistent') or by its own kernels on a pool of streams (mode
+'streams'), equals the FP64 oracle run of that problem alone."""
 import math
 
 import numpy as np
@@ -36,11 +37,14 @@ def run_oracle(spec, fl, steps):
     return q.run(f, tau, steps, bcx, bcy)[0]
 
 
-@pytest.mark.parametrize("autotune", [False, True])
-def test_mixed_batch_matches_oracle_per_problem(autotune):
+@pytest.mark.parametrize("mode,autotune", [("persistent", False), ("persistent", True), ("streams", False)])
+def test_mixed_batch_matches_oracle_per_problem(mode, autotune):
     b = R.Batch(MIXED, N=2, precision="fp64")
     if autotune:
         b.autotune(2)
+    else:
+        b.set_mode(mode)
+    assert b.mode in R.Batch.MODES
     fields = [W.random_fields(s[0], s[1], seed=40 + i) for i, s in enumerate(MIXED)]
     for p, fl in zip(b.problems, fields):
         p.init_fields(fl)
@@ -55,20 +59,29 @@ def test_mixed_batch_matches_oracle_per_problem(autotune):
         assert relerr(p.get_populations(), ref) < 1e-12, i
 
 
-def test_batch_fp32_matches_oracle():
-    b = R.Batch(MIXED[:4], N=2, precision="fp32")
-    fields = [W.random_fields(s[0], s[1], seed=7 + i) for i, s in enumerate(MIXED[:4])]
+@pytest.mark.parametrize("mode", ["persistent", "streams", "autotuned"])
+def test_batch_fp32_matches_oracle(mode):
+    b = R.Batch(MIXED, N=2, precision="fp32")
+    if mode == "autotuned":
+        b.autotune(2)
+    else:
+        b.set_mode(mode)
+    fields = [W.random_fields(s[0], s[1], seed=7 + i) for i, s in enumerate(MIXED)]
     for p, fl in zip(b.problems, fields):
         p.init_fields(fl)
     b.step(20)
+    b.step(13)  # 32-step graphs and single launches per problem in the streams mode
     b.sync()
     for i, (p, fl) in enumerate(zip(b.problems, fields)):
-        ref = run_oracle(MIXED[i], fl, 20)
-        assert relerr(p.get_populations().astype(np.float64), ref) < 2e-5, i
+        ref = run_oracle(MIXED[i], fl, 33)
+        assert p.steps_done == 33
+        assert relerr(p.get_populations().astype(np.float64), ref) < 3e-5, i
 
 
-def test_batch_reinit_one_problem_midway():
+@pytest.mark.parametrize("mode", ["persistent", "streams"])
+def test_batch_reinit_one_problem_midway(mode):
     b = R.Batch(MIXED[:3], N=2, precision="fp64")
+    b.set_mode(mode)
     fields = [W.random_fields(s[0], s[1], seed=3 + i) for i, s in enumerate(MIXED[:3])]
     for p, fl in zip(b.problems, fields):
         p.init_fields(fl)
@@ -91,3 +104,22 @@ def test_batch_barrier_timeout_is_reported():
         b.sync()
     b.step(2)  # the context and the batch still work
     b.sync()
+
+
+def test_batch_mode_switch_keeps_the_state():
+    """Switching modes between calls re-tiles the problems but keeps their state."""
+    b = R.Batch(MIXED[:5], N=2, precision="fp32")
+    fields = [W.random_fields(s[0], s[1], seed=90 + i) for i, s in enumerate(MIXED[:5])]
+    for p, fl in zip(b.problems, fields):
+        p.init_fields(fl)
+    b.step(6)
+    b.set_mode("streams")
+    b.step(5)
+    b.set_mode("persistent")
+    b.step(4)
+    b.sync()
+    for i, (p, fl) in enumerate(zip(b.problems, fields)):
+        assert relerr(p.get_populations().astype(np.float64), run_oracle(MIXED[i], fl, 15)) < 3e-5, i
+    b.set_mode("streams")
+    with pytest.raises(R.RLBMError):
+        b.test_stall_next_step()  # no barrier to stall in this mode

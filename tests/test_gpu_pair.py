@@ -35,45 +35,34 @@ def relerr(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-ES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp16n": 2, "bf16n": 2}
-
-
-def staged_ok(nx, precision):
-    """The staged first pass copies whole 16-byte chunks of a row."""
-    return (nx * ES[precision]) % 16 == 0
-
-
-def pair_sim(nx, ny, N, K, tau, precision, bcx, bcy, P, kind=None):
-    kind = kind or ("pair" if staged_ok(nx, precision) else "pair-plain")
+def pair_sim(nx, ny, N, K, tau, precision, bcx, bcy, P):
     sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
-    sim.set_tiling(P, kind)
-    assert sim.step_kernel == kind and sim.tile_populations == P
+    sim.set_tiling(P, "pair")
+    assert sim.step_kernel == "pair" and sim.tile_populations == P
     return sim
 
 
-@pytest.mark.parametrize("kind", ["pair", "pair-plain"])
 @pytest.mark.parametrize("nx,ny,N,K,P,bcx,bcy", [
     (128, 1, 2, 16, 16, W.BC_COPYOUT, W.BC_PERIODIC),   # 1D, two full tiles
     (100, 1, 3, 64, 32, W.BC_PERIODIC, W.BC_PERIODIC),  # ragged last tile (36 of 64 sites)
     (2, 3, 2, 24, 24, W.BC_PERIODIC, W.BC_PERIODIC),    # one pair per row: both neighbours wrap
-    (4, 4, 2, 24, 24, W.BC_COPYOUT, W.BC_PERIODIC),     # one 16-byte chunk per row
+    (4, 4, 2, 24, 8, W.BC_COPYOUT, W.BC_PERIODIC),
     (66, 5, 2, 48, 16, W.BC_COPYOUT, W.BC_COPYOUT),     # 2D copy-out corners, 2 sites in the last tile
-    (68, 5, 2, 48, 16, W.BC_PERIODIC, W.BC_COPYOUT),    # 4 sites in the last tile, halo wraps
+    (68, 5, 2, 48, 12, W.BC_PERIODIC, W.BC_COPYOUT),    # 4 sites in the last tile, halo wraps
     (70, 6, 3, 32, 32, W.BC_PERIODIC, W.BC_PERIODIC),   # 2D periodic wrap
     (64, 4, 2, 48, 24, W.BC_PERIODIC, W.BC_COPYOUT),
-    (132, 3, 2, 16, 16, W.BC_COPYOUT, W.BC_COPYOUT),
-    (196, 3, 3, 16, 16, W.BC_COPYOUT, W.BC_PERIODIC),
+    (132, 3, 2, 24, 12, W.BC_COPYOUT, W.BC_COPYOUT),
+    (196, 3, 3, 16, 8, W.BC_COPYOUT, W.BC_PERIODIC),
+    (130, 1, 3, 32, 8, W.BC_PERIODIC, W.BC_PERIODIC),
 ])
-def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy, kind):
-    if kind == "pair" and not staged_ok(nx, "fp32"):
-        pytest.skip("row pitch not a whole number of 16-byte chunks")
+def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy):
     steps, tau = 9, 2.5
     fl = W.random_fields(nx, ny, seed=nx + 7 * ny + K)
     q = O.Quadrature(N, K)
     f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
     ref, flagged = q.run(f0, tau, steps, bcx, bcy)
     assert flagged == 0
-    sim = pair_sim(nx, ny, N, K, tau, "fp32", bcx, bcy, P, kind)
+    sim = pair_sim(nx, ny, N, K, tau, "fp32", bcx, bcy, P)
     sim.init_fields(fl)
     sim.step(steps)
     got = sim.get_populations().astype(np.float64)
@@ -84,13 +73,13 @@ def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy, kind):
         assert relerr(m[k], mac[k]) < fp32_tol(tau, steps), k
 
 
-@pytest.mark.parametrize("P,kind", [(16, "pair"), (32, "pair"), (32, "pair-plain")])
-def test_pair_kernel_full_size_8192x4_one_step(P, kind):
+@pytest.mark.parametrize("P", [16, 32])
+def test_pair_kernel_full_size_8192x4_one_step(P):
     """The benchmark problem (8192 x 4, N=3, K=64, FP32) one step at full size."""
     nx, ny, N, K = 8192, 4, 3, 64
     tau = W.tau_from_kn(0.1, nx)
     fl = W.shock_tube(nx, ny)
-    sim = pair_sim(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, P, kind)
+    sim = pair_sim(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, P)
     sim.init_fields(fl)
     sim.step(40)
     f40 = sim.get_populations().astype(np.float64)
@@ -106,15 +95,15 @@ def test_pair_and_per_tile_kernels_agree(precision):
     nx, ny, N, K = 96, 7, 2, 48
     fl = W.random_fields(nx, ny, seed=5)
     out = {}
-    for kind in ("pair", "pair-plain", "per-tile"):
+    for kind, P in (("pair", 24), ("pair", 12), ("per-tile", 24)):
         s = R.Simulation(nx, ny, N, K, 3.0, precision, W.BC_COPYOUT, W.BC_COPYOUT)
-        s.set_tiling(24, kind)
+        s.set_tiling(P, kind)
         s.init_fields(fl)
         s.step(6)
-        out[kind] = s.moments()
+        out[kind, P] = s.moments()
     tol = 1e-6 if precision == "fp32" else 2e-3
-    assert relerr(out["pair"], out["per-tile"]) < tol
-    assert relerr(out["pair-plain"], out["per-tile"]) < tol
+    assert relerr(out["pair", 24], out["per-tile", 24]) < tol
+    assert relerr(out["pair", 12], out["per-tile", 24]) < tol
 
 
 @pytest.mark.parametrize("precision", ["fp16n", "bf16n"])
@@ -166,15 +155,14 @@ def test_pair_kernel_refused_where_it_does_not_apply():
         dict(nx=64, ny=2, precision="fp64", tau=2.0, P=16),          # FP64 arithmetic
         dict(nx=65, ny=2, precision="fp32", tau=2.0, P=16),          # odd row length
         dict(nx=64, ny=2, precision="fp32", tau=float("inf"), P=16),  # no collision
-        dict(nx=64, ny=2, precision="fp32", tau=2.0, P=12),          # P not compiled for it
-        dict(nx=66, ny=2, precision="fp32", tau=2.0, P=16, kind="pair"),  # row not whole 16-byte chunks
+        dict(nx=64, ny=2, precision="fp32", tau=2.0, P=48),          # P not compiled for it
+        dict(nx=64, ny=2, precision="fp32", tau=2.0, P=8),           # 18 warps: more than 16
     ]
     for c in cases:
         s = R.Simulation(c["nx"], c["ny"], 2, 48, c["tau"], c["precision"], W.BC_COPYOUT, W.BC_PERIODIC)
-        for kind in ([c["kind"]] if "kind" in c else ["pair", "pair-plain"]):
-            with pytest.raises(R.RLBMError):
-                s.set_tiling(c["P"], kind)
-            assert s.step_kernel == "per-tile"
+        with pytest.raises(R.RLBMError):
+            s.set_tiling(c["P"], "pair")
+        assert s.step_kernel != "pair"
         s.close()
 
 
