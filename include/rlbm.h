@@ -156,16 +156,18 @@ long long rlbm_kernel_launches(const rlbm_t *h);
  * (row pitch a multiple of 16 bytes and nx >= one box), 2 = two sites per
  * lane (64-site tiles, packed f32x2 arithmetic; FP32 arithmetic, finite tau,
  * nx even, K a multiple of P in {8, 12, 16, 24, 32}, at most 16 warps),
- * 0 = per-tile kernel. */
+ * 3 = the same with its first pass staged through shared memory by
+ * cp.async.bulk on interior tiles (row pitch a multiple of 16 bytes; bounded
+ * mbarrier waits), 0 = per-tile kernel. */
 int rlbm_step_kernel_variant(const rlbm_t *h);
 
 /* Select the tiling and step kernel directly (no counterpart in the paper:
  * a performance choice that does not change what a step computes beyond
  * rounding).  P = populations per warp (one of 8, 12, 16, 24, 32, 48, 64 that
  * fits K and N); kind = 0 per-tile, 1 persistent TMA-staged, 2 two sites per
- * lane.  RLBM_ERR_UNSUPPORTED if the kernel is not possible for this handle
- * (the handle then keeps tiling P with the per-tile kernel); RLBM_ERR_ARG for
- * a kind outside 0..2.
+ * lane, 3 two sites per lane with bulk-staged loads.  RLBM_ERR_UNSUPPORTED if
+ * the kernel is not possible for this handle (the handle then keeps tiling P
+ * with the per-tile kernel); RLBM_ERR_ARG for a kind outside 0..3.
  * Synchronises the stream; the state is kept. */
 rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind);
 
@@ -185,15 +187,16 @@ int rlbm_tile_populations(const rlbm_t *h);
  * tiling.  Synchronises the stream. */
 rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms);
 
-/* Bound, in SM clock cycles, of every mbarrier wait in the TMA-staged step
- * kernel (default 4e9, about 2 s).  A wait that runs out makes the kernel
- * record RLBM_ERR_TIMEOUT, drain its own copies (bounded) and return; the next
- * synchronising call reports it.  cycles >= 1000. */
+/* Bound, in SM clock cycles, of every mbarrier wait in the TMA-staged and the
+ * bulk-staged step kernels (default 4e9, about 2 s).  A wait that runs out
+ * makes the kernel record RLBM_ERR_TIMEOUT, drain its own copies (bounded) and
+ * skip its stores; the next synchronising call reports it.  cycles >= 1000. */
 rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles);
 
 /* Test hook for the timeout path: the next step launch expects 16 bytes more
  * than its copies deliver, so its waits run out after the wait limit.
- * RLBM_ERR_UNSUPPORTED when the handle uses the per-tile kernel. */
+ * RLBM_ERR_UNSUPPORTED when the step kernel has no device waits (per-tile,
+ * two sites per lane without staging). */
 rlbm_status rlbm_test_stall_next_step(rlbm_t *h);
 
 /* ------------------------------------------------------------------ */

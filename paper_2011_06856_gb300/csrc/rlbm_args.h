@@ -38,18 +38,38 @@ struct KernelArgs {
     double *out[6];                            // MODE_MOMENTS fields
     const unsigned long long *masks; // per warp: bit k = (v_x >= 0), (v_y >= 0) of its population k (k < 64)
     const void *pairtab; // npop x (N+4) float4: paired constants of the two-sites-per-lane kernel (FP32 arithmetic)
+    long long wait_cycles; // bound of every mbarrier wait of the bulk-staged pair kernel (SM cycles)
+    unsigned extra_tx;     // test hook: bytes expected on top of the copies (makes the waits run out)
     int *status;
     unsigned *ctr; // [0] completed step launches (seeds stochastic rounding), [1] CTAs done
 };
 
 __host__ __device__ constexpr int tab_width(int N) { return ((2 * N + 5) + 3) / 4 * 4; }
 
-// Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory
-// (angular sums [5][G][64], per-site coefficients [(N+1)(2N+1) + 3][64], FP32).
+// Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory:
+// angular sums [5][G][64] and per-site coefficients [(N+1)(2N+1) + 3][64]
+// (FP32); for the bulk-staged form then, per warp, kPairDepth mbarriers and
+// kPairDepth slots of kPairChunk populations x rows x (64 sites + 16 bytes of
+// halo on each side).
 constexpr int kPairSites = 64;
-__host__ __device__ constexpr size_t pair_smem_bytes(int N, int G)
+constexpr int kPairChunk = 4;
+constexpr int kPairDepth = 3;
+__host__ __device__ constexpr size_t pair_bars_offset(int N, int G)
 {
-    return (size_t(5) * G + size_t(N + 1) * (2 * N + 1) + 3) * kPairSites * 4;
+    return ((size_t(5) * G + size_t(N + 1) * (2 * N + 1) + 3) * kPairSites * 4 + 15) / 16 * 16;
+}
+__host__ __device__ constexpr size_t pair_slots_offset(int N, int G)
+{
+    return pair_bars_offset(N, G) + (size_t(G) * kPairDepth * 8 + 15) / 16 * 16;
+}
+__host__ __device__ constexpr size_t pair_slot_bytes(int elem_bytes, bool two_d)
+{
+    return size_t(kPairChunk) * (two_d ? 2 : 1) * (kPairSites * elem_bytes + 32);
+}
+__host__ __device__ constexpr size_t pair_smem_bytes(int N, int G, bool bulk, int elem_bytes, bool two_d)
+{
+    return bulk ? pair_slots_offset(N, G) + size_t(G) * kPairDepth * pair_slot_bytes(elem_bytes, two_d)
+                : pair_bars_offset(N, G);
 }
 
 // Arguments of the persistent TMA-staged step kernel.
@@ -100,10 +120,11 @@ cudaError_t launch_f16(int mode, int N, int P, bool two_d, bool full, dim3 grid,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_bf16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t st, const KernelArgs &a);
-// Two-sites-per-lane step kernel (rlbm_pair.cuh): 64-site tiles, PP in {8, 12, 16, 24, 32}.
+// Two-sites-per-lane step kernel (rlbm_pair.cuh): 64-site tiles, PP in {8, 12, 16, 24, 32};
+// bulk: interior tiles staged through shared memory by cp.async.bulk.
 #define RLBM_DECLARE_PAIR(name)                                                                          \
-    cudaError_t launch_pair_##name(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,       \
-                                   cudaStream_t st, const KernelArgs &a);
+    cudaError_t launch_pair_##name(int N, int PP, bool two_d, bool bulk, dim3 grid, dim3 block,          \
+                                   size_t smem, cudaStream_t st, const KernelArgs &a);
 RLBM_DECLARE_PAIR(f32)
 RLBM_DECLARE_PAIR(f16)
 RLBM_DECLARE_PAIR(bf16)

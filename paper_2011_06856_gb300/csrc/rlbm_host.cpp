@@ -209,6 +209,8 @@ struct rlbm {
     bool stall_next = false; // test hook: next launch waits for bytes that never arrive
     bool no_tma = false;     // tiling choice: per-tile kernel even where TMA is possible
     bool use_pair = false;   // two-sites-per-lane step kernel (rlbm_pair.cuh)
+    bool pair_bulk = false;  // ... with its first pass staged by cp.async.bulk on interior tiles
+    long long wait_cycles = 4000000000LL; // bound of the device waits (about 2 s at the maximum clock)
     std::string err;
 };
 
@@ -436,6 +438,8 @@ rlbm_status build_tables(rlbm_t *h)
     a.pairtab = ptab.empty() ? nullptr : (const unsigned char *)h->d_tabs + o_pair;
     a.status = h->d_status;
     a.ctr = reinterpret_cast<unsigned *>(h->d_status + 1);
+    a.wait_cycles = h->wait_cycles;
+    a.extra_tx = 0;
     return RLBM_OK;
 }
 
@@ -478,18 +482,27 @@ bool pair_possible(const rlbm_t *h, int P)
     return (h->K / P) * (h->N + 1) <= rlbmk::kMaxWarps;
 }
 
+// The bulk-staged form copies row segments of whole 16-byte chunks from
+// 16-byte aligned buffers.
+bool pair_bulk_possible(const rlbm_t *h)
+{
+    return (size_t(h->grid.nx) * storage_size(h->prec)) % 16 == 0 && reinterpret_cast<uintptr_t>(h->buf) % 16 == 0;
+}
+
 cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
 {
     const dim3 grid((h->grid.nx + rlbmk::kPairSites - 1) / rlbmk::kPairSites, h->grid.ny);
     const dim3 block(32, h->G);
-    const bool two_d = h->grid.ny > 1;
-    const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G);
+    const bool two_d = h->grid.ny > 1, bulk = h->pair_bulk;
+    const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G, bulk, int(storage_size(h->prec)), two_d);
     cudaError_t e;
     switch (h->prec) {
-    case RLBM_FP32: e = rlbmk::launch_pair_f32(h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    case RLBM_FP32: e = rlbmk::launch_pair_f32(h->N, h->P, two_d, bulk, grid, block, smem, h->stream, a); break;
     case RLBM_FP16_DEV:
-    case RLBM_FP16_NORM: e = rlbmk::launch_pair_f16(h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
-    default: e = rlbmk::launch_pair_bf16(h->N, h->P, two_d, grid, block, smem, h->stream, a); break;
+    case RLBM_FP16_NORM:
+        e = rlbmk::launch_pair_f16(h->N, h->P, two_d, bulk, grid, block, smem, h->stream, a);
+        break;
+    default: e = rlbmk::launch_pair_bf16(h->N, h->P, two_d, bulk, grid, block, smem, h->stream, a); break;
     }
     if (e == cudaSuccess) ++h->launches;
     return e;
@@ -525,7 +538,11 @@ cudaError_t launch_step(rlbm_t *h, int from)
     rlbmk::KernelArgs a = h->base;
     a.fin = buffer(h, from);
     a.fout = buffer(h, 1 - from);
-    if (h->use_pair) return launch_pair(h, a);
+    if (h->use_pair) {
+        if (h->pair_bulk && h->stall_next) a.extra_tx = 16u;
+        h->stall_next = false;
+        return launch_pair(h, a);
+    }
     return launch(h, rlbmk::MODE_STEP, a);
 }
 
@@ -670,13 +687,18 @@ rlbm_status retile(rlbm_t *h, int P, int kind)
     h->Gs = (h->K + P - 1) / P;
     h->G = h->Gs * (h->N + 1);
     h->no_tma = kind != 1;
-    h->use_pair = kind == 2 && pair_possible(h, P);
+    h->use_pair = (kind == 2 || kind == 3) && pair_possible(h, P);
+    h->pair_bulk = h->use_pair && kind == 3 && pair_bulk_possible(h);
     rlbm_status st = build_tables(h);
     if (st) return st;
     return setup_tma(h);
 }
 
-int kernel_kind(const rlbm_t *h) { return h->use_pair ? 2 : (h->use_tma ? 1 : 0); }
+int kernel_kind(const rlbm_t *h)
+{
+    if (h->use_pair) return h->pair_bulk ? 3 : 2;
+    return h->use_tma ? 1 : 0;
+}
 
 struct TuneKey {
     int nx, ny, N, K, prec, bcx, bcy, site64;
@@ -974,14 +996,14 @@ int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? kernel_kind(h) : -1; 
 rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
 {
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
-    if (kind < 0 || kind > 2) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0, 1 or 2 (got %d)", kind);
+    if (kind < 0 || kind > 3) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0..3 (got %d)", kind);
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
     bool ok = false;
     for (int v : sizes) ok = ok || v == P;
     const int gs = ok ? (h->K + P - 1) / P : 0;
     if (!ok || gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K)
         return fail(h, RLBM_ERR_UNSUPPORTED, "no compiled tiling with P=%d for N=%d, K=%d", P, h->N, h->K);
-    if (kind == 2 && !pair_possible(h, P)) {
+    if ((kind == 2 || kind == 3) && !pair_possible(h, P)) {
         rlbm_status st0 = retile(h, P, 0);
         if (st0) return st0;
         return fail(h, RLBM_ERR_UNSUPPORTED,
@@ -993,7 +1015,8 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
     if (kernel_kind(h) != kind) {
         st = retile(h, P, 0);
         if (st) return st;
-        return fail(h, RLBM_ERR_UNSUPPORTED, "TMA-staged kernel not possible for this grid and tiling");
+        return fail(h, RLBM_ERR_UNSUPPORTED, kind == 1 ? "TMA-staged kernel not possible for this grid and tiling"
+                                                       : "bulk staging needs rows of whole 16-byte chunks");
     }
     return RLBM_OK;
 }
@@ -1026,7 +1049,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
         const int gs = (h->K + P - 1) / P;
         if (gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K) continue;
         if (P > 2 * h->K) continue;
-        for (int kind = 2; kind >= 0 && st == RLBM_OK; --kind) {
+        for (int kind = 3; kind >= 0 && st == RLBM_OK; --kind) {
             st = retile(h, P, kind);
             if (st) break;
             if (kernel_kind(h) != kind) continue; // kernel kind not possible for this tiling
@@ -1066,13 +1089,18 @@ rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles)
     if (cycles < 1000) return fail(h, RLBM_ERR_ARG, "wait limit must be >= 1000 cycles");
     if (h->tma)
         for (int b = 0; b < 2; ++b) h->tma[b].wait_cycles = cycles;
+    h->wait_cycles = cycles;
+    h->base.wait_cycles = cycles;
+    for (auto &g : h->graph)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     return RLBM_OK;
 }
 
 rlbm_status rlbm_test_stall_next_step(rlbm_t *h)
 {
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
-    if (!h->use_tma) return fail(h, RLBM_ERR_UNSUPPORTED, "the per-tile step kernel has no device waits");
+    if (!h->use_tma && !h->pair_bulk)
+        return fail(h, RLBM_ERR_UNSUPPORTED, "this step kernel has no device waits");
     h->stall_next = true;
     return RLBM_OK;
 }
@@ -1271,7 +1299,7 @@ void solo_default(const rlbm_t *h, int &P, int &kind)
 {
     static const int sizes[] = {8, 12, 16, 24, 32};
     for (int v : sizes)
-        if (pair_possible(h, v)) { P = v; kind = 2; return; }
+        if (pair_possible(h, v)) { P = v; kind = pair_bulk_possible(h) ? 3 : 2; return; }
     int gs = 0;
     choose_tiling(h->N, h->K, P, gs);
     kind = 0;
@@ -1628,7 +1656,7 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *bes
         for (int P : psizes) {
             std::vector<int> members;
             for (int i : c.second)
-                if (pair_possible(b->probs[i], P) && !(b->solo_kind[i] == 2 && b->solo_P[i] == P)) members.push_back(i);
+                if (pair_possible(b->probs[i], P) && !(b->solo_kind[i] >= 2 && b->solo_P[i] == P)) members.push_back(i);
             if (members.empty()) continue;
             std::vector<int> oldP, oldK;
             if (!st) st = batch_sync_all(b);
@@ -1636,8 +1664,8 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int steps_per_trial, float *bes
                 oldP.push_back(b->solo_P[i]);
                 oldK.push_back(b->solo_kind[i]);
                 b->solo_P[i] = P;
-                b->solo_kind[i] = 2;
-                if (!st) st = retile(b->probs[i], P, 2);
+                b->solo_kind[i] = pair_bulk_possible(b->probs[i]) ? 3 : 2;
+                if (!st) st = retile(b->probs[i], P, b->solo_kind[i]);
             }
             float ms = 0.f;
             if (!st) st = trial1(ms);

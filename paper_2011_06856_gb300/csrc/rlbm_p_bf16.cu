@@ -1,9 +1,9 @@
 // Two-sites-per-lane step kernel, __nv_bfloat16 storage, FP32 arithmetic.
 #include "rlbm_pair.cuh"
 namespace rlbmk {
-cudaError_t launch_pair_bf16(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              const KernelArgs &a)
+cudaError_t launch_pair_bf16(int N, int PP, bool two_d, bool bulk, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, const KernelArgs &a)
 {
-    return launch_pair_t<__nv_bfloat16>(N, PP, two_d, grid, block, smem, st, a);
+    return launch_pair_t<__nv_bfloat16>(N, PP, two_d, bulk, grid, block, smem, st, a);
 }
 } // namespace rlbmk

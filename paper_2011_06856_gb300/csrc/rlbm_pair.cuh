@@ -23,6 +23,17 @@
 // Per-population constants come from a pair table (each constant twice, so a
 // 16-byte load gives two packed operands): (|c|,|c|,|s|,|s|), (c,c,s,s),
 // (cc,cc,cs,cs), then the 2N+1 equilibrium basis values E_t in pairs.
+//
+// BULK form (row pitch a whole number of 16-byte chunks): on interior tiles
+// pass 1 reads shared memory.  Each warp streams its own populations through
+// kPairDepth slots, kPairChunk populations per slot, two slots ahead of the
+// arithmetic: one lane per (population, row) issues one cp.async.bulk of the
+// row segment [x0 - 16 bytes, x0 + 64 sites + 16 bytes) (the row y and, in
+// 2D, the boundary-mapped row y - sgn(v_y)), and the slot's mbarrier counts
+// the bytes.  Every wait is bounded (wait_cycles): on expiry the warp sets
+// bit 1 of the status word, waits (bounded) for its copies in flight, skips
+// its stores and still takes part in the CTA barriers.  Tiles touching the
+// x boundary use plain loads.
 #pragma once
 
 #include "rlbm_device.cuh"
@@ -40,6 +51,48 @@ __device__ __forceinline__ float2 f2sub(float2 a, float2 b)
     return d;
 }
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+__device__ __forceinline__ unsigned sptr(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ bool pbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase of the given parity; false when the bound ran out
+__device__ __forceinline__ bool pbar_wait(unsigned bar, unsigned parity, long long max_cycles)
+{
+    const long long t0 = clock64();
+    while (!pbar_try_wait(bar, parity))
+        if (clock64() - t0 > max_cycles) return false;
+    return true;
+}
+
+template <class St> __device__ __forceinline__ float2 lds2(const St *p);
+template <> __device__ __forceinline__ float2 lds2<float>(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+template <> __device__ __forceinline__ float2 lds2<__half>(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+template <> __device__ __forceinline__ float2 lds2<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const unsigned u = *reinterpret_cast<const unsigned *>(p);
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+template <class St> __device__ __forceinline__ float lds1(const St *p);
+template <> __device__ __forceinline__ float lds1<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float lds1<__half>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float lds1<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(*p);
+}
 
 
 // paired storage access: two consecutive sites (the first at an even index)
@@ -209,9 +262,10 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
 }
 
 // St: storage type; N: quadrature order; PP: populations per warp (K is a
-// multiple of PP); TWO_D: ny > 1.  Requires nx even (paired access) and a
-// collision (tau finite).
-template <class St, int N, int PP, bool TWO_D>
+// multiple of PP); TWO_D: ny > 1; BULK: staged pass 1 on interior tiles (row
+// pitch a multiple of 16 bytes, buffers 16-byte aligned).  Requires nx even
+// (paired access) and a collision (tau finite).
+template <class St, int N, int PP, bool TWO_D, bool BULK>
 __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelArgs a)
 {
     constexpr int NC = 2 * N + 1;
@@ -262,29 +316,98 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
         scs = __ffma2_rn(f2(t2.z, t2.w), v, scs);
     };
 
-    // populations whose loads are in flight together (registers: 6 per population in 2D)
-    constexpr int CH = TWO_D ? (PP <= 8 ? PP : (PP == 12 ? 6 : 4)) : (PP <= 16 ? PP : 8);
-    static_assert(PP % CH == 0, "chunking");
-#pragma unroll
-    for (int c0 = 0; c0 < PP; c0 += CH) {
-        float2 ca[CH], cb[TWO_D ? CH : 1];
-        float ea[CH], eb[TWO_D ? CH : 1];
-#pragma unroll
-        for (int kk = 0; kk < CH; ++kk) {
-            const int k = c0 + kk;
-            const St *pk = base + (long long)k * S;
-            const int xs = ((mx >> k) & 1ull) ? xm : xp;
-            ca[kk] = PIo<St>::ld2(pk + xa);
-            ea[kk] = PIo<St>::ld1(pk + xs);
-            if (TWO_D) {
-                const long long dy = ((my >> k) & 1ull) ? dym : dyp;
-                cb[kk] = PIo<St>::ld2(pk + dy + xa);
-                eb[kk] = PIo<St>::ld1(pk + dy + xs);
-            }
+    constexpr int HX = 16 / int(sizeof(St));    // halo elements on each side (16 bytes)
+    constexpr int BW = kPairSites + 2 * HX;      // staged row width (elements)
+    constexpr int RW = TWO_D ? 2 : 1;            // staged rows per population
+    constexpr int NCH = PP / kPairChunk;         // chunks per warp
+    const bool staged = BULK && x0 >= HX && x0 + kPairSites + HX <= a.nx;
+    bool good = true; // every bounded wait of this warp completed
+    if (staged) {
+        static_assert(PP % kPairChunk == 0, "chunking");
+        constexpr unsigned SLOT = unsigned(pair_slot_bytes(int(sizeof(St)), TWO_D));
+        unsigned char *slots = smem_raw + pair_slots_offset(N, G) + size_t(g) * kPairDepth * SLOT;
+        const unsigned bar0 = sptr(smem_raw + pair_bars_offset(N, G) + size_t(g) * kPairDepth * 8);
+        if (lane == 0) {
+            for (int d = 0; d < kPairDepth; ++d)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * d) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
+        __syncwarp();
+        // lane j < kPairChunk * RW copies row (j % RW) of population j / RW of a chunk
+        const int jk = lane / RW, jr = lane % RW;
+        auto issue = [&](int c) {
+            const unsigned bar = bar0 + 8 * (c % kPairDepth);
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                             "r"(unsigned(kPairChunk * RW * BW * int(sizeof(St))) + a.extra_tx)
+                             : "memory");
+            __syncwarp();
+            if (lane < kPairChunk * RW) {
+                const int k = c * kPairChunk + jk;
+                const long long dy = jr == 0 ? 0 : (((my >> k) & 1ull) ? dym : dyp);
+                const St *src = base + (long long)k * S + dy + (x0 - HX);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                 sptr(slots + (c % kPairDepth) * SLOT + lane * (BW * int(sizeof(St))))),
+                             "l"(src), "r"(unsigned(BW * int(sizeof(St)))), "r"(bar)
+                             : "memory");
+            }
+        };
+        int issued = 0;
+        for (; issued < kPairDepth - 1 && issued < NCH; ++issued) issue(issued);
 #pragma unroll
-        for (int kk = 0; kk < CH; ++kk)
-            stream_pop(c0 + kk, ca[kk], ea[kk], TWO_D ? cb[kk] : f2(0.f, 0.f), TWO_D ? eb[kk] : 0.f);
+        for (int c = 0; c < NCH; ++c) {
+            if (good && issued < NCH && issued == c + kPairDepth - 1) issue(issued++);
+            if (good) good = __all_sync(0xffffffffu, pbar_wait(bar0 + 8 * (c % kPairDepth), (c / kPairDepth) & 1, a.wait_cycles));
+            if (!good) break;
+            const St *slot = reinterpret_cast<const St *>(slots + (c % kPairDepth) * SLOT);
+#pragma unroll
+            for (int kk = 0; kk < kPairChunk; ++kk) {
+                const int k = c * kPairChunk + kk;
+                const bool px = (mx >> k) & 1ull;
+                const St *ra = slot + (kk * RW) * BW + HX + 2 * lane;
+                const float2 C = lds2<St>(ra);
+                const float e = lds1<St>(ra + (px ? -1 : 2));
+                float2 C2 = f2(0.f, 0.f);
+                float e2 = 0.f;
+                if (TWO_D) {
+                    C2 = lds2<St>(ra + BW);
+                    e2 = lds1<St>(ra + BW + (px ? -1 : 2));
+                }
+                stream_pop(k, C, e, C2, e2);
+            }
+            __syncwarp(); // the slot is refilled by a later issue
+        }
+        if (!good) {
+            if (lane == 0) atomicOr(a.status, 2);
+            // drain this warp's copies still in flight (bounded) before the CTA can exit
+            for (int c = 0; c < issued; ++c) pbar_wait(bar0 + 8 * (c % kPairDepth), (c / kPairDepth) & 1, a.wait_cycles);
+        }
+    } else {
+        // populations whose loads are in flight together (registers: 6 per population in 2D)
+        constexpr int CH = TWO_D ? (PP <= 8 ? PP : (PP == 12 ? 6 : 4)) : (PP <= 16 ? PP : 8);
+        static_assert(PP % CH == 0, "chunking");
+#pragma unroll
+        for (int c0 = 0; c0 < PP; c0 += CH) {
+            float2 ca[CH], cb[TWO_D ? CH : 1];
+            float ea[CH], eb[TWO_D ? CH : 1];
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                const int k = c0 + kk;
+                const St *pk = base + (long long)k * S;
+                const int xs = ((mx >> k) & 1ull) ? xm : xp;
+                ca[kk] = PIo<St>::ld2(pk + xa);
+                ea[kk] = PIo<St>::ld1(pk + xs);
+                if (TWO_D) {
+                    const long long dy = ((my >> k) & 1ull) ? dym : dyp;
+                    cb[kk] = PIo<St>::ld2(pk + dy + xa);
+                    eb[kk] = PIo<St>::ld1(pk + dy + xs);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk)
+                stream_pop(c0 + kk, ca[kk], ea[kk], TWO_D ? cb[kk] : f2(0.f, 0.f), TWO_D ? eb[kk] : 0.f);
+        }
     }
     float2 *red2 = reinterpret_cast<float2 *>(red);
     red2[(0 * G + g) * 32 + lane] = s0;
@@ -323,7 +446,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
         }
         const float2 om = __ffma2_rn(no2, f2(t1.z, t1.w), __ffma2_rn(no1, f2(t1.x, t1.y), o0));
         const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
-        if (act) PIo<St>::st2(ob + (long long)k * S, out, rng);
+        if (act && good) PIo<St>::st2(ob + (long long)k * S, out, rng);
     }
     if (kSR) {
         __syncthreads();
@@ -332,10 +455,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
 }
 
 template <class St, int N, int PP>
-static cudaError_t launch_pair_np(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+static cudaError_t launch_pair_np(bool two_d, bool bulk, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                   const KernelArgs &a)
 {
-    void (*k)(const KernelArgs) = two_d ? rlbm_pair_kernel<St, N, PP, true> : rlbm_pair_kernel<St, N, PP, false>;
+    void (*k)(const KernelArgs) =
+        two_d ? (bulk ? rlbm_pair_kernel<St, N, PP, true, true> : rlbm_pair_kernel<St, N, PP, true, false>)
+              : (bulk ? rlbm_pair_kernel<St, N, PP, false, true> : rlbm_pair_kernel<St, N, PP, false, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -345,11 +470,11 @@ static cudaError_t launch_pair_np(bool two_d, dim3 grid, dim3 block, size_t smem
 }
 
 template <class St>
-static cudaError_t launch_pair_t(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                                 const KernelArgs &a)
+static cudaError_t launch_pair_t(int N, int PP, bool two_d, bool bulk, dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, const KernelArgs &a)
 {
 #define RLBM_PAIR_CASE(n, p)                                                                                 \
-    if (N == n && PP == p) return launch_pair_np<St, n, p>(two_d, grid, block, smem, st, a);
+    if (N == n && PP == p) return launch_pair_np<St, n, p>(two_d, bulk, grid, block, smem, st, a);
     RLBM_PAIR_CASE(2, 8) RLBM_PAIR_CASE(2, 12) RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
     RLBM_PAIR_CASE(3, 8) RLBM_PAIR_CASE(3, 12) RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
 #undef RLBM_PAIR_CASE

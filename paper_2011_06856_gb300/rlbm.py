@@ -348,11 +348,12 @@ class Simulation:
     def tile_populations(self) -> int:
         return lib().rlbm_tile_populations(self._h)
 
-    KERNELS = ("per-tile", "tma", "pair")
+    KERNELS = ("per-tile", "tma", "pair", "pair-bulk")
 
     @property
     def step_kernel(self) -> str:
-        """'per-tile', 'tma' or 'pair' (two sites per lane)."""
+        """'per-tile', 'tma', 'pair' (two sites per lane) or 'pair-bulk' (two
+        sites per lane, first pass staged by bulk copies)."""
         return self.KERNELS[lib().rlbm_step_kernel_variant(self._h)]
 
     def set_tiling(self, P: int, kind: str):

@@ -37,7 +37,7 @@ def main(argv=None):
     ap.add_argument("--bcy", type=int, default=None)
     ap.add_argument("--tile-p", type=int, default=None, help="populations per warp")
     ap.add_argument("--per-tile", action="store_true", help="do not use the TMA-staged kernel")
-    ap.add_argument("--kernel", choices=("per-tile", "tma", "pair"), default=None,
+    ap.add_argument("--kernel", choices=("per-tile", "tma", "pair", "pair-bulk"), default=None,
                     help="step kernel (with --tile-p as its populations per warp)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--out", default=None)

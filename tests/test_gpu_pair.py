@@ -35,10 +35,18 @@ def relerr(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def pair_sim(nx, ny, N, K, tau, precision, bcx, bcy, P):
+ES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp16n": 2, "bf16n": 2}
+
+
+def bulk_ok(nx, precision):
+    """The bulk-staged form copies rows of whole 16-byte chunks."""
+    return (nx * ES[precision]) % 16 == 0
+
+
+def pair_sim(nx, ny, N, K, tau, precision, bcx, bcy, P, kind="pair"):
     sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
-    sim.set_tiling(P, "pair")
-    assert sim.step_kernel == "pair" and sim.tile_populations == P
+    sim.set_tiling(P, kind)
+    assert sim.step_kernel == kind and sim.tile_populations == P
     return sim
 
 
@@ -54,15 +62,21 @@ def pair_sim(nx, ny, N, K, tau, precision, bcx, bcy, P):
     (132, 3, 2, 24, 12, W.BC_COPYOUT, W.BC_COPYOUT),
     (196, 3, 3, 16, 8, W.BC_COPYOUT, W.BC_PERIODIC),
     (130, 1, 3, 32, 8, W.BC_PERIODIC, W.BC_PERIODIC),
+    (200, 1, 2, 16, 8, W.BC_PERIODIC, W.BC_PERIODIC),   # interior tiles at x0 = 64, 128; ragged edge tile
+    (256, 3, 2, 24, 12, W.BC_COPYOUT, W.BC_COPYOUT),    # interior tiles at x0 = 64, 128
+    (320, 4, 3, 16, 16, W.BC_PERIODIC, W.BC_PERIODIC),
 ])
-def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy):
+@pytest.mark.parametrize("kind", ["pair", "pair-bulk"])
+def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy, kind):
+    if kind == "pair-bulk" and not bulk_ok(nx, "fp32"):
+        pytest.skip("row pitch not a whole number of 16-byte chunks")
     steps, tau = 9, 2.5
     fl = W.random_fields(nx, ny, seed=nx + 7 * ny + K)
     q = O.Quadrature(N, K)
     f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
     ref, flagged = q.run(f0, tau, steps, bcx, bcy)
     assert flagged == 0
-    sim = pair_sim(nx, ny, N, K, tau, "fp32", bcx, bcy, P)
+    sim = pair_sim(nx, ny, N, K, tau, "fp32", bcx, bcy, P, kind)
     sim.init_fields(fl)
     sim.step(steps)
     got = sim.get_populations().astype(np.float64)
@@ -73,13 +87,13 @@ def test_pair_kernel_fp32_matches_oracle(nx, ny, N, K, P, bcx, bcy):
         assert relerr(m[k], mac[k]) < fp32_tol(tau, steps), k
 
 
-@pytest.mark.parametrize("P", [16, 32])
-def test_pair_kernel_full_size_8192x4_one_step(P):
+@pytest.mark.parametrize("P,kind", [(16, "pair"), (32, "pair"), (32, "pair-bulk"), (16, "pair-bulk")])
+def test_pair_kernel_full_size_8192x4_one_step(P, kind):
     """The benchmark problem (8192 x 4, N=3, K=64, FP32) one step at full size."""
     nx, ny, N, K = 8192, 4, 3, 64
     tau = W.tau_from_kn(0.1, nx)
     fl = W.shock_tube(nx, ny)
-    sim = pair_sim(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, P)
+    sim = pair_sim(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC, P, kind)
     sim.init_fields(fl)
     sim.step(40)
     f40 = sim.get_populations().astype(np.float64)
@@ -95,7 +109,7 @@ def test_pair_and_per_tile_kernels_agree(precision):
     nx, ny, N, K = 96, 7, 2, 48
     fl = W.random_fields(nx, ny, seed=5)
     out = {}
-    for kind, P in (("pair", 24), ("pair", 12), ("per-tile", 24)):
+    for kind, P in (("pair", 24), ("pair", 12), ("pair-bulk", 12), ("per-tile", 24)):
         s = R.Simulation(nx, ny, N, K, 3.0, precision, W.BC_COPYOUT, W.BC_COPYOUT)
         s.set_tiling(P, kind)
         s.init_fields(fl)
@@ -104,10 +118,12 @@ def test_pair_and_per_tile_kernels_agree(precision):
     tol = 1e-6 if precision == "fp32" else 2e-3
     assert relerr(out["pair", 24], out["per-tile", 24]) < tol
     assert relerr(out["pair", 12], out["per-tile", 24]) < tol
+    assert relerr(out["pair-bulk", 12], out["per-tile", 24]) < tol
 
 
+@pytest.mark.parametrize("kind", ["pair", "pair-bulk"])
 @pytest.mark.parametrize("precision", ["fp16n", "bf16n"])
-def test_pair_kernel_16bit_riemann_matches_oracle(precision):
+def test_pair_kernel_16bit_riemann_matches_oracle(precision, kind):
     """Four-quadrant Riemann problem, N=2 x K=48 at 96^2, Kn = 0.05, 150 steps."""
     nx = ny = 96
     N, K, steps = 2, 48, 150
@@ -117,7 +133,7 @@ def test_pair_kernel_16bit_riemann_matches_oracle(precision):
     ref, flagged = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
     assert flagged == 0
     mac, _ = q.macro(ref)
-    sim = pair_sim(nx, ny, N, K, tau, precision, W.BC_COPYOUT, W.BC_COPYOUT, 24)
+    sim = pair_sim(nx, ny, N, K, tau, precision, W.BC_COPYOUT, W.BC_COPYOUT, 24, kind)
     sim.init_fields(fl)
     sim.step(steps)
     m = sim.moments()
