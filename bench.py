@@ -79,22 +79,26 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h"):
+    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h", "rlbm_pair.cuh"):
         with open(os.path.join(ROOT, "paper_2011_06856_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, precision: str):
+def profiled_traffic(workload: str, precision: str, kernel: str, tile_p: int):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel sources changed since."""
+    or None when the summary is missing, covers another kernel or tiling, or
+    the kernel sources changed since."""
     path = os.path.join(ROOT, "profiles", f"rlbm_step_{workload}_{precision}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    k = re.search(r"step_kernel:\s*(\S+)\s+P=(\d+)", text)
     if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    if not k or k.group(1) != kernel or int(k.group(2)) != tile_p:
         return None
     return float(m.group(1))
 
@@ -378,8 +382,9 @@ def main():
         for sim in sims:
             sim.init_device(*d_fields)
             sim.autotune(8)
-    tiling = {"populations_per_warp": sims[0].tile_populations,
-              "kernel": "persistent TMA-staged" if sims[0].uses_tma else "per-tile"}
+    tiling = {"populations_per_warp": sims[0].tile_populations, "kernel": sims[0].step_kernel}
+    kernel_names = {"per-tile": "rlbm_kernel<MODE_STEP>", "tma": "rlbm_step_tma",
+                    "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
 
     def one_step():
         for sim in sims:
@@ -476,8 +481,9 @@ def main():
                        "tiling": tiling},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": profiled_traffic(w.name, precision),
-                         "kernel": "rlbm_step_tma" if sims[0].uses_tma else "rlbm_kernel<MODE_STEP>",
+                         "traffic": profiled_traffic(w.name, precision, sims[0].step_kernel,
+                                                     sims[0].tile_populations),
+                         "kernel": kernel_names[sims[0].step_kernel],
                          "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes},
             "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": METRIC,

@@ -37,7 +37,7 @@ struct KernelArgs {
     const double *in_n, *in_T, *in_bx, *in_by; // MODE_INIT fields
     double *out[6];                            // MODE_MOMENTS fields
     const unsigned long long *masks; // per warp: bit k = (v_x >= 0), (v_y >= 0) of its population k (k < 64)
-    const void *pairtab; // npop x (N+4) float4: paired constants of the two-sites-per-lane kernel (FP32 arithmetic)
+    const void *pairtab; // npop x 3 float4: paired constants of the two-sites-per-lane kernel (FP32 arithmetic)
     long long wait_cycles; // bound of every mbarrier wait of the bulk-staged pair kernel (SM cycles)
     unsigned extra_tx;     // test hook: bytes expected on top of the copies (makes the waits run out)
     int *status;

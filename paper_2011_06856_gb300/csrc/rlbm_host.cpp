@@ -368,18 +368,17 @@ rlbm_status build_tables(rlbm_t *h)
     const size_t o_rt = o_shell + align256(shell.size() * ls);
     const size_t o_mask = o_rt + align256(rt.size() * ls);
     // pair table of the two-sites-per-lane kernel (FP32 arithmetic only):
-    // (|c|,|c|,|s|,|s|), (c,c,s,s), (cc,cc,cs,cs), then E_0..E_2N in pairs
-    const int PQ = N + 4;
+    // (c,c,s,s), (|c|,|c|,|s|,|s|), (w/alpha, w/alpha, 0, 0) per population
+    const int PQ = 3;
     std::vector<double> ptab;
     if (!r64) {
         ptab.assign(size_t(npop) * PQ * 4, 0.0);
         for (int i = 0; i < npop; ++i) {
             const double *t = &pop[size_t(i) * TW];
             double *o = &ptab[size_t(i) * PQ * 4];
-            const double v[12] = {std::fabs(t[0]), std::fabs(t[0]), std::fabs(t[1]), std::fabs(t[1]),
-                                  t[0], t[0], t[1], t[1], t[2], t[2], t[3], t[3]};
+            const double v[12] = {t[0], t[0], t[1], t[1], std::fabs(t[0]), std::fabs(t[0]),
+                                  std::fabs(t[1]), std::fabs(t[1]), t[4], t[4], 0.0, 0.0};
             for (int u = 0; u < 12; ++u) o[u] = v[u];
-            for (int e = 0; e <= 2 * N; ++e) o[12 + 2 * e] = o[12 + 2 * e + 1] = t[4 + e];
         }
     }
     const size_t o_pair = o_mask + align256(masks.size() * sizeof(unsigned long long));

@@ -21,8 +21,13 @@
 //           (Eq. discrete-rbe), one paired store per population.
 //
 // Per-population constants come from a pair table (each constant twice, so a
-// 16-byte load gives two packed operands): (|c|,|c|,|s|,|s|), (c,c,s,s),
-// (cc,cc,cs,cs), then the 2N+1 equilibrium basis values E_t in pairs.
+// 16-byte load gives two packed operands): (c,c,s,s), (|c|,|c|,|s|,|s|) and
+// (w',w',0,0), w' = w_i / alpha_i in stored units.  The equilibrium of shell
+// r at angle theta is a trigonometric polynomial of degree N; with
+// cos 2t = 2 cc - 1, sin 2t = 2 cs, cos 3t = 4 c cc - 3 c, sin 3t = 4 s cc - s
+// it becomes w' (b0 + b1 c + b2 s + b3 cc + b4 cs [+ b5 c cc + b6 s cc]),
+// the b's formed once per site from the Fourier coefficients, so that the
+// per-population basis is a few packed products of c and s.
 //
 // BULK form (row pitch a whole number of 16-byte chunks): on interior tiles
 // pass 1 reads shared memory.  Each warp streams its own populations through
@@ -235,9 +240,11 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
 #pragma unroll
     for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
     const float *rtab = reinterpret_cast<const float *>(a.rtab);
+    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
 #pragma unroll
     for (int r = 0; r <= N; ++r) {
         const float *rt = rtab + r * (N + 1) * (N + 1);
+        float cf[NC]; // Fourier coefficients: cf[0] = Re C_0 - offset, cf[2m-1], cf[2m] = Re, Im C_m
 #pragma unroll
         for (int mm = 0; mm <= N; ++mm) {
             float cre = 0.f, cim = 0.f;
@@ -248,12 +255,27 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
                 cim += wgt * acci[mm][k];
             }
             if (mm == 0) {
-                sres[(r * NC) * kPairSites + s] = cre - a.feq_off_f;
+                cf[0] = cre - a.feq_off_f;
             } else {
-                sres[(r * NC + 2 * mm - 1) * kPairSites + s] = cre;
-                sres[(r * NC + 2 * mm) * kPairSites + s] = cim;
+                cf[2 * mm - 1] = cre;
+                cf[2 * mm] = cim;
             }
         }
+        // coefficients of the basis (1, c, s, cc, cs [, c cc, s cc])
+        float b[NC];
+        b[0] = cf[0] - cf[3];
+        b[1] = cf[1];
+        b[2] = cf[2];
+        b[3] = 2.f * cf[3];
+        b[4] = 2.f * cf[4];
+        if (N == 3) {
+            b[1] -= 3.f * cf[NC - 2];
+            b[2] -= cf[NC - 1];
+            b[NC - 2] = 4.f * cf[NC - 2];
+            b[NC - 1] = 4.f * cf[NC - 1];
+        }
+#pragma unroll
+        for (int t = 0; t < NC; ++t) sres[(r * NC + t) * kPairSites + s] = b[t];
     }
     const float itau = a.inv_tau_f;
     sres[((N + 1) * NC + 0) * kPairSites + s] = U0 * itau;
@@ -269,7 +291,7 @@ template <class St, int N, int PP, bool TWO_D, bool BULK>
 __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelArgs a)
 {
     constexpr int NC = 2 * N + 1;
-    constexpr int PQ = N + 4; // float4 per population in the pair table
+    constexpr int PQ = 3; // float4 per population in the pair table
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x, g = threadIdx.y, G = blockDim.y;
     const int x0 = blockIdx.x * kPairSites;
@@ -298,22 +320,24 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
     // streamed pair of population k from its centre pair C, neighbour e (row y),
     // and, in 2D, C2, e2 of the pull row; accumulates the angular sums
     auto stream_pop = [&](int k, float2 C, float e, float2 C2, float e2) {
-        const float4 t0 = __ldg(tb + k * PQ), t1 = __ldg(tb + k * PQ + 1), t2 = __ldg(tb + k * PQ + 2);
+        const float4 t0 = __ldg(tb + k * PQ), t1 = __ldg(tb + k * PQ + 1); // (c,c,s,s), (|c|,|c|,|s|,|s|)
         const bool px = (mx >> k) & 1ull; // v_x >= 0: pull from x - 1
         const float2 B = px ? f2(e, C.x) : f2(C.y, e);
-        const float2 ac = f2(t0.x, t0.y);
+        const float2 ac = f2(t1.x, t1.y);
         float2 v = __ffma2_rn(ac, f2sub(B, C), C);
         if (TWO_D) {
             const float2 B2 = px ? f2(e2, C2.x) : f2(C2.y, e2);
             const float2 hi = __ffma2_rn(ac, f2sub(B2, C2), C2);
-            v = __ffma2_rn(f2(t0.z, t0.w), f2sub(hi, v), v);
+            v = __ffma2_rn(f2(t1.z, t1.w), f2sub(hi, v), v);
         }
         fs[k] = v;
+        const float2 c = f2(t0.x, t0.y), sn = f2(t0.z, t0.w);
+        const float2 cv = __fmul2_rn(c, v);
         s0 = __fadd2_rn(s0, v);
-        sc = __ffma2_rn(f2(t1.x, t1.y), v, sc);
-        ss = __ffma2_rn(f2(t1.z, t1.w), v, ss);
-        scc = __ffma2_rn(f2(t2.x, t2.y), v, scc);
-        scs = __ffma2_rn(f2(t2.z, t2.w), v, scs);
+        sc = __fadd2_rn(sc, cv);
+        ss = __ffma2_rn(sn, v, ss);
+        scc = __ffma2_rn(c, cv, scc);
+        scs = __ffma2_rn(sn, cv, scs);
     };
 
     constexpr int HX = 16 / int(sizeof(St));    // halo elements on each side (16 bytes)
@@ -436,15 +460,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelA
     St *ob = fout + (long long)i0 * S + (long long)y * a.nx + xa;
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
-        const float4 t1 = __ldg(tb + k * PQ + 1);
-        float2 feq = f2(0.f, 0.f);
-#pragma unroll
-        for (int t = 0; t < NC; t += 2) {
-            const float4 e = __ldg(tb + k * PQ + 3 + t / 2);
-            feq = (t == 0) ? __fmul2_rn(cr[0], f2(e.x, e.y)) : __ffma2_rn(cr[t], f2(e.x, e.y), feq);
-            if (t + 1 < NC) feq = __ffma2_rn(cr[t + 1], f2(e.z, e.w), feq);
+        const float4 t0 = __ldg(tb + k * PQ);                                       // (c,c,s,s)
+        const float2 wq = __ldg(reinterpret_cast<const float2 *>(tb + k * PQ + 2)); // (w', w')
+        const float2 c = f2(t0.x, t0.y), sn = f2(t0.z, t0.w);
+        const float2 cc = __fmul2_rn(c, c), cs = __fmul2_rn(c, sn);
+        float2 pe = __ffma2_rn(cr[1], c, cr[0]);
+        pe = __ffma2_rn(cr[2], sn, pe);
+        pe = __ffma2_rn(cr[3], cc, pe);
+        pe = __ffma2_rn(cr[4], cs, pe);
+        if (N == 3) {
+            pe = __ffma2_rn(cr[NC - 2], __fmul2_rn(c, cc), pe);
+            pe = __ffma2_rn(cr[NC - 1], __fmul2_rn(sn, cc), pe);
         }
-        const float2 om = __ffma2_rn(no2, f2(t1.z, t1.w), __ffma2_rn(no1, f2(t1.x, t1.y), o0));
+        const float2 feq = __fmul2_rn(wq, pe);
+        const float2 om = __ffma2_rn(no2, sn, __ffma2_rn(no1, c, o0));
         const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
         if (act && good) PIo<St>::st2(ob + (long long)k * S, out, rng);
     }
