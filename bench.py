@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--timesteps", type=int, default=None,
                     help="override time steps per problem (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["per-tile", "tma", "pair", "pair-bulk"],
+                    help="pin the step kernel (with --tile-p) instead of autotuning; for profiling runs")
+    ap.add_argument("--tile-p", type=int, default=None, help="populations per warp with --kernel")
     return ap.parse_args()
 
 
@@ -381,7 +384,10 @@ def main():
     with torch.cuda.stream(stream):
         for sim in sims:
             sim.init_device(*d_fields)
-            sim.autotune(8)
+            if args.kernel:
+                sim.set_tiling(args.tile_p or sim.tile_populations, args.kernel)
+            else:
+                sim.autotune(8)
     tiling = {"populations_per_warp": sims[0].tile_populations, "kernel": sims[0].step_kernel}
     kernel_names = {"per-tile": "rlbm_kernel<MODE_STEP>", "tma": "rlbm_step_tma",
                     "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
