@@ -288,7 +288,7 @@ def run_batch(args):
 def run_closure(args):
     """Learned closure at the deployment size: time per step of the fine plain run
     (K = 128), the coarse plain run (K = 24) and the coarse run with the fused
-    correction, on a 4096^2 Riemann problem (FP32), after a short training on
+    correction, on a 4096^2 Riemann problem (FP32), after a training on
     128^2 runs of the method.  Reports corrected-coarse population updates/s."""
     import torch
     from paper_2011_06856_gb300 import build as B
@@ -298,7 +298,7 @@ def run_closure(args):
     n = 4096
     cl = R.Closure(2, 24, seed=7)
     X, T = CL.generate(cl, 128, 128, kns=(0.02, 0.1, 0.5, 2.0), steps=32, every=2)
-    CL.train(cl, X, T, iters=1500, batch=8192, lr=2e-3)
+    CL.train(cl, X, T, iters=4000, batch=16384, lr=2e-3, decay=True)
     del X, T
     fl = W.riemann_2d(n, n, CL.RIEMANN, jitter=0.01)
     kn = 0.3
@@ -325,6 +325,12 @@ def run_closure(args):
         e1.synchronize()
         times[name] = e0.elapsed_time(e1) / nst
         sim.close()
+    # accuracy at the training size: a Riemann problem not in the training set
+    acc = {}
+    for kn_e in (0.3, 1.0):
+        mf, mc, ml = CL.deploy(cl, 128, 128, kn_e, 64)
+        acc[f"kn{kn_e}"] = {"plain_coarse_rel_l2_n_eps": [CL.rel_l2(mc[i], mf[i]) for i in (0, 1)],
+                            "corrected_rel_l2_n_eps": [CL.rel_l2(ml[i], mf[i]) for i in (0, 1)]}
     upd = n * n * 72
     value = upd / (times["coarse_K24_closure"] * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": 20, "warmup": 3,
@@ -332,7 +338,10 @@ def run_closure(args):
             "vs_baseline": None, "dtype": "f32 (bf16 network weights)", "data": "synthetic",
             "config": {"workload": "closure4096", "grid": [n, n], "N": 2, "K_coarse": 24,
                        "K_fine": 128, "kn": kn, "ms_per_time_step": times,
-                       "fine_over_corrected_time": times["fine_K128"] / times["coarse_K24_closure"]},
+                       "fine_over_corrected_time": times["fine_K128"] / times["coarse_K24_closure"],
+                       "accuracy_vs_fine_128sq_64_steps": acc,
+                       "training": "tensor-core kernels, 4000 Adam steps of 16384 columns from 128^2 runs "
+                                   "at Kn 0.02, 0.1, 0.5, 2 (32 steps each)"},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
     print(json.dumps(line), flush=True)
 

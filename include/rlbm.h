@@ -336,6 +336,15 @@ rlbm_status rlbm_closure_apply_buffer(rlbm_closure_t *c, float *d_f, long long s
  * mma.sync, activations rounded to BF16; the default when N_pop <= 80) or one
  * thread per site with FP32 activations (tensor_cores = 0). */
 rlbm_status rlbm_closure_set_apply_path(rlbm_closure_t *c, int tensor_cores);
+/* Choose the kernels of rlbm_closure_gradient / rlbm_closure_train_step:
+ * tensor cores (the default for the specialised rules N = 2 with K = 16 or
+ * 24, and N = 3 with K = 16: one fused forward + backward + weight-gradient
+ * kernel, BF16 mma.sync with FP32 accumulation; the layer inputs x, h1, h2
+ * and the back-propagated deltas dY, dz2, dz1 are rounded to BF16 as they
+ * enter a product; the work array is not used) or one thread per site with
+ * FP32 activations and deltas (tensor_cores = 0; the work array holds the
+ * pre-activations and dY). */
+rlbm_status rlbm_closure_set_train_path(rlbm_closure_t *c, int tensor_cores);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free single step                                          */

@@ -72,7 +72,9 @@ def _view(sim: R.Simulation):
 
 
 def train(closure: R.Closure, X, T, iters: int = 300, batch: int = 4096, lr: float = 2e-3,
-          seed: int = 0, log_every: int = 0):
+          seed: int = 0, log_every: int = 0, decay: bool = False):
+    """Adam on random contiguous column blocks; with decay the step size
+    follows a half cosine from lr down to 0 over the iterations."""
     cols = X.shape[1]
     batch = min(batch, cols)
     work = closure.work(X.shape[1])
@@ -80,7 +82,8 @@ def train(closure: R.Closure, X, T, iters: int = 300, batch: int = 4096, lr: flo
     losses = []
     for it in range(iters):
         off = int(rng.integers(0, cols - batch + 1))
-        losses.append(closure.train_step(X, T, off, batch, lr, work))
+        lr_it = lr * 0.5 * (1.0 + math.cos(math.pi * it / iters)) if decay else lr
+        losses.append(closure.train_step(X, T, off, batch, max(lr_it, 1e-7), work))
         if log_every and it % log_every == 0:
             print(f"iter {it} loss {losses[-1]:.4e}")
     return losses

@@ -759,6 +759,278 @@ TcKernel tc_kernel(int N, int K, size_t *smem)
     return nullptr;
 }
 
+// ---------------------------------------------------------------- tensor-core training
+// One training pass (forward, loss, backward, weight gradients) on BF16
+// tensor cores, specialised like the correction kernel.  A CTA of TR_WARPS
+// warps takes tiles of TR_SITES columns of the feature matrix (persistent
+// over the batch); warp w owns rows 16w..16w+15 of the tile.
+//
+// per warp:  x -> z1 = x W1 + b1 -> h1 = GELU -> z2 -> h2 -> y  (mma.sync, z in
+//            registers); dY = 2 (y - t) / (count O); dz2 = (dY W3^T) GELU'(z2);
+//            dz1 = (dz2 W2^T) GELU'(z1) (mma.sync; the accumulators of the
+//            products share the fragment layout of z, so the derivative is
+//            applied in registers).  The layer inputs x, h1, h2 and the deltas
+//            dY, dz2, dz1 are rounded to BF16 as they enter a product.
+// per CTA:   the weight gradients gW3 = h2^T dY, gW2 = h1^T dz2, gW1 = x^T dz1
+//            are reductions over the tile's sites: their 16 x 8 blocks are
+//            spread over the warps, fragments taken transposed (ldmatrix.trans)
+//            from the row-major tile buffers, and accumulated in registers over
+//            all of the CTA's tiles; bias gradients are column sums (FP32) in
+//            shared memory.  Both go to the global gradient once per CTA.
+constexpr int TR_WARPS = 8;
+constexpr int TR_SITES = 16 * TR_WARPS;
+
+__device__ __forceinline__ void ldsm_x4_t(const void *p, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(const void *p, unsigned &r0, unsigned &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_addr(p)));
+}
+
+template <int N, int K>
+struct TrGeom {
+    static constexpr int NPOP = (N + 1) * K, F = 10 + NPOP, O = NPOP;
+    static constexpr int KS1 = (F + 15) / 16, FP = 16 * KS1, SX = FP + 8;
+    static constexpr int NT3 = O / 8, OP = 16 * ((O + 15) / 16), SO = OP + 8, KS3 = OP / 16;
+    static constexpr int NB = 4 * NT3 + 32 + 8 * KS1;     // weight-gradient blocks
+    static constexpr int NBW = (NB + TR_WARPS - 1) / TR_WARPS; // per warp
+    static constexpr size_t W1T = 0, W2T = W1T + size_t(64) * SX * 2, W2N = W2T + size_t(64) * SH * 2,
+                            W3T = W2N + size_t(64) * SH * 2, W3N = W3T + size_t(O) * SH * 2,
+                            BIAS = W3N + size_t(64) * SO * 2, GB = BIAS + size_t(128 + OP) * 4,
+                            XA = GB + size_t(128 + OP) * 4, H1 = XA + size_t(TR_SITES) * SX * 2,
+                            H2 = H1 + size_t(TR_SITES) * SH * 2, DY = H2 + size_t(TR_SITES) * SH * 2,
+                            D2 = DY + size_t(TR_SITES) * SO * 2, D1 = D2 + size_t(TR_SITES) * SH * 2,
+                            TOTAL = D1 + size_t(TR_SITES) * SH * 2;
+};
+
+// rows g, g+8 of a 16 x 64 fragment set, as BF16, into a row-major tile (stride SH);
+// FP32 column sums of the 16 rows added to colsum[]
+__device__ __forceinline__ void store_rows_colsum(float (*acc)[4], __nv_bfloat16 *h, float *colsum, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int c = nt * 8 + t * 2;
+        *reinterpret_cast<unsigned *>(h + g * SH + c) = pack_bf16(acc[nt][0], acc[nt][1]);
+        *reinterpret_cast<unsigned *>(h + (g + 8) * SH + c) = pack_bf16(acc[nt][2], acc[nt][3]);
+        float c0 = acc[nt][0] + acc[nt][2], c1 = acc[nt][1] + acc[nt][3];
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        }
+        if (g == 0) {
+            atomicAdd(&colsum[c], c0);
+            atomicAdd(&colsum[c + 1], c1);
+        }
+    }
+}
+
+template <int N, int K>
+__global__ void __launch_bounds__(TR_WARPS * 32, 1)
+    train_tc_kernel(Net net, const float *__restrict__ X, const float *__restrict__ T, long long ld, long long off,
+                    int count, float inv_count, float *__restrict__ grad, float *__restrict__ loss)
+{
+    using Gm = TrGeom<N, K>;
+    constexpr int F = Gm::F, O = Gm::O, SX = Gm::SX, SO = Gm::SO, NT3 = Gm::NT3, OP = Gm::OP, FP = Gm::FP;
+    static_assert(O % 8 == 0 && O <= 128, "output geometry");
+    extern __shared__ __align__(16) unsigned char sm[];
+    __nv_bfloat16 *w1t = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W1T); // [64][SX]  W1^T
+    __nv_bfloat16 *w2t = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W2T); // [64][SH]  W2^T
+    __nv_bfloat16 *w2n = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W2N); // [64][SH]  W2
+    __nv_bfloat16 *w3t = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W3T); // [O][SH]   W3^T
+    __nv_bfloat16 *w3n = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W3N); // [64][SO]  W3
+    float *bias = reinterpret_cast<float *>(sm + Gm::BIAS);               // b1 | b2 | b3
+    float *gbs = reinterpret_cast<float *>(sm + Gm::GB);                  // bias gradients
+    __nv_bfloat16 *xa = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::XA);   // [TR_SITES][SX]
+    __nv_bfloat16 *h1b = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::H1);  // [TR_SITES][SH]
+    __nv_bfloat16 *h2b = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::H2);
+    __nv_bfloat16 *dyb = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::DY);  // [TR_SITES][SO]
+    __nv_bfloat16 *d2b = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::D2);  // [TR_SITES][SH]
+    __nv_bfloat16 *d1b = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::D1);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int e = tid; e < 64 * SX; e += blockDim.x) {
+        const int n = e / SX, k = e % SX;
+        w1t[e] = (k < F) ? net.W1[k * H + n] : zero;
+    }
+    for (int e = tid; e < 64 * SH; e += blockDim.x) {
+        const int n = e / SH, k = e % SH;
+        w2t[e] = (k < H) ? net.W2[k * H + n] : zero;
+        w2n[e] = (k < H) ? net.W2[n * H + k] : zero;
+    }
+    for (int e = tid; e < O * SH; e += blockDim.x) {
+        const int n = e / SH, k = e % SH;
+        w3t[e] = (k < H) ? net.W3[k * O + n] : zero;
+    }
+    for (int e = tid; e < 64 * SO; e += blockDim.x) {
+        const int n = e / SO, k = e % SO;
+        w3n[e] = (k < O) ? net.W3[n * O + k] : zero;
+    }
+    for (int e = tid; e < 128 + OP; e += blockDim.x) {
+        bias[e] = e < 64 ? net.b1[e] : e < 128 ? net.b2[e - 64] : (e - 128 < O ? net.b3[e - 128] : 0.f);
+        gbs[e] = 0.f;
+    }
+    for (int e = tid; e < TR_SITES * SO; e += blockDim.x) dyb[e] = zero; // columns O..SO-1 stay zero
+    __syncthreads();
+
+    float ga[Gm::NBW][4];
+#pragma unroll
+    for (int i = 0; i < Gm::NBW; ++i)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ga[i][u] = 0.f;
+    float lsum = 0.f;
+    const int g8 = lane >> 2, t4 = lane & 3, mi = lane >> 3, r8 = lane & 7;
+    const long long ntile = (count + TR_SITES - 1) / TR_SITES;
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const long long s0 = tile * TR_SITES + wid * 16; // the warp's first column (relative to off)
+        __nv_bfloat16 *xr = xa + wid * 16 * SX, *h1r = h1b + wid * 16 * SH, *h2r = h2b + wid * 16 * SH;
+        __nv_bfloat16 *dyr = dyb + wid * 16 * SO, *d2r = d2b + wid * 16 * SH, *d1r = d1b + wid * 16 * SH;
+        {   // input rows (BF16), zero beyond F and beyond the batch
+            const int ls = lane & 15, half = lane >> 4;
+            const long long sc = s0 + ls;
+            const bool v = sc < count;
+            for (int f = half; f < FP; f += 2)
+                xr[ls * SX + f] = __float2bfloat16_rn(v && f < F ? X[(long long)f * ld + off + sc] : 0.f);
+        }
+        __syncwarp();
+        float z1[8][4], z2[8][4], y[NT3][4];
+        bias_init(z1, bias, 8, lane);
+        warp_gemm<Gm::KS1, 8>(xr, SX, w1t, SX, z1, lane);
+        gelu_rows(z1, h1r, lane);
+        __syncwarp();
+        bias_init(z2, bias + 64, 8, lane);
+        warp_gemm<4, 8>(h1r, SH, w2t, SH, z2, lane);
+        gelu_rows(z2, h2r, lane);
+        __syncwarp();
+        bias_init(y, bias + 128, NT3, lane);
+        warp_gemm<4, NT3>(h2r, SH, w3t, SH, y, lane);
+        // loss and dY = 2 (y - t) / (count O); rows g8 (u = 0, 1) and g8 + 8 (u = 2, 3)
+        const long long sa = s0 + g8, sb = sa + 8;
+        const bool va = sa < count, vb = sb < count;
+#pragma unroll
+        for (int nt = 0; nt < NT3; ++nt) {
+            const int c = nt * 8 + 2 * t4;
+            const float d0 = va ? y[nt][0] - T[(long long)c * ld + off + sa] : 0.f;
+            const float d1 = va ? y[nt][1] - T[(long long)(c + 1) * ld + off + sa] : 0.f;
+            const float d2 = vb ? y[nt][2] - T[(long long)c * ld + off + sb] : 0.f;
+            const float d3 = vb ? y[nt][3] - T[(long long)(c + 1) * ld + off + sb] : 0.f;
+            lsum += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            const float q = 2.f * inv_count;
+            y[nt][0] = q * d0; y[nt][1] = q * d1; y[nt][2] = q * d2; y[nt][3] = q * d3;
+            *reinterpret_cast<unsigned *>(dyr + g8 * SO + c) = pack_bf16(y[nt][0], y[nt][1]);
+            *reinterpret_cast<unsigned *>(dyr + (g8 + 8) * SO + c) = pack_bf16(y[nt][2], y[nt][3]);
+            float c0 = y[nt][0] + y[nt][2], c1 = y[nt][1] + y[nt][3];
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+                c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            }
+            if (g8 == 0) {
+                atomicAdd(&gbs[128 + c], c0);
+                atomicAdd(&gbs[128 + c + 1], c1);
+            }
+        }
+        __syncwarp();
+        // dz2 = (dY W3^T) GELU'(z2)
+        float da[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) da[nt][u] = 0.f;
+        warp_gemm<Gm::KS3, 8>(dyr, SO, w3n, SO, da, lane);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) da[nt][u] *= gelu_grad(z2[nt][u]);
+        store_rows_colsum(da, d2r, gbs + 64, lane);
+        __syncwarp();
+        // dz1 = (dz2 W2^T) GELU'(z1)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) da[nt][u] = 0.f;
+        warp_gemm<4, 8>(d2r, SH, w2n, SH, da, lane);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) da[nt][u] *= gelu_grad(z1[nt][u]);
+        store_rows_colsum(da, d1r, gbs, lane);
+        __syncthreads();
+        // weight-gradient blocks over the tile's TR_SITES sites
+#pragma unroll
+        for (int i = 0; i < Gm::NBW; ++i) {
+            const int b = wid + TR_WARPS * i;
+            if (b < Gm::NB) {
+                const __nv_bfloat16 *As, *Bs;
+                int sa_, sb_, m0, n0;
+                if (b < 4 * NT3) {
+                    As = h2b; sa_ = SH; Bs = dyb; sb_ = SO; m0 = (b / NT3) * 16; n0 = (b % NT3) * 8;
+                } else if (b < 4 * NT3 + 32) {
+                    const int bb = b - 4 * NT3;
+                    As = h1b; sa_ = SH; Bs = d2b; sb_ = SH; m0 = (bb / 8) * 16; n0 = (bb % 8) * 8;
+                } else {
+                    const int bb = b - 4 * NT3 - 32;
+                    As = xa; sa_ = SX; Bs = d1b; sb_ = SH; m0 = (bb / 8) * 16; n0 = (bb % 8) * 8;
+                }
+#pragma unroll
+                for (int ks = 0; ks < TR_SITES / 16; ++ks) {
+                    const int k0 = ks * 16;
+                    unsigned a0, a1, a2, a3, b0, b1;
+                    ldsm_x4_t(As + (k0 + (mi >> 1) * 8 + r8) * sa_ + m0 + (mi & 1) * 8, a0, a1, a2, a3);
+                    ldsm_x2_t(Bs + (k0 + (mi & 1) * 8 + r8) * sb_ + n0, b0, b1);
+                    mma_bf16(ga[i], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+        __syncthreads(); // the tile buffers are rewritten by the next tile
+    }
+    // the CTA's contributions to the global gradient (layout W1 [F][H] | b1 | W2 [H][H] | b2 | W3 [H][O] | b3)
+    float *gW1 = grad, *gb1 = gW1 + F * H, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + H * O;
+#pragma unroll
+    for (int i = 0; i < Gm::NBW; ++i) {
+        const int b = wid + TR_WARPS * i;
+        if (b >= Gm::NB) continue;
+        int m0, n0, which;
+        if (b < 4 * NT3) { which = 3; m0 = (b / NT3) * 16; n0 = (b % NT3) * 8; }
+        else if (b < 4 * NT3 + 32) { which = 2; m0 = ((b - 4 * NT3) / 8) * 16; n0 = ((b - 4 * NT3) % 8) * 8; }
+        else { which = 1; m0 = ((b - 4 * NT3 - 32) / 8) * 16; n0 = ((b - 4 * NT3 - 32) % 8) * 8; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = m0 + g8 + (u < 2 ? 0 : 8), n = n0 + 2 * t4 + (u & 1);
+            if (which == 3) atomicAdd(&gW3[m * O + n], ga[i][u]);
+            else if (which == 2) atomicAdd(&gW2[m * H + n], ga[i][u]);
+            else if (m < F) atomicAdd(&gW1[m * H + n], ga[i][u]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) atomicAdd(loss, lsum);
+    __syncthreads();
+    for (int e = tid; e < 128 + O; e += blockDim.x) {
+        if (e < 64) atomicAdd(&gb1[e], gbs[e]);
+        else if (e < 128) atomicAdd(&gb2[e - 64], gbs[e]);
+        else atomicAdd(&gb3[e - 128], gbs[e]);
+    }
+}
+
+using TrKernel = void (*)(Net, const float *, const float *, long long, long long, int, float, float *, float *);
+
+TrKernel tr_kernel(int N, int K, size_t *smem)
+{
+    if (N == 2 && K == 24) { *smem = TrGeom<2, 24>::TOTAL; return train_tc_kernel<2, 24>; }
+    if (N == 2 && K == 16) { *smem = TrGeom<2, 16>::TOTAL; return train_tc_kernel<2, 16>; }
+    if (N == 3 && K == 16) { *smem = TrGeom<3, 16>::TOTAL; return train_tc_kernel<3, 16>; }
+    return nullptr;
+}
+
 } // namespace
 
 // ==================================================================== host side
@@ -774,6 +1046,7 @@ struct rlbm_closure {
     float *d_loss = nullptr;
     int adam_t = 0;
     bool simt_apply = false;
+    bool simt_train = false;
     std::string err;
     size_t off_W1, off_b1, off_W2, off_b2, off_W3, off_b3;
 };
@@ -838,6 +1111,10 @@ size_t bwd_smem(const rlbm_closure *c) { return (size_t(MAXO) + 2 * H + c->F) * 
 
 bool tc_attributes(const rlbm_closure *c)
 {
+    size_t trsmem = 0;
+    TrKernel tk = tr_kernel(c->N, c->K, &trsmem);
+    if (tk && cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsmem) != cudaSuccess)
+        return false;
     for (int v = 0; v < 2; ++v) {
         size_t smem = 0;
         TcKernel k = v ? tc_kernel<4>(c->N, c->K, &smem) : tc_kernel<1>(c->N, c->K, &smem);
@@ -1084,6 +1361,26 @@ static rlbm_status closure_grad(rlbm_closure_t *c, const float *d_x, const float
 {
     CL_CUDA(c, cudaMemsetAsync(c->d_g, 0, c->nparam * 4, c->stream));
     CL_CUDA(c, cudaMemsetAsync(c->d_loss, 0, 4, c->stream));
+    size_t trsmem = 0;
+    TrKernel tk = c->simt_train ? nullptr : tr_kernel(c->N, c->K, &trsmem);
+    if (tk) {
+        // tensor-core path: forward, backward and weight gradients in one persistent kernel
+        int dev = 0, sms = 0;
+        CL_CUDA(c, cudaGetDevice(&dev));
+        CL_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long tiles = (count + TR_SITES - 1) / TR_SITES;
+        const int grid = int(std::min<long long>(sms, tiles));
+        tk<<<grid, TR_WARPS * 32, trsmem, c->stream>>>(net_of(c), d_x, d_t, ld, off, count,
+                                                      1.0f / (float(count) * float(c->O)), c->d_g, c->d_loss);
+        CL_CUDA(c, cudaGetLastError());
+        if (loss) {
+            float l = 0.f;
+            CL_CUDA(c, cudaMemcpyAsync(&l, c->d_loss, 4, cudaMemcpyDeviceToHost, c->stream));
+            CL_CUDA(c, cudaStreamSynchronize(c->stream));
+            *loss = l / (float(count) * float(c->O));
+        }
+        return RLBM_OK;
+    }
     const int grid = std::min(2048, (count + 127) / 128);
     const float inv = 1.0f / (float(count) * float(c->O));
     // activations are stored with leading dimension `count`, columns relative to off
@@ -1159,6 +1456,13 @@ rlbm_status rlbm_closure_apply_buffer(rlbm_closure_t *c, float *d_f, long long s
     const int grid = int(std::min<long long>(4096, (sites + 127) / 128));
     apply_kernel<<<grid, 128, fwd_smem(c, true), c->stream>>>(net_of(c), tab_of(c), d_f, sites, float(kn));
     CL_CUDA(c, cudaGetLastError());
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_closure_set_train_path(rlbm_closure_t *c, int tensor_cores)
+{
+    if (!c) return cfail(nullptr, RLBM_ERR_ARG, "NULL closure");
+    c->simt_train = !tensor_cores;
     return RLBM_OK;
 }
 

@@ -40,7 +40,7 @@ EXPORTS = [
     "rlbm_closure_param_count", "rlbm_closure_get_params", "rlbm_closure_set_params",
     "rlbm_closure_features", "rlbm_closure_target", "rlbm_closure_restrict",
     "rlbm_closure_forward", "rlbm_closure_work_floats", "rlbm_closure_gradient",
-    "rlbm_closure_train_step", "rlbm_closure_apply_buffer", "rlbm_closure_set_apply_path", "rlbm_batch_set_mode", "rlbm_batch_mode",
+    "rlbm_closure_train_step", "rlbm_closure_apply_buffer", "rlbm_closure_set_apply_path", "rlbm_closure_set_train_path", "rlbm_batch_set_mode", "rlbm_batch_mode",
 ]
 
 
@@ -193,6 +193,8 @@ def lib(path: str = LIB_PATH):
     L.rlbm_batch_set_mode.argtypes = [_vp, ctypes.c_int]
     L.rlbm_batch_mode.restype = ctypes.c_int
     L.rlbm_batch_mode.argtypes = [_vp]
+    L.rlbm_closure_set_train_path.restype = st
+    L.rlbm_closure_set_train_path.argtypes = [_vp, ctypes.c_int]
     L.rlbm_closure_set_apply_path.restype = st
     L.rlbm_closure_set_apply_path.argtypes = [_vp, ctypes.c_int]
     _lib = L
@@ -626,6 +628,9 @@ class Closure:
 
     def apply_buffer(self, f_ptr: int, sites: int, kn: float):
         self._check(lib().rlbm_closure_apply_buffer(self._c, _vp(f_ptr), int(sites), float(kn)))
+
+    def set_train_path(self, tensor_cores: bool):
+        self._check(lib().rlbm_closure_set_train_path(self._c, 1 if tensor_cores else 0))
 
     def set_apply_path(self, tensor_cores: bool):
         self._check(lib().rlbm_closure_set_apply_path(self._c, 1 if tensor_cores else 0))

@@ -84,12 +84,64 @@ def test_forward_and_gradient_match_reference():
     yref, _ = C.mlp_forward(params, X.T.astype(np.float64))
     np.testing.assert_allclose(Y.cpu().numpy(), yref.T, rtol=1e-4, atol=1e-5)
     work = cl.work(S)
+    cl.set_train_path(False)  # one thread per site, FP32 activations and deltas
     grad, loss = cl.gradient(Xd, Td, 100, 500, work)
     lref, gref = C.mlp_loss_and_grad(params, X[:, 100:600].T.astype(np.float64),
                                      T[:, 100:600].T.astype(np.float64))
     assert abs(loss - lref) < 1e-4 * lref
     flat = np.concatenate([a.ravel() for a in gref])
     assert np.abs(grad - flat).max() < 1e-3 * np.abs(flat).max()
+
+
+def bf16_loss_and_grad(params, X, T):
+    """Loss and gradient with the BF16 roundings of the tensor-core training
+    kernel: the layer inputs x, h1, h2 and the deltas dY, dz2, dz1 rounded to
+    BF16 where they enter a product (bias gradients from the unrounded deltas);
+    FP64 otherwise."""
+    W1, b1, W2, b2, W3, b3 = params
+    xb = bf16(X)
+    z1 = xb @ W1 + b1
+    h1 = bf16(C.gelu(z1))
+    z2 = h1 @ W2 + b2
+    h2 = bf16(C.gelu(z2))
+    y = h2 @ W3 + b3
+    dY = 2.0 * (y - T) / y.size
+    dYb = bf16(dY)
+    dz2 = (dYb @ W3.T) * C.gelu_grad(z2)
+    dz2b = bf16(dz2)
+    dz1 = (dz2b @ W2.T) * C.gelu_grad(z1)
+    dz1b = bf16(dz1)
+    g = (xb.T @ dz1b, dz1.sum(0), h1.T @ dz2b, dz2.sum(0), h2.T @ dYb, dY.sum(0))
+    return float(((y - T) ** 2).mean()), g
+
+
+@pytest.mark.parametrize("n,k,S,off,count", [(2, 24, 700, 100, 500), (2, 24, 21000, 300, 20000),
+                                             (2, 16, 1500, 0, 1333), (3, 16, 1500, 17, 1400)])
+def test_tensor_core_gradient_matches_bf16_reference(n, k, S, off, count):
+    """Fused tensor-core training pass (ragged last tile; above 152 x 128
+    columns the CTAs loop over tiles) against the reference with the same BF16
+    roundings, and against the exact FP64 gradient: the BF16 roundings of the
+    activations and deltas (relative 2^-9) leave the gradient direction intact."""
+    cl = R.Closure(n, k, seed=11)
+    g = np.random.default_rng(n * 100 + k)
+    X = g.normal(0, 0.5, (cl.F, S)).astype(np.float32)
+    T = g.normal(0, 0.1, (cl.npop, S)).astype(np.float32)
+    Xd = torch.tensor(X, device="cuda")
+    Td = torch.tensor(T, device="cuda")
+    cl.set_train_path(True)
+    grad, loss = cl.gradient(Xd, Td, off, count, cl.work(S))
+    params = ref_params(cl)
+    Xs = X[:, off:off + count].T.astype(np.float64)
+    Ts = T[:, off:off + count].T.astype(np.float64)
+    lb, gb = bf16_loss_and_grad(params, Xs, Ts)
+    flat = np.concatenate([a.ravel() for a in gb])
+    assert abs(loss - lb) < 1e-4 * lb
+    assert np.abs(grad - flat).max() < 2e-3 * np.abs(flat).max()
+    lref, gref = C.mlp_loss_and_grad(params, Xs, Ts)
+    exact = np.concatenate([a.ravel() for a in gref])
+    assert abs(loss - lref) < 1e-2 * lref
+    cos = float(grad @ exact / (np.linalg.norm(grad) * np.linalg.norm(exact)))
+    assert cos > 0.999, cos
 
 
 def bf16_forward(params, X):
@@ -164,13 +216,14 @@ def test_training_on_method_data_reduces_loss():
 
 
 def test_trained_closure_reduces_coarse_error_vs_fine():
-    """Gain test: trained on runs of the method itself (K = 128 fine, K = 24 coarse),
+    """Gain test: trained on runs of the method itself (K = 128 fine, K = 24 coarse;
+    tensor-core training, 4000 Adam steps of 16384 columns, cosine step decay),
     the corrected coarse run is closer to the fine run than the plain coarse run
     (relative L2, Eq. rel_err, of n and eps) on a Riemann problem not in the
     training set, at Kn = 0.3 and Kn = 1."""
     cl = R.Closure(N, K, seed=7)
     X, T = CL.generate(cl, 64, KF, kns=(0.02, 0.1, 0.5, 2.0), steps=48, every=2)
-    CL.train(cl, X, T, iters=1500, batch=8192, lr=2e-3)
+    CL.train(cl, X, T, iters=4000, batch=16384, lr=2e-3, decay=True)
     plain, learned = [], []
     for kn in (0.3, 1.0):
         mf, mc, ml = CL.deploy(cl, 64, KF, kn, 48)
@@ -178,4 +231,4 @@ def test_trained_closure_reduces_coarse_error_vs_fine():
             plain.append(CL.rel_l2(mc[i], mf[i]))
             learned.append(CL.rel_l2(ml[i], mf[i]))
     print("plain", plain, "learned", learned)
-    assert np.mean(learned) < 0.95 * np.mean(plain)
+    assert np.mean(learned) < 0.8 * np.mean(plain)
