@@ -288,7 +288,7 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
 // pitch a multiple of 16 bytes, buffers 16-byte aligned).  Requires nx even
 // (paired access) and a collision (tau finite).
 template <class St, int N, int PP, bool TWO_D, bool BULK>
-__global__ void __launch_bounds__(kMaxWarps * 32) rlbm_pair_kernel(const KernelArgs a)
+__global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_kernel(const KernelArgs a)
 {
     constexpr int NC = 2 * N + 1;
     constexpr int PQ = 3; // float4 per population in the pair table
