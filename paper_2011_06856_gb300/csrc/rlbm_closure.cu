@@ -465,6 +465,27 @@ __device__ __forceinline__ float gelu_as(float x)
     return x * (x >= 0.f ? 1.f - h : h);
 }
 
+// GELU of two values with packed f32x2 arithmetic (same formula as gelu_as)
+__device__ __forceinline__ float2 gelu2(float2 x)
+{
+    const float2 z = make_float2(fabsf(x.x) * 0.70710678118654752f, fabsf(x.y) * 0.70710678118654752f);
+    const float2 den = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), z, make_float2(1.f, 1.f));
+    float2 t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.x) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.y) : "f"(den.y));
+    float2 q = __ffma2_rn(make_float2(1.061405429f, 1.061405429f), t, make_float2(-1.453152027f, -1.453152027f));
+    q = __ffma2_rn(q, t, make_float2(1.421413741f, 1.421413741f));
+    q = __ffma2_rn(q, t, make_float2(-0.284496736f, -0.284496736f));
+    q = __ffma2_rn(q, t, make_float2(0.254829592f, 0.254829592f));
+    q = __fmul2_rn(q, t);
+    const float2 a = __fmul2_rn(__fmul2_rn(z, z), make_float2(-1.4426950408889634f, -1.4426950408889634f));
+    float2 e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(a.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(a.y));
+    const float2 xh = __fmul2_rn(x, __fmul2_rn(__fmul2_rn(q, e), make_float2(0.5f, 0.5f))); // x (1 - erf(z)) / 2
+    return make_float2(x.x >= 0.f ? x.x - xh.x : xh.x, x.y >= 0.f ? x.y - xh.y : xh.y);
+}
+
 // acc[nt][4] += A[16 x 16 KS] (row stride sa) x Bt[8 NT x 16 KS]^T (row stride sb)
 template <int KS, int NT>
 __device__ __forceinline__ void warp_gemm(const __nv_bfloat16 *A, int sa, const __nv_bfloat16 *Bt, int sb,
@@ -507,9 +528,10 @@ __device__ __forceinline__ void gelu_rows(float (*acc)[4], __nv_bfloat16 *h, int
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int c = nt * 8 + t * 2;
-        *reinterpret_cast<unsigned *>(h + g * SH + c) = pack_bf16(gelu_as(acc[nt][0]), gelu_as(acc[nt][1]));
-        *reinterpret_cast<unsigned *>(h + (g + 8) * SH + c) =
-            pack_bf16(gelu_as(acc[nt][2]), gelu_as(acc[nt][3]));
+        const float2 a = gelu2(make_float2(acc[nt][0], acc[nt][1]));
+        const float2 b = gelu2(make_float2(acc[nt][2], acc[nt][3]));
+        *reinterpret_cast<unsigned *>(h + g * SH + c) = pack_bf16(a.x, a.y);
+        *reinterpret_cast<unsigned *>(h + (g + 8) * SH + c) = pack_bf16(b.x, b.y);
     }
 }
 
@@ -581,8 +603,9 @@ __global__ void __launch_bounds__(TC_WARPS * 32, 1) apply_tc_kernel(Net net, Coa
     __nv_bfloat16 *w3h = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W3H); // [NPOP][SH]
     __nv_bfloat16 *w3l = reinterpret_cast<__nv_bfloat16 *>(sm + Gm::W3L); // [NPOP][SH]
     float *bias = reinterpret_cast<float *>(sm + Gm::BIAS);               // b1[64] b2[64] b3'[NPOP]
-    float2 *cs = reinterpret_cast<float2 *>(sm + Gm::TAB);                // (v_x, v_y) per population
-    float *invw = reinterpret_cast<float *>(cs + NPOP);
+    float *cvec = reinterpret_cast<float *>(sm + Gm::TAB);                // v_x per population
+    float *svec = cvec + NPOP;                                            // v_y per population
+    float *invw = svec + NPOP;
     float *wq = invw + NPOP;
     float *pr = wq + NPOP;                                                // p_r per shell
     float *wv = reinterpret_cast<float *>(sm + Gm::WV);                   // (W3 V^T)[64][4], V b3 [4]
@@ -604,7 +627,8 @@ __global__ void __launch_bounds__(TC_WARPS * 32, 1) apply_tc_kernel(Net net, Coa
     }
     for (int e = tid; e < 64; e += blockDim.x) { bias[e] = net.b1[e]; bias[64 + e] = net.b2[e]; }
     for (int e = tid; e < NPOP; e += blockDim.x) {
-        cs[e] = make_float2(q.c[e], q.s[e]);
+        cvec[e] = q.c[e];
+        svec[e] = q.s[e];
         invw[e] = 1.f / q.w[e];
         wq[e] = q.w[e];
     }
@@ -665,23 +689,27 @@ __global__ void __launch_bounds__(TC_WARPS * 32, 1) apply_tc_kernel(Net net, Coa
         // ---- features of the warp's 16 sites: this lane takes angles [half K/2, (half+1) K/2) of every shell
         const int col = wid * 16 + ls;
         const bool valid = site0 + col < S;
-        float v[N + 1][KH];
+        // populations in pairs (i, i+1): the angular sums run on packed f32x2 operands
+        float2 v[N + 1][KH / 2];
         float m[9];
 #pragma unroll
         for (int a0 = 0; a0 < 9; ++a0) m[a0] = 0.f;
 #pragma unroll
         for (int r = 0; r <= N; ++r) {
-            float s0 = 0.f, sc = 0.f, ss = 0.f, scc = 0.f, scs = 0.f, sss = 0.f;
+            float2 S0 = make_float2(0.f, 0.f), Sc = S0, Ss = S0, Scc = S0, Scs = S0, Sss = S0;
 #pragma unroll
-            for (int jj = 0; jj < KH; ++jj) {
+            for (int jj = 0; jj < KH; jj += 2) {
                 const int i = r * K + half * KH + jj;
-                const float x = cur[i * LDF + col];
-                const float2 d = cs[i];
-                v[r][jj] = x;
-                const float cx = d.x * x, sx = d.y * x;
-                s0 += x; sc += cx; ss += sx;
-                scc = fmaf(d.x, cx, scc); scs = fmaf(d.x, sx, scs); sss = fmaf(d.y, sx, sss);
+                const float2 x = make_float2(cur[i * LDF + col], cur[(i + 1) * LDF + col]);
+                const float2 cp = *reinterpret_cast<const float2 *>(cvec + i);
+                const float2 sp = *reinterpret_cast<const float2 *>(svec + i);
+                v[r][jj / 2] = x;
+                const float2 cx = __fmul2_rn(cp, x), sx = __fmul2_rn(sp, x);
+                S0 = __fadd2_rn(S0, x); Sc = __fadd2_rn(Sc, cx); Ss = __fadd2_rn(Ss, sx);
+                Scc = __ffma2_rn(cp, cx, Scc); Scs = __ffma2_rn(cp, sx, Scs); Sss = __ffma2_rn(sp, sx, Sss);
             }
+            const float s0 = S0.x + S0.y, sc = Sc.x + Sc.y, ss = Ss.x + Ss.y;
+            const float scc = Scc.x + Scc.y, scs = Scs.x + Scs.y, sss = Sss.x + Sss.y;
             const float p = pr[r], p2 = p * p;
             m[0] = fmaf(p, s0, m[0]); m[1] = fmaf(p, sc, m[1]); m[2] = fmaf(p, ss, m[2]);
             m[3] = fmaf(p2, s0, m[3]); m[4] = fmaf(p2, sc, m[4]); m[5] = fmaf(p2, ss, m[5]);
@@ -703,8 +731,8 @@ __global__ void __launch_bounds__(TC_WARPS * 32, 1) apply_tc_kernel(Net net, Coa
             for (int jj = 0; jj < KH; jj += 2) {
                 const int i = r * K + half * KH + jj;
                 const float2 iw = *reinterpret_cast<const float2 *>(invw + i);
-                *reinterpret_cast<unsigned *>(xr + 10 + i) =
-                    pack_bf16(v[r][jj] * iw.x * inv, v[r][jj + 1] * iw.y * inv);
+                const float2 sc2 = __fmul2_rn(__fmul2_rn(v[r][jj / 2], iw), make_float2(inv, inv));
+                *reinterpret_cast<unsigned *>(xr + 10 + i) = pack_bf16(sc2.x, sc2.y);
             }
         // zero padding of layer 1's k range (the hidden tile of the previous tile overlaps it)
         constexpr int PADP = (16 * Gm::KS1 - F) / 2;
