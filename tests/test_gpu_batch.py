@@ -123,3 +123,46 @@ def test_batch_mode_switch_keeps_the_state():
     b.set_mode("streams")
     with pytest.raises(R.RLBMError):
         b.test_stall_next_step()  # no barrier to stall in this mode
+
+
+@pytest.mark.parametrize("mode", ["streams", "persistent"])
+def test_full_batch_256_sampled_problems_one_step(mode):
+    """The batched benchmark workload at full size (256 uneven problems, FP32,
+    61.7 GB of populations) in both execution modes: four problems (the
+    smallest, the largest, a 64-row and a long 1D one) start from the oracle's
+    initial state (uploaded), the rest from the GPU initialisation; after one
+    batched step the four are checked against one oracle step, on whole 1D
+    problems and on interior rows of 2D ones (a three-row band reproduces its
+    middle row exactly)."""
+    probs = W.batch_problems(256)
+    specs = [(p.nx, p.ny, p.bcx, p.bcy, p.K, W.tau_from_kn(p.kn, p.nx)) for p in probs]
+    b = R.Batch(specs, N=2, precision="fp32")
+    b.set_mode(mode)
+    size = [nx * ny * K for (nx, ny, _, _, K, _) in specs]
+    picks = {int(np.argmin(size)), int(np.argmax(size))}
+    picks.add(next(i for i, s in enumerate(specs) if s[1] == 64))
+    picks.add(max((i for i, s in enumerate(specs) if s[1] == 1), key=lambda i: specs[i][0]))
+    states = {}
+    for i, (p, pb) in enumerate(zip(b.problems, probs)):
+        fl = W.shock_tube(pb.nx, pb.ny, pb.left, pb.right)
+        if i in picks:
+            q = O.Quadrature(2, pb.K)
+            f0 = q.init(fl.n, fl.T, fl.bx, fl.by).astype(np.float32)
+            p.set_populations(f0)
+            states[i] = (q, f0)
+        else:
+            p.init_fields(fl)
+    b.step(1)
+    b.sync()
+    for i, (q, f0) in states.items():
+        nx, ny, bcx, bcy, K, tau = specs[i]
+        got = b.problems[i].get_populations().astype(np.float64)
+        if ny == 1:
+            ref, _ = q.run(f0.astype(np.float64), tau, 1, bcx, bcy)
+            assert relerr(got, ref) < 2e-6, i
+        else:
+            for y in (1, ny // 2, ny - 2):
+                band = np.ascontiguousarray(f0[:, y - 1:y + 2, :].astype(np.float64))
+                ref, _ = q.run(band, tau, 1, bcx, bcy)
+                assert relerr(got[:, y, :], ref[:, 1, :]) < 2e-6, (i, y)
+    b.close()
