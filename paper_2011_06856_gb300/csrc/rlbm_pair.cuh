@@ -14,9 +14,10 @@
 //           pair; five per-shell angular sums S0, Sc, Ss, Scc, Scs of f*;
 //   site    two warps (one site per lane) fold the sums of all warps into
 //           N^a and T^ab (Eq. discrete_sum_moments), solve the Landau frame
-//           (landau_fast), and form the truncated-equilibrium coefficients of
-//           every shell (Eqs. mj-projection-coefficients,
+//           (landau_fast), and form the shell-independent part of the
+//           truncated-equilibrium coefficients (Eqs. mj-projection-coefficients,
 //           mj-feq-expansion-truncated) once per site, into shared memory;
+//           every warp then combines them into its own shell's coefficients;
 //   pass 2  f^eq_i and the relaxation f <- f* + omega_i (f^eq - f*)
 //           (Eq. discrete-rbe), one paired store per population.
 //
@@ -166,9 +167,10 @@ template <> struct PIo<__nv_bfloat16> {
 };
 
 // The per-site part for site s of the tile (FP32): moments from the warps'
-// angular sums, Landau frame, and the equilibrium coefficients of all N+1
-// shells (the boosted-direction sums acc are shared by the shells), written
-// to sres[(r NC + t) 64 + s]; then U^a / tau at rows (N+1) NC + 0..2.
+// angular sums, Landau frame, and the shell-independent part of the
+// equilibrium coefficients (the boosted-direction sums acc, weighted by
+// n T^(k-1)), written to sres[row 64 + s]; then U^a / tau at rows
+// (N+1)^2 + 0..2.  Every warp forms its own shell's coefficients from these.
 template <int N>
 __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float *red, int G, int s, bool act,
                                                 float *sres)
@@ -239,48 +241,21 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
     tk[0] = n / T;
 #pragma unroll
     for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
-    const float *rtab = reinterpret_cast<const float *>(a.rtab);
-    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
+    // shell-independent part of the coefficients, T^(k-1)-weighted: w_{m,k} = tk[k] acc_{m,k}
+    // (rows: Re for m = 0..N, k = m..N, then Im for m = 1..N; then U^a / tau)
+    int row = 0;
 #pragma unroll
-    for (int r = 0; r <= N; ++r) {
-        const float *rt = rtab + r * (N + 1) * (N + 1);
-        float cf[NC]; // Fourier coefficients: cf[0] = Re C_0 - offset, cf[2m-1], cf[2m] = Re, Im C_m
+    for (int mm = 0; mm <= N; ++mm)
 #pragma unroll
-        for (int mm = 0; mm <= N; ++mm) {
-            float cre = 0.f, cim = 0.f;
+        for (int k = mm; k <= N; ++k) sres[(row++) * kPairSites + s] = tk[k] * accr[mm][k];
 #pragma unroll
-            for (int k = mm; k <= N; ++k) {
-                const float wgt = __ldg(rt + mm * (N + 1) + k) * tk[k];
-                cre += wgt * accr[mm][k];
-                cim += wgt * acci[mm][k];
-            }
-            if (mm == 0) {
-                cf[0] = cre - a.feq_off_f;
-            } else {
-                cf[2 * mm - 1] = cre;
-                cf[2 * mm] = cim;
-            }
-        }
-        // coefficients of the basis (1, c, s, cc, cs [, c cc, s cc])
-        float b[NC];
-        b[0] = cf[0] - cf[3];
-        b[1] = cf[1];
-        b[2] = cf[2];
-        b[3] = 2.f * cf[3];
-        b[4] = 2.f * cf[4];
-        if (N == 3) {
-            b[1] -= 3.f * cf[NC - 2];
-            b[2] -= cf[NC - 1];
-            b[NC - 2] = 4.f * cf[NC - 2];
-            b[NC - 1] = 4.f * cf[NC - 1];
-        }
+    for (int mm = 1; mm <= N; ++mm)
 #pragma unroll
-        for (int t = 0; t < NC; ++t) sres[(r * NC + t) * kPairSites + s] = b[t];
-    }
+        for (int k = mm; k <= N; ++k) sres[(row++) * kPairSites + s] = tk[k] * acci[mm][k];
     const float itau = a.inv_tau_f;
-    sres[((N + 1) * NC + 0) * kPairSites + s] = U0 * itau;
-    sres[((N + 1) * NC + 1) * kPairSites + s] = Ux * itau;
-    sres[((N + 1) * NC + 2) * kPairSites + s] = Uy * itau;
+    sres[((N + 1) * (N + 1) + 0) * kPairSites + s] = U0 * itau;
+    sres[((N + 1) * (N + 1) + 1) * kPairSites + s] = Ux * itau;
+    sres[((N + 1) * (N + 1) + 2) * kPairSites + s] = Uy * itau;
 }
 
 // St: storage type; N: quadrature order; PP: populations per warp (K is a
@@ -305,7 +280,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
     const St *fin = reinterpret_cast<const St *>(a.fin);
     St *fout = reinterpret_cast<St *>(a.fout);
     float *red = reinterpret_cast<float *>(smem_raw); // [5][G][64]
-    float *sres = red + 5 * G * kPairSites;           // [(N+1) NC + 3][64]
+    float *sres = red + 5 * G * kPairSites;           // [(N+1)^2 + 3][64] used of [(N+1) NC + 3][64]
     const float4 *tb = reinterpret_cast<const float4 *>(a.pairtab) + size_t(i0) * PQ;
 
     const int xm = bc_index(xa - 1, a.nx, a.bcx), xp = bc_index(xa + 2, a.nx, a.bcx);
@@ -446,13 +421,52 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
     }
     __syncthreads();
 
+    // this warp's shell: Fourier coefficients C_{r,m} = sum_k R'[r][m][k] w_{m,k} of its two
+    // sites (packed), then the basis (1, c, s, cc, cs [, c cc, s cc]):
+    // cos 2t = 2 cc - 1, sin 2t = 2 cs, cos 3t = 4 c cc - 3 c, sin 3t = 4 s cc - s
+    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
     const float2 *sres2 = reinterpret_cast<const float2 *>(sres);
-    float2 cr[NC];
+    const float *rt = reinterpret_cast<const float *>(a.rtab) + r * (N + 1) * (N + 1);
+    float2 cf[NC];
+    {
+        int row = 0;
 #pragma unroll
-    for (int t = 0; t < NC; ++t) cr[t] = sres2[(r * NC + t) * 32 + lane];
-    const float2 o0 = sres2[((N + 1) * NC + 0) * 32 + lane];
-    const float2 o1 = sres2[((N + 1) * NC + 1) * 32 + lane];
-    const float2 o2 = sres2[((N + 1) * NC + 2) * 32 + lane];
+        for (int mm = 0; mm <= N; ++mm) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float w = __ldg(rt + mm * (N + 1) + k);
+                acc = __ffma2_rn(f2(w, w), sres2[(row++) * 32 + lane], acc);
+            }
+            if (mm == 0) cf[0] = __fadd2_rn(acc, f2(-a.feq_off_f, -a.feq_off_f));
+            else cf[2 * mm - 1] = acc;
+        }
+#pragma unroll
+        for (int mm = 1; mm <= N; ++mm) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float w = __ldg(rt + mm * (N + 1) + k);
+                acc = __ffma2_rn(f2(w, w), sres2[(row++) * 32 + lane], acc);
+            }
+            cf[2 * mm] = acc;
+        }
+    }
+    float2 cr[NC];
+    cr[0] = f2sub(cf[0], cf[3]);
+    cr[1] = cf[1];
+    cr[2] = cf[2];
+    cr[3] = __fmul2_rn(f2(2.f, 2.f), cf[3]);
+    cr[4] = __fmul2_rn(f2(2.f, 2.f), cf[4]);
+    if (N == 3) {
+        cr[1] = __ffma2_rn(f2(-3.f, -3.f), cf[NC - 2], cr[1]);
+        cr[2] = f2sub(cr[2], cf[NC - 1]);
+        cr[NC - 2] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 2]);
+        cr[NC - 1] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 1]);
+    }
+    const float2 o0 = sres2[((N + 1) * (N + 1) + 0) * 32 + lane];
+    const float2 o1 = sres2[((N + 1) * (N + 1) + 1) * 32 + lane];
+    const float2 o2 = sres2[((N + 1) * (N + 1) + 2) * 32 + lane];
     const float2 no1 = f2(-o1.x, -o1.y), no2 = f2(-o2.x, -o2.y);
     constexpr bool kSR = sizeof(St) == 2;
     unsigned rng = 0;
