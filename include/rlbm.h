@@ -89,6 +89,10 @@ size_t rlbm_population_bytes(rlbm_grid grid, int order_N, int angles_K, int prec
 
 /* Create a handle for one problem.  Validates N >= 2, K >= 2N+1, nx, ny >= 1,
  * tau > 0 (or +INFINITY), bc values and precision; RLBM_ERR_ARG otherwise.
+ * RLBM_ERR_UNSUPPORTED for N > 5 (the kernels are compiled for N = 2..5; the
+ * two-sites-per-lane, TMA-staged and batched kernels for N = 2, 3) and for K
+ * beyond one population group per warp in 16-bit storage
+ * (rlbm_population_groups).
  * dev_buffers: optional caller-owned device memory of at least
  * 2 * rlbm_population_bytes() bytes, 256-byte aligned, holding both
  * population buffers (it must outlive the handle); NULL makes the library
@@ -174,6 +178,15 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind);
 /* Populations per warp of the handle's current tiling (the tile is 32 sites
  * of one row x all populations; G = ceil(K / P) (N+1) warps per CTA). */
 int rlbm_tile_populations(const rlbm_t *h);
+
+/* Groups of P populations each warp of the per-tile kernel owns: 1, unless K
+ * exceeds what one group per warp holds (K > 64 floor(16 / (N+1)), e.g. the
+ * paper's K = 600 reference runs with N = 3).  Then floor(16 / (N+1)) warps
+ * per shell own ceil(K / (warps P)) groups each; the streamed values of all
+ * but the last group are parked in the output buffer between the two passes
+ * (FP32 and FP64 storage; rlbm_create refuses such K in 16-bit storage), and
+ * only the per-tile kernel applies.  -1 for a NULL handle. */
+int rlbm_population_groups(const rlbm_t *h);
 
 /* Autotuner: time every compiled tiling of the step kernel (P populations per
  * warp in {8,12,16,24,32,48,64} that fits K and N, each with the two-sites-

@@ -20,6 +20,7 @@ struct KernelArgs {
     long long S;
     int K, Gs;      // angles per shell, warps per shell
     int P;          // populations per warp (the last warp of a shell may own fewer)
+    int R;          // groups of P populations per warp (many angles); 0 or 1: one group
     int bcx, bcy;   // 0 periodic, 1 copy-out
     int collide;    // 0 for tau = +inf (free streaming)
     double inv_tau;
@@ -120,6 +121,15 @@ cudaError_t launch_f16(int mode, int N, int P, bool two_d, bool full, dim3 grid,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_bf16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t st, const KernelArgs &a);
+// The same per-tile kernel for N = 4, 5, with FP64 per-site arithmetic in every storage type.
+cudaError_t launch_f64_n45(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_f32_n45(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_f16_n45(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_bf16_n45(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                            size_t smem, cudaStream_t st, const KernelArgs &a);
 // Two-sites-per-lane step kernel (rlbm_pair.cuh): 64-site tiles, PP in {8, 12, 16, 24, 32};
 // bulk: interior tiles staged through shared memory by cp.async.bulk.
 #define RLBM_DECLARE_PAIR(name)                                                                          \

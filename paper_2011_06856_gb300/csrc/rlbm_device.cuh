@@ -20,6 +20,14 @@
 // Populations are read once and written once per step; halo values of the
 // neighbouring tile come through L1/L2.  All per-population constants are
 // warp-uniform loads of a small table (L1 resident).
+//
+// Many angles (K beyond what 16 warps of at most 64 populations hold): warp
+// (r, q) then owns a.R groups of P populations of its shell, group rho being
+// "virtual warp" v = rho Gs + q (populations r K + v P + k).  Pass 1 streams
+// the groups one after another and parks the streamed values f* of all but
+// the last group in their own output slots (same thread, same address: no
+// synchronisation needed); pass 2 handles the last group from registers and
+// reads the others back.  FP32 and FP64 storage only (f* is parked exactly).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -360,12 +368,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     const int x = act ? xr : a.nx - 1;
     const int y = blockIdx.y;
     const int r = g / a.Gs, q = g % a.Gs;
-    const int i0 = r * a.K + q * a.P;
-    // populations of this warp (FULL: K is a multiple of P, every warp owns P)
-    const int pc = FULL ? P : min(a.P, a.K - q * a.P);
+    const int NR = a.R > 1 ? a.R : 1; // groups of P populations per warp
+    const int Gv = a.Gs * NR;         // virtual warps per shell
     const long long S = a.S;
     const long long site = (long long)y * a.nx + x;
-    const R *tab = reinterpret_cast<const R *>(a.poptab) + (long long)i0 * TW;
     const St *fin = reinterpret_cast<const St *>(a.fin);
     St *fout = reinterpret_cast<St *>(a.fout);
     LR *red = reinterpret_cast<LR *>(smem_raw); // [5][G][32]
@@ -381,10 +387,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         const int xm = bc_index(x - 1, a.nx, a.bcx), xp = bc_index(x + 1, a.nx, a.bcx);
         const int ym = TWO_D ? bc_index(y - 1, a.ny, a.bcy) : y;
         const int yp = TWO_D ? bc_index(y + 1, a.ny, a.bcy) : y;
-        const unsigned long long mx = stream ? __ldg(a.masks + 2 * g) : 0ull;
-        const unsigned long long my = stream ? __ldg(a.masks + 2 * g + 1) : 0ull;
-        const St *base = fin + (long long)i0 * S + (long long)y * a.nx;
         const long long dym = (long long)(ym - y) * a.nx, dyp = (long long)(yp - y) * a.nx;
+#pragma unroll 1
+        for (int rho = 0; rho < NR; ++rho) {
+        const int vw = rho * a.Gs + q;
+        const int i0 = r * a.K + vw * a.P;
+        // populations of this group (FULL: every group owns exactly P)
+        const int pc = FULL ? P : min(a.P, a.K - vw * a.P);
+        const R *tab = reinterpret_cast<const R *>(a.poptab) + (long long)i0 * TW;
+        const unsigned long long mx = stream ? __ldg(a.masks + 2 * (r * Gv + vw)) : 0ull;
+        const unsigned long long my = stream ? __ldg(a.masks + 2 * (r * Gv + vw) + 1) : 0ull;
+        const St *base = fin + (long long)i0 * S + (long long)y * a.nx;
         // Loads first (a chunk of populations at a time, all independent), then
         // arithmetic: the pull direction of population k comes from the warp's
         // sign masks, so no load waits for the table.
@@ -432,6 +445,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
                 }
             }
         }
+        // free streaming stores every group now; a collision parks all groups but the last
+        if (MODE == MODE_STEP && (!need_site || rho + 1 < NR) && act) {
+            St *ob = fout + (long long)i0 * S + site;
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+                if (k < pc) Io<St, R>::st(ob + (long long)k * S, fs[k]);
+        }
+        } // groups
         if (need_site) {
             red[(0 * G + g) * 32 + lane] = LR(s0[0] + s0[1]);
             red[(1 * G + g) * 32 + lane] = LR(sc[0] + sc[1]);
@@ -441,15 +462,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         }
     }
 
-    St *obase = fout + (long long)i0 * S + site;
-    if (!need_site) { // free streaming: f <- f*
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < P; ++k)
-                if (k < pc) Io<St, R>::st(obase + (long long)k * S, fs[k]);
-        }
-        return;
-    }
+    if (!need_site) return; // free streaming: f <- f*, stored above
     if (MODE != MODE_INIT) __syncthreads();
     if (MODE == MODE_MOMENTS && g != 0) return;
 
@@ -489,6 +502,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     constexpr bool kSR = (sizeof(St) == 2) && (MODE == MODE_STEP);
     unsigned rng = 0;
     if (kSR) rng = mix32(unsigned(site) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
+#pragma unroll 1
+    for (int rho = NR - 1; rho >= 0; --rho) {
+    const int vw = rho * a.Gs + q;
+    const int i0 = r * a.K + vw * a.P;
+    const int pc = FULL ? P : min(a.P, a.K - vw * a.P);
+    const R *tab = reinterpret_cast<const R *>(a.poptab) + (long long)i0 * TW;
+    St *obase = fout + (long long)i0 * S + site;
+    if (MODE == MODE_STEP && rho + 1 < NR && act) { // parked group: f* back from its output slot
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            if (k < pc) fs[k] = Io<St, R>::lds(obase + (long long)k * S);
+    }
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         if (k < pc) {
@@ -515,6 +540,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
             }
         }
     }
+    } // groups
     if (kSR) {
         __syncthreads();
         if (threadIdx.x == 0 && threadIdx.y == 0) advance_launch_counter(a.ctr, gridDim.x * gridDim.y);

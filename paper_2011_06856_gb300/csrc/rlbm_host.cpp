@@ -197,6 +197,7 @@ struct rlbm {
     int *d_status = nullptr;
     rlbmk::KernelArgs base{};
     int P = 0, Gs = 0, G = 0;
+    int R = 1; // groups of P populations per warp (K beyond one group per warp)
     bool site_fp64 = false;
     // CUDA graphs of kGraphSteps steps starting from buffer 0 / buffer 1
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -244,9 +245,39 @@ rlbm_status cuda_fail(rlbm_t *h, cudaError_t e, const char *what)
 // Pick P (populations per warp, one of the compiled sizes) and Gs (warps per
 // energy shell, G = Gs (N+1) warps per CTA): fewest idle population slots,
 // then the larger P (fewer warps sharing the per-site work).
-bool choose_tiling(int N, int K, int &P, int &Gs)
+// Warps per shell and groups per warp of a tiling with P populations per
+// warp: one group while ceil(K / P) warps per shell fit the CTA, otherwise
+// as many warps as fit and several groups, but only when K exceeds what one
+// group per warp can hold at all (K > 64 floor(16 / (N+1))).
+int single_group_capacity(int N) { return 64 * (rlbmk::kMaxWarps / (N + 1)); }
+bool group_tiling(int N, int K, int P, int &Gs, int &R)
+{
+    const int gs = (K + P - 1) / P;
+    if (gs * (N + 1) <= rlbmk::kMaxWarps && (gs - 1) * P < K) {
+        Gs = gs;
+        R = 1;
+        return true;
+    }
+    if (K <= single_group_capacity(N)) return false;
+    Gs = rlbmk::kMaxWarps / (N + 1);
+    R = (K + Gs * P - 1) / (Gs * P); // trailing groups may be empty (the kernel skips them)
+    return true;
+}
+
+bool choose_tiling(int N, int K, int &P, int &Gs, int &R)
 {
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
+    R = 1;
+    if (K > single_group_capacity(N)) { // fewest groups, then least padding
+        int best = 1 << 30;
+        for (int p : sizes) {
+            int gs = 0, r = 0;
+            if (!group_tiling(N, K, p, gs, r)) continue;
+            const int score = r * 4096 + (r * gs * p - K);
+            if (score < best) { best = score; P = p; Gs = gs; R = r; }
+        }
+        return best < (1 << 30);
+    }
     int best_waste = 1 << 30;
     bool found = false;
     for (int gs = 1; gs * (N + 1) <= rlbmk::kMaxWarps; ++gs) {
@@ -348,11 +379,13 @@ rlbm_status build_tables(rlbm_t *h)
     // per-warp sign masks of the populations it owns
     static_assert(sizeof(unsigned long long) == 8, "64-bit masks");
     if (h->P > 64) return fail(h, RLBM_ERR_UNSUPPORTED, "at most 64 populations per warp");
-    std::vector<unsigned long long> masks(size_t(h->G) * 2, 0ull);
-    for (int g = 0; g < h->G; ++g) {
-        const int r = g / h->Gs, qq = g % h->Gs;
+    // (one pair per group of populations: virtual warp v of shell r at r Gs R + v)
+    const int Gv = h->Gs * h->R;
+    std::vector<unsigned long long> masks(size_t(N + 1) * Gv * 2, 0ull);
+    for (int g = 0; g < (N + 1) * Gv; ++g) {
+        const int r = g / Gv, vv = g % Gv;
         for (int k = 0; k < h->P; ++k) {
-            const int j = qq * h->P + k;
+            const int j = vv * h->P + k;
             if (j >= K) break;
             const int i = r * K + j;
             if (q.vx[i] >= 0.0) masks[2 * g] |= 1ull << k;
@@ -411,6 +444,7 @@ rlbm_status build_tables(rlbm_t *h)
     a.K = K;
     a.Gs = h->Gs;
     a.P = h->P;
+    a.R = h->R;
     a.bcx = h->grid.bc_x;
     a.bcy = h->grid.bc_y;
     a.collide = std::isinf(h->tau) ? 0 : 1;
@@ -456,7 +490,7 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     const dim3 block(32, h->G);
     const size_t smem = smem_bytes(h);
     const bool two_d = h->grid.ny > 1;
-    const bool full = (h->K % h->P) == 0;
+    const bool full = h->K == h->R * h->Gs * h->P;
     cudaError_t e;
     switch (h->prec) {
     case RLBM_FP64: e = rlbmk::launch_f64(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
@@ -475,7 +509,7 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
 // collision, an even row length, K a multiple of P and P in {8, 12, 16, 24, 32}.
 bool pair_possible(const rlbm_t *h, int P)
 {
-    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau)) return false;
+    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3) return false;
     if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
     if (!(P == 8 || P == 12 || P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
     return (h->K / P) * (h->N + 1) <= rlbmk::kMaxWarps;
@@ -559,7 +593,7 @@ rlbm_status setup_tma(rlbm_t *h)
     delete[] h->tma;
     h->tma = nullptr;
     const char *off = std::getenv("RLBM_NO_TMA");
-    if ((off && off[0] == '1') || h->no_tma) return RLBM_OK;
+    if ((off && off[0] == '1') || h->no_tma || h->N > 3 || h->R > 1) return RLBM_OK;
     const size_t es = storage_size(h->prec);
     const int HX = int(16 / es), BW = 32 + 2 * HX;
     const int nx = h->grid.nx, ny = h->grid.ny, npop = h->npop;
@@ -683,7 +717,10 @@ rlbm_status retile(rlbm_t *h, int P, int kind)
     for (auto &g : h->graph)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     h->P = P;
-    h->Gs = (h->K + P - 1) / P;
+    if (!group_tiling(h->N, h->K, P, h->Gs, h->R)) {
+        h->Gs = (h->K + P - 1) / P;
+        h->R = 1;
+    }
     h->G = h->Gs * (h->N + 1);
     h->no_tma = kind != 1;
     h->use_pair = (kind == 2 || kind == 3) && pair_possible(h, P);
@@ -759,8 +796,9 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
     if (!(tau > 0.0)) return fail(nullptr, RLBM_ERR_ARG, "tau must be > 0 or +inf (got %g)", tau);
     if (storage_size(precision) == 0)
         return fail(nullptr, RLBM_ERR_ARG, "unknown precision %d", precision);
-    if (order_N > 3)
-        return fail(nullptr, RLBM_ERR_UNSUPPORTED, "kernels are built for N = 2, 3 (got N=%d)", order_N);
+    if (order_N > rlbmk::kMaxN)
+        return fail(nullptr, RLBM_ERR_UNSUPPORTED, "kernels are built for N = 2..%d (got N=%d)", rlbmk::kMaxN,
+                    order_N);
 
     rlbm_t *h = new (std::nothrow) rlbm();
     if (!h) return fail(nullptr, RLBM_ERR_OOM, "host allocation failed");
@@ -771,14 +809,25 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
     h->prec = precision;
     h->tau = tau;
     const char *env = std::getenv("RLBM_FP32_SITE_FP64");
-    h->site_fp64 = (precision == RLBM_FP32) && env && env[0] == '1';
+    // N >= 4: the radial projection weights (inverse of a factorial Gram matrix)
+    // cancel too many digits for FP32 per-site arithmetic, so the per-site part
+    // runs in FP64 for every storage type
+    h->site_fp64 = (precision != RLBM_FP64) &&
+                   (order_N >= 4 || ((precision == RLBM_FP32) && env && env[0] == '1'));
     if (!make_quadrature(order_N, angles_K, h->q)) {
         delete h;
         return fail(nullptr, RLBM_ERR_ARG, "quadrature construction failed");
     }
-    if (!choose_tiling(order_N, angles_K, h->P, h->Gs)) {
+    if (!choose_tiling(order_N, angles_K, h->P, h->Gs, h->R)) {
         delete h;
         return fail(nullptr, RLBM_ERR_UNSUPPORTED, "no compiled tiling for K=%d", angles_K);
+    }
+    if (h->R > 1 && storage_size(precision) == 2) {
+        delete h;
+        return fail(nullptr, RLBM_ERR_UNSUPPORTED,
+                    "K=%d needs several population groups per warp, built for FP32 and FP64 storage only "
+                    "(at most %d angles with N=%d in 16-bit storage)",
+                    angles_K, single_group_capacity(order_N), order_N);
     }
     if (const char *ep = std::getenv("RLBM_TILE_P")) { // experiment hook: force P if it fits
         const int P = std::atoi(ep);
@@ -999,9 +1048,12 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
     bool ok = false;
     for (int v : sizes) ok = ok || v == P;
-    const int gs = ok ? (h->K + P - 1) / P : 0;
-    if (!ok || gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K)
+    int gs = 0, ng = 0;
+    if (!ok || !group_tiling(h->N, h->K, P, gs, ng))
         return fail(h, RLBM_ERR_UNSUPPORTED, "no compiled tiling with P=%d for N=%d, K=%d", P, h->N, h->K);
+    if (ng > 1 && kind != 0)
+        return fail(h, RLBM_ERR_UNSUPPORTED, "K=%d needs several population groups per warp: per-tile kernel only",
+                    h->K);
     if ((kind == 2 || kind == 3) && !pair_possible(h, P)) {
         rlbm_status st0 = retile(h, P, 0);
         if (st0) return st0;
@@ -1021,6 +1073,8 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
 }
 
 int rlbm_tile_populations(const rlbm_t *h) { return h ? h->P : -1; }
+
+int rlbm_population_groups(const rlbm_t *h) { return h ? h->R : -1; }
 
 rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
 {
@@ -1045,8 +1099,8 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
     const long long launches0 = h->launches;
     rlbm_status st = RLBM_OK;
     for (int P : sizes) {
-        const int gs = (h->K + P - 1) / P;
-        if (gs * (h->N + 1) > rlbmk::kMaxWarps || (gs - 1) * P >= h->K) continue;
+        int gs = 0, ng = 0;
+        if (!group_tiling(h->N, h->K, P, gs, ng)) continue;
         if (P > 2 * h->K) continue;
         for (int kind = 3; kind >= 0 && st == RLBM_OK; --kind) {
             st = retile(h, P, kind);
@@ -1299,8 +1353,8 @@ void solo_default(const rlbm_t *h, int &P, int &kind)
     static const int sizes[] = {8, 12, 16, 24, 32};
     for (int v : sizes)
         if (pair_possible(h, v)) { P = v; kind = pair_bulk_possible(h) ? 3 : 2; return; }
-    int gs = 0;
-    choose_tiling(h->N, h->K, P, gs);
+    int gs = 0, ng = 0;
+    choose_tiling(h->N, h->K, P, gs, ng);
     kind = 0;
 }
 

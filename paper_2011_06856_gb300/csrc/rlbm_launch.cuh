@@ -48,6 +48,7 @@ static cudaError_t launch_n(int mode, int P, bool two_d, bool full, dim3 grid, d
     }
 }
 
+// N = 2, 3 here; N = 4, 5 (launch_t_hi) live in their own units (rlbm_k*_n45.cu).
 template <class St, class R, class LR>
 static cudaError_t launch_t(int mode, int N, int P, bool two_d, bool full, dim3 grid,
                            dim3 block, size_t smem, cudaStream_t st, const KernelArgs &a)
@@ -55,6 +56,17 @@ static cudaError_t launch_t(int mode, int N, int P, bool two_d, bool full, dim3 
     switch (N) {
     case 2: return launch_n<St, R, LR, 2>(mode, P, two_d, full, grid, block, smem, st, a);
     case 3: return launch_n<St, R, LR, 3>(mode, P, two_d, full, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class St, class R, class LR>
+static cudaError_t launch_t_hi(int mode, int N, int P, bool two_d, bool full, dim3 grid,
+                              dim3 block, size_t smem, cudaStream_t st, const KernelArgs &a)
+{
+    switch (N) {
+    case 4: return launch_n<St, R, LR, 4>(mode, P, two_d, full, grid, block, smem, st, a);
+    case 5: return launch_n<St, R, LR, 5>(mode, P, two_d, full, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
     }
 }

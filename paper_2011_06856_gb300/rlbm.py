@@ -31,7 +31,7 @@ EXPORTS = [
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
     "rlbm_step_kernel_variant", "rlbm_set_wait_limit", "rlbm_test_stall_next_step",
-    "rlbm_tile_populations", "rlbm_autotune", "rlbm_set_tiling",
+    "rlbm_tile_populations", "rlbm_population_groups", "rlbm_autotune", "rlbm_set_tiling",
     "rlbm_batch_arena_bytes", "rlbm_batch_create", "rlbm_batch_destroy", "rlbm_batch_last_error",
     "rlbm_batch_count", "rlbm_batch_problem", "rlbm_batch_step", "rlbm_batch_sync",
     "rlbm_batch_kernel_launches", "rlbm_batch_autotune", "rlbm_batch_set_wait_limit",
@@ -123,6 +123,8 @@ def lib(path: str = LIB_PATH):
     L.rlbm_test_stall_next_step.argtypes = [_vp]
     L.rlbm_tile_populations.restype = ctypes.c_int
     L.rlbm_tile_populations.argtypes = [_vp]
+    L.rlbm_population_groups.restype = ctypes.c_int
+    L.rlbm_population_groups.argtypes = [_vp]
     L.rlbm_set_tiling.restype = st
     L.rlbm_set_tiling.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.rlbm_autotune.restype = st
@@ -349,6 +351,12 @@ class Simulation:
     @property
     def tile_populations(self) -> int:
         return lib().rlbm_tile_populations(self._h)
+
+    @property
+    def population_groups(self) -> int:
+        """Groups of tile_populations populations per warp (> 1 only for K beyond
+        one group per warp, see rlbm_population_groups)."""
+        return lib().rlbm_population_groups(self._h)
 
     KERNELS = ("per-tile", "tma", "pair", "pair-bulk")
 

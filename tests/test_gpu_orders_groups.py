@@ -1,0 +1,207 @@
+"""GPU parity for quadrature orders N = 4, 5 and for many angles (several
+groups of populations per warp), against the FP64 oracle.
+
+The paper's 1D runs (Sec. 3.1) use N = 3 with K up to 120 on 2000x1, N = 5 with
+K = 12, and a K = 600 (N_pop = 2400) reference on 4000x1.  K beyond 64
+floor(16 / (N+1)) angles per shell makes every warp own several groups of
+populations (rlbm_population_groups > 1).  Tolerances as in the other parity
+tests: 1e-12 normwise in FP64, the FP32 bound max(1e-5, b omega_max steps).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import appendix_a as A
+from paper_2011_06856_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2011_06856_gb300 import build as B  # noqa: E402
+from paper_2011_06856_gb300 import rlbm as R  # noqa: E402
+
+B.build()
+
+FP64_TOL = 1e-12
+FP32_BIAS = 4e-7
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def fields_err(got, ref):
+    """Largest normwise error over n, eps, T, U^0 and the spatial U (one shared scale)."""
+    e = [relerr(got[i], ref[i]) for i in range(4)]
+    us = max(np.abs(ref[4:6]).max(), 1e-300)
+    e.append(np.abs(got[4:6] - ref[4:6]).max() / us)
+    return max(e)
+
+
+def oracle_run(N, K, fl, tau, steps, bcx, bcy):
+    q = O.Quadrature(N, K)
+    f, flagged = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), tau, steps, bcx, bcy)
+    assert flagged == 0
+    mac, _ = q.macro(f)
+    return f, mac
+
+
+def gpu_run(N, K, fl, tau, steps, bcx, bcy, precision="fp64", P=None):
+    ny, nx = fl.shape
+    sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
+    if P is not None:
+        sim.set_tiling(P, "per-tile")
+    sim.init_fields(fl)
+    sim.step(steps)
+    return sim, sim.moments()
+
+
+# ------------------------------------------------------------ N = 4, 5
+
+@pytest.mark.parametrize("N,K", [(4, 9), (4, 16), (4, 40), (5, 12), (5, 24), (5, 100)])
+def test_fp64_higher_orders_2d_ragged(N, K):
+    """Random smooth fields on 70x37 (ragged x tail), copy-out, 6 steps."""
+    nx, ny, steps, tau = 70, 37, 6, 3.0
+    fl = W.random_fields(nx, ny, seed=11 + K + N)
+    f_ref, mac_ref = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    sim, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    assert sim.population_groups == 1
+    assert sim.step_kernel == "per-tile"
+    assert fields_err(mac, mac_ref) < FP64_TOL
+    assert relerr(sim.get_populations(), f_ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16n", "bf16n"])
+def test_higher_order_reduced_precision(precision):
+    """N = 5, K = 12 in FP32 and 16-bit storage (tolerances of the other parity tests)."""
+    nx, ny, N, K, steps, tau = 96, 5, 5, 12, 20, 4.0
+    fl = W.shock_tube(nx, ny, (1.5, 1.5), (0.1, 0.5))
+    _, mac_ref = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    _, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, precision)
+    tol = {"fp32": max(1e-5, FP32_BIAS * 1.2 / tau * steps), "fp16n": 3e-3, "bf16n": 2.4e-2}[precision]
+    for i in range(3):
+        assert relerr(mac[i], mac_ref[i]) < tol, (precision, i)
+
+
+def test_higher_order_free_streaming():
+    """N = 5, K = 12, tau = inf: every population shifts by its own bilinear pull."""
+    nx, ny, N, K, steps = 130, 3, 5, 12, 40
+    q = O.Quadrature(N, K)
+    f0 = W.random_populations(q.npop, ny, nx, seed=9) * q.w[:, None, None]
+    ref, _ = q.run(f0, math.inf, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim = R.Simulation(nx, ny, N, K, math.inf, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    sim.set_populations(f0)
+    sim.step(steps)
+    assert relerr(sim.get_populations(), ref) < FP64_TOL
+
+
+# ------------------------------------------------------------ several groups per warp
+
+GROUP_CASES = [  # N, K, nx, ny, bcx, bcy
+    (3, 600, 40, 1, W.BC_COPYOUT, W.BC_PERIODIC),   # the paper's reference rule, N_pop = 2400
+    (3, 300, 33, 3, W.BC_PERIODIC, W.BC_COPYOUT),   # ragged tile, empty trailing groups
+    (2, 400, 20, 5, W.BC_COPYOUT, W.BC_COPYOUT),
+    (5, 200, 17, 2, W.BC_PERIODIC, W.BC_PERIODIC),
+    (3, 257, 64, 2, W.BC_COPYOUT, W.BC_PERIODIC),   # one angle beyond one group per warp
+]
+
+
+@pytest.mark.parametrize("N,K,nx,ny,bcx,bcy", GROUP_CASES)
+def test_fp64_population_groups(N, K, nx, ny, bcx, bcy):
+    steps, tau = 5, 2.5
+    fl = W.random_fields(nx, ny, seed=K + nx)
+    f_ref, mac_ref = oracle_run(N, K, fl, tau, steps, bcx, bcy)
+    sim, mac = gpu_run(N, K, fl, tau, steps, bcx, bcy)
+    assert sim.population_groups > 1
+    assert fields_err(mac, mac_ref) < FP64_TOL
+    assert relerr(sim.get_populations(), f_ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("P", [8, 16, 24, 32, 48, 64])
+def test_fp64_population_groups_every_tiling(P):
+    """K = 600, N = 3 with every group size; groups = ceil(600 / (4 P))."""
+    N, K, nx, ny, steps, tau = 3, 600, 24, 2, 3, 1.5
+    fl = W.random_fields(nx, ny, seed=5)
+    f_ref, _ = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim, _ = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, P=P)
+    assert sim.tile_populations == P
+    assert sim.population_groups == -(-K // (4 * P))
+    assert relerr(sim.get_populations(), f_ref) < FP64_TOL
+
+
+def test_fp32_population_groups():
+    N, K, nx, ny, steps = 3, 600, 64, 2, 30
+    tau = 3.0
+    fl = W.shock_tube(nx, ny, (1.5, 1.5), (0.1, 0.5))
+    _, mac_ref = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
+    assert sim.population_groups > 1
+    tol = max(1e-5, FP32_BIAS * 1.2 / tau * steps)
+    for i in range(3):
+        assert relerr(mac[i], mac_ref[i]) < tol, i
+
+
+def test_population_groups_free_streaming_and_init():
+    """tau = inf stores every group in pass 1; init and moments run the group loop too."""
+    N, K, nx, ny, steps = 3, 600, 50, 1, 25
+    q = O.Quadrature(N, K)
+    f0 = W.random_populations(q.npop, ny, nx, seed=21) * q.w[:, None, None]
+    ref, _ = q.run(f0, math.inf, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim = R.Simulation(nx, ny, N, K, math.inf, "fp64", W.BC_COPYOUT, W.BC_PERIODIC)
+    assert sim.population_groups > 1
+    sim.set_populations(f0)
+    sim.step(steps)
+    assert relerr(sim.get_populations(), ref) < FP64_TOL
+    fl = W.random_fields(nx, ny, seed=2, beta_max=0.5)
+    sim.init_fields(fl)
+    assert relerr(sim.get_populations(), q.init(fl.n, fl.T, fl.bx, fl.by)) < 1e-13
+    mac = sim.moments()
+    np.testing.assert_allclose(mac[0], fl.n, rtol=1e-12)
+    np.testing.assert_allclose(mac[2], fl.T, rtol=1e-12)
+
+
+def test_population_groups_refusals_and_autotune():
+    with pytest.raises(R.RLBMError) as e:
+        R.Simulation(32, 1, 3, 600, 2.0, "fp16n")
+    assert e.value.status == R.ERR_UNSUPPORTED
+    sim = R.Simulation(64, 2, 3, 600, 2.0, "fp32")
+    with pytest.raises(R.RLBMError) as e:
+        sim.set_tiling(32, "pair")
+    assert e.value.status == R.ERR_UNSUPPORTED
+    assert sim.step_kernel == "per-tile"
+    fl = W.shock_tube(64, 2, (1.5, 1.5), (0.1, 0.5))
+    sim.init_fields(fl)
+    sim.autotune(2)
+    assert sim.step_kernel == "per-tile" and sim.population_groups > 1
+    sim.step(4)
+    sim.moments()
+
+
+# ------------------------------------------------------------ the paper's Fig. 2 runs
+
+def appendix_a_beta(nx, steps):
+    x = np.arange(nx) + 0.5 - nx / 2
+    cont = A.continuum_moments(x / steps, 1.5, 2.25, 0.1, 0.05)
+    return np.array([(lambda m: m[4] / m[3])(O.landau(cont[:, s])[1]) for s in range(nx)])
+
+
+@pytest.mark.parametrize("N,K", [(3, 12), (5, 12), (3, 120)])
+def test_fig2_sod_free_streaming_2000x1(N, K):
+    """Sec. 3.1, Fig. 2: 2000x1, tau -> inf, 900 steps (t/t_max = 0.9): the
+    library equals the oracle (FP64), and the FP32 run gives the same error
+    against Appendix A (Eq. rel_err) to 1e-4."""
+    nx, steps = 2000, 900
+    fl = W.shock_tube(nx, 1, (1.5, 1.5), (0.1, 0.5))
+    f_ref, mac_ref = oracle_run(N, K, fl, math.inf, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim, mac = gpu_run(N, K, fl, math.inf, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    assert fields_err(mac, mac_ref) < FP64_TOL
+    bref = appendix_a_beta(nx, steps)
+    e_ref = np.linalg.norm(mac_ref[4, 0] / mac_ref[3, 0] - bref) / np.linalg.norm(bref)
+    _, mac32 = gpu_run(N, K, fl, math.inf, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
+    e32 = np.linalg.norm(mac32[4, 0] / mac32[3, 0] - bref) / np.linalg.norm(bref)
+    assert abs(e32 - e_ref) < 1e-4, (e32, e_ref)

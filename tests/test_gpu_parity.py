@@ -370,7 +370,7 @@ def test_unphysical_state_is_reported_not_trapped():
 
 def test_many_handles_and_unsupported_order():
     with pytest.raises(R.RLBMError) as e:
-        R.Simulation(16, 1, 5, 12, 1.0)
+        R.Simulation(16, 1, 6, 16, 1.0)
     assert e.value.status == R.ERR_UNSUPPORTED
     sims = [R.Simulation(32, 2, 2, 16, 2.0, "fp32") for _ in range(8)]
     for s in sims:

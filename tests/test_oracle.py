@@ -77,7 +77,8 @@ def test_angular_integral_closed_form():
             assert abs(O.angular_integral(a, b) - ref) < 1e-12
 
 
-@pytest.mark.parametrize("N,K", [(2, 5), (2, 16), (3, 7), (3, 12), (3, 64), (2, 48)])
+@pytest.mark.parametrize("N,K", [(2, 5), (2, 16), (3, 7), (3, 12), (3, 64), (2, 48), (5, 12), (4, 9),
+                                 (3, 600)])
 def test_product_rule_exactness(N, K):
     """Eq. (quad-integrals): the product rule with rotated shells integrates
     exp(-p) p^k cos^a sin^b (a+b <= k) exactly for k <= 2N; angular part
@@ -182,7 +183,7 @@ STATES = [(0.7, 0.8, 0.3, -0.2), (1.0, 1.0, 0.0, 0.0), (0.25, 0.6, 0.0, 0.0),
           (1.4, 1.6, -0.45, 0.1), (0.1, 0.5, 0.05, 0.02)]
 
 
-@pytest.mark.parametrize("N,K", [(2, 16), (2, 48), (3, 12), (3, 64), (4, 9)])
+@pytest.mark.parametrize("N,K", [(2, 16), (2, 48), (3, 12), (3, 64), (4, 9), (5, 12), (3, 600)])
 def test_feq_reproduces_conserved_moments(N, K):
     """Eqs. (mj-feq-expansion-truncated), (discrete_sum_moments): for N >= 2 the
     discrete equilibrium carries exactly N^a = n U^a and the ideal-gas T^ab."""
@@ -215,6 +216,8 @@ def test_feq_third_moments_need_N3():
     np.testing.assert_allclose(rank3(q3.feq(n, T, U[1], U[2]), q3), ref, atol=1e-12)
     q2 = O.Quadrature(2, 16)
     assert np.abs(rank3(q2.feq(n, T, U[1], U[2]), q2) - ref).max() > 1e-4
+    q5 = O.Quadrature(5, 12)
+    np.testing.assert_allclose(rank3(q5.feq(n, T, U[1], U[2]), q5), ref, atol=1e-12)
 
 
 def test_feq_is_degree_N_polynomial_on_nodes():
@@ -245,12 +248,15 @@ def test_feq_is_degree_N_polynomial_on_nodes():
         assert abs(ip) < 1e-9, ip
 
 
-@pytest.mark.parametrize("N,K", [(2, 16), (3, 64)])
+@pytest.mark.parametrize("N,K", [(2, 16), (3, 64), (5, 12)])
 def test_feq_rest_state_closed_form(N, K):
-    """At U = 0 and T = T0 = 1, f^MJ/omega = n/(2 pi) is constant, so f^eq_i = n w_i / (2 pi)."""
+    """At U = 0 and T = T0 = 1, f^MJ/omega = n/(2 pi) is constant, so f^eq_i = n w_i / (2 pi).
+    The radial projection solves a factorial Gram system whose conditioning grows
+    with N: relative rounding 1e-13 up to N = 3, 1e-11 at N = 5."""
     q = O.Quadrature(N, K)
+    rtol = 1e-13 * 10.0 ** max(0, N - 3)
     for n in (1.0, 0.37):
-        np.testing.assert_allclose(q.feq(n, 1.0, 0.0, 0.0), n * q.w / (2 * math.pi), rtol=1e-13,
+        np.testing.assert_allclose(q.feq(n, 1.0, 0.0, 0.0), n * q.w / (2 * math.pi), rtol=rtol,
                                    atol=1e-17)
 
 
@@ -297,7 +303,7 @@ def test_landau_flags_unphysical_state():
 
 # --------------------------------------------------------------- stream / collide
 
-@pytest.mark.parametrize("N,K", [(2, 16), (3, 12)])
+@pytest.mark.parametrize("N,K", [(2, 16), (3, 12), (5, 12)])
 def test_collision_conserves_N0_and_T0nu(N, K):
     """Anderson-Witting with Landau-frame (n, eps, U): sum p^0 df = 0 and
     sum p^0 p^nu df = 0; the spatial particle current is not conserved."""
@@ -309,7 +315,8 @@ def test_collision_conserves_N0_and_T0nu(N, K):
     fr = f.reshape(q.npop, -1)
     for wgt in [q.p0, q.p0 * q.p0, q.p0 * q.p0 * q.vx, q.p0 * q.p0 * q.vy]:
         scale = (np.abs(wgt)[:, None] * fr).sum(0)
-        assert (np.abs((wgt[:, None] * d).sum(0)) / scale).max() < 5e-14
+        # rounding of the radial projection grows with N (factorial Gram system)
+        assert (np.abs((wgt[:, None] * d).sum(0)) / scale).max() < 5e-14 * 10.0 ** max(0, N - 3)
     assert np.abs(((q.p0 * q.vx)[:, None] * d).sum(0)).max() > 1e-6
 
 
@@ -490,3 +497,30 @@ def test_lattice_ballistic_sod_approaches_appendix_a():
     betas = np.array(betas)
     err = np.linalg.norm(beta - betas) / np.linalg.norm(betas)
     assert err < 0.01, err
+
+
+def sod_beta_error(N, K, nx=2000, steps=900):
+    """Relative L2 error (Eq. rel_err) of the free-streaming lattice velocity
+    profile of the paper's 1D Sod tube (Eq. initial-cond-macro: (P, n, T) =
+    (2.25, 1.5, 1.5) | (0.05, 0.1, 0.5)) at t = 0.9 t_max, t_max = nx/2 (the
+    front moves at c = 1 from the middle to the edge), against Appendix A."""
+    fl = W.shock_tube(nx, 1, (1.5, 1.5), (0.1, 0.5))
+    q = O.Quadrature(N, K)
+    f, _ = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), math.inf, steps)
+    mac, _ = q.macro(f)
+    beta = mac[4, 0] / mac[3, 0]
+    x = np.arange(nx) + 0.5 - nx / 2
+    cont = A.continuum_moments(x / steps, 1.5, 2.25, 0.1, 0.05)
+    bref = np.array([(lambda m: m[4] / m[3])(O.landau(cont[:, s])[1]) for s in range(nx)])
+    return np.linalg.norm(beta - bref) / np.linalg.norm(bref)
+
+
+def test_fig2_more_angles_not_higher_order():
+    """Sec. 3.1, Fig. 2 (2000x1, tau -> inf, t/t_max = 0.9): at K = 12 the fifth
+    order rule is no better than the third order one, while N = 3 with K = 120
+    follows the analytic solution closely."""
+    e3, e5, e120 = sod_beta_error(3, 12), sod_beta_error(5, 12), sod_beta_error(3, 120)
+    assert 0.8 < e5 / e3 < 1.2, (e3, e5)
+    assert e120 < e3 / 10, (e3, e120)
+    assert e120 < 5e-3
+
