@@ -41,6 +41,11 @@ FALLBACK_HBM_GBS = 6800.0
 METRIC = "population-updates/s"
 
 
+def kn_json(kn_list):
+    """Kn values for the JSON line (tau -> inf, free streaming, as the string "inf")."""
+    return [k if math.isfinite(k) else "inf" for k in kn_list]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,7 +236,7 @@ def run_reference(args, w: W.Workload, precision: str):
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
-                       "npop": w.npop, "kn": kn_list, "time_steps_per_problem": steps_per,
+                       "npop": w.npop, "kn": kn_json(kn_list), "time_steps_per_problem": steps_per,
                        "precision": "fp64", "device": "host cores (oracle)"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -433,7 +438,8 @@ def main():
                 sim.set_tiling(args.tile_p or sim.tile_populations, args.kernel)
             else:
                 sim.autotune(8)
-    tiling = {"populations_per_warp": sims[0].tile_populations, "kernel": sims[0].step_kernel}
+    tiling = {"populations_per_warp": sims[0].tile_populations, "kernel": sims[0].step_kernel,
+              "population_groups_per_warp": sims[0].population_groups}
     kernel_names = {"per-tile": "rlbm_kernel<MODE_STEP>", "tma": "rlbm_step_tma",
                     "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
 
@@ -525,7 +531,7 @@ def main():
                       "bf16n": "bf16-storage/f32"}[precision],
             "data": "synthetic",
             "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
-                       "npop": w.npop, "kn": kn_list, "time_steps_per_problem": steps_pp,
+                       "npop": w.npop, "kn": kn_json(kn_list), "time_steps_per_problem": steps_pp,
                        "problems_per_step": len(kn_list), "precision": precision,
                        "bc": ["copy-out" if w.bcx else "periodic", "copy-out" if w.bcy else "periodic"],
                        "l2": f"flushed between timed steps (256 MB write); working set "

@@ -115,8 +115,14 @@ def tau_from_kn(kn: float, L: int) -> float:
 
 
 # --------------------------------------------------------------------------
-# The five synthetic workloads (grid, quadrature, Kn, steps, precision)
+# The synthetic workloads (grid, quadrature, Kn, steps, precision)
 # --------------------------------------------------------------------------
+
+# The paper's 1D Sod states (Sec. 3.1, Eq. initial-cond-macro), (n, T) of
+# (P, n, T) = (2.25, 1.5, 1.5) for x < 0 and (0.05, 0.1, 0.5) for x > 0.
+PAPER_SOD_LEFT = (1.5, 1.5)
+PAPER_SOD_RIGHT = (0.1, 0.5)
+_PAPER_SOD = {"left": PAPER_SOD_LEFT, "right": PAPER_SOD_RIGHT}
 
 @dataclass
 class Workload:
@@ -153,6 +159,15 @@ WORKLOADS = {
                                      {"states": [(1.0, 1.0, 0.0, 0.0), (0.5, 0.8, 0.0, 0.0),
                                                  (0.25, 0.6, 0.0, 0.0), (0.5, 0.8, 0.0, 0.0)],
                                       "jitter": 0.01}),
+    # the paper's Fig. 2 runs: 2000 x 1, tau -> inf, t = 0.9 t_max = 900 steps
+    "sod1d_2000x1_N3K120": Workload("sod1d_2000x1_N3K120", 2000, 1, 3, 120, (math.inf,), 900, "fp32",
+                                    extra=dict(_PAPER_SOD)),
+    "sod1d_2000x1_N5K12": Workload("sod1d_2000x1_N5K12", 2000, 1, 5, 12, (math.inf,), 900, "fp32",
+                                   extra=dict(_PAPER_SOD)),
+    # the paper's reference rule of Fig. 3: N = 3, K = 600 (2400 populations), 4000 x 1,
+    # t = 0.9 t_max = 1800 steps, three Kn of the figure's range
+    "sod1d_4000x1_N3K600": Workload("sod1d_4000x1_N3K600", 4000, 1, 3, 600, (0.05, 1.0, 10.0), 1800,
+                                    "fp32", extra=dict(_PAPER_SOD)),
 }
 
 SHOCK_LEFT = (1.0, 1.0)
@@ -165,7 +180,7 @@ def workload_fields(w: Workload, nx: int | None = None, ny: int | None = None,
     ny = ny or w.ny
     if "states" in w.extra:
         return riemann_2d(nx, ny, w.extra["states"], w.extra.get("jitter", 0.0), seed)
-    return shock_tube(nx, ny, SHOCK_LEFT, SHOCK_RIGHT)
+    return shock_tube(nx, ny, w.extra.get("left", SHOCK_LEFT), w.extra.get("right", SHOCK_RIGHT))
 
 
 @dataclass

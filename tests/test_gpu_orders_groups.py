@@ -205,3 +205,38 @@ def test_fig2_sod_free_streaming_2000x1(N, K):
     _, mac32 = gpu_run(N, K, fl, math.inf, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
     e32 = np.linalg.norm(mac32[4, 0] / mac32[3, 0] - bref) / np.linalg.norm(bref)
     assert abs(e32 - e_ref) < 1e-4, (e32, e_ref)
+
+
+# ------------------------------------------------------------ the paper's Fig. 3 K-sweep
+
+def test_ksweep_matches_oracle_at_L200():
+    """The sweep driver (library, FP64) gives the oracle's errors (Eq. rel_err)
+    for a 400x1, K = 600 reference (groups of populations) and K in {12, 120}."""
+    from paper_2011_06856_gb300 import ksweep
+    L, steps = 200, 90
+    rows = ksweep.sweep([0.02, 10.0], [12, 120], L=L, k_ref=600, precision="fp64")
+    for row, kn in zip(rows, (0.02, 10.0)):
+        q = O.Quadrature(3, 600)
+        fl = W.shock_tube(2 * L, 1, W.PAPER_SOD_LEFT, W.PAPER_SOD_RIGHT)
+        f, _ = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), W.tau_from_kn(kn, 2 * L), 2 * steps)
+        mac, _ = q.macro(f)
+        bf = mac[4, 0] / mac[3, 0]
+        bref = 0.5 * (bf[0::2] + bf[1::2])
+        for K, e in zip(row["K"], row["eps"]):
+            qk = O.Quadrature(3, K)
+            flk = W.shock_tube(L, 1, W.PAPER_SOD_LEFT, W.PAPER_SOD_RIGHT)
+            fk, _ = qk.run(qk.init(flk.n, flk.T, flk.bx, flk.by), W.tau_from_kn(kn, L), steps)
+            mk, _ = qk.macro(fk)
+            e_ref = np.linalg.norm(mk[4, 0] / mk[3, 0] - bref) / np.linalg.norm(bref)
+            assert abs(e - e_ref) < 1e-9 * max(1.0, e_ref), (kn, K, e, e_ref)
+
+
+def test_ksweep_full_size_kinetic_regime():
+    """Fig. 3 at the paper's size (2000x1 against 4000x1, K_ref = 600), Kn = 10:
+    the error falls with K (no parity: the paper prints no values)."""
+    from paper_2011_06856_gb300 import ksweep
+    row = ksweep.sweep([10.0], [12, 48, 120], L=2000, k_ref=600, precision="fp32")[0]
+    e12, e48, e120 = row["eps"]
+    assert e12 > e48 > e120, row["eps"]
+    assert e12 > 5 * e120, row["eps"]
+

@@ -524,3 +524,33 @@ def test_fig2_more_angles_not_higher_order():
     assert e120 < e3 / 10, (e3, e120)
     assert e120 < 5e-3
 
+
+def sod_beta(L, N, K, kn, steps):
+    fl = W.shock_tube(L, 1, W.PAPER_SOD_LEFT, W.PAPER_SOD_RIGHT)
+    q = O.Quadrature(N, K)
+    f, flagged = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), W.tau_from_kn(kn, L), steps)
+    assert flagged == 0
+    mac, _ = q.macro(f)
+    return mac[4, 0] / mac[3, 0]
+
+
+def test_fig3_ksweep_hydro_flat_kinetic_decaying():
+    """Sec. 3.1, Fig. 3 (scaled to L = 200 against a 400x1, K = 600 reference at
+    the same physical time, t = 0.9 t_max): in the hydrodynamic regime the error
+    (Eq. rel_err) does not depend on K; at large Kn it falls with K until the
+    spatial error takes over (saturation)."""
+    L = 200
+    steps = int(round(0.9 * L / 2))
+    eps = {}
+    for kn in (0.02, 10.0):
+        bf = sod_beta(2 * L, 3, 600, kn, 2 * steps)
+        bref = 0.5 * (bf[0::2] + bf[1::2])
+        for K in (12, 48, 120, 240):
+            b = sod_beta(L, 3, K, kn, steps)
+            eps[kn, K] = np.linalg.norm(b - bref) / np.linalg.norm(bref)
+    hydro = [eps[0.02, K] for K in (12, 48, 120, 240)]
+    assert max(hydro) / min(hydro) < 1.1, hydro
+    assert eps[10.0, 12] > 5 * eps[10.0, 120], eps
+    assert eps[10.0, 48] < eps[10.0, 12]
+    assert abs(eps[10.0, 240] - eps[10.0, 120]) < 0.1 * eps[10.0, 120], eps
+
