@@ -1,4 +1,5 @@
-"""K-sweep of the 1D Sod tube against a finely resolved reference (Sec. 3.1, Fig. 3).
+"""K-sweeps against a finely resolved reference: the 1D Sod tube (Sec. 3.1,
+Fig. 3) and the 2D Sod problem (Sec. 3.2, Fig. 6).
 
 For each Knudsen number Kn = c tau / L the tube of L x 1 cells is run with the
 N = 3 rule at several K, and compared with a reference on 2L x 1 cells with
@@ -13,6 +14,12 @@ library on the GPU; the initial states are the paper's (Eq. initial-cond-macro).
 
     python -m paper_2011_06856_gb300.ksweep [--L 2000] [--kn 0.05 0.2 1 10]
         [--K 12 24 48 96 120 240 480] [--kref 600] [--precision fp64]
+
+With --dim 2 the problem is the paper's four-quadrant one on L x L cells (copy-out
+walls), the reference on (4L) x (4L) cells (Fig. 6: 250^2 against 1000^2), the
+coarse run takes round(0.9 L/2) steps and the reference 4x as many, beta_ref is
+the mean over the 4 x 4 fine cells of a coarse cell, and the norm runs over both
+velocity components.
 
 Prints one JSON object per Kn.  A run that reaches a cell without a physical
 Landau frame (the library raises Unphysical; at Kn = 0.002 on 2000 x 1, tau = 4,
@@ -31,14 +38,22 @@ import numpy as np
 from . import workloads as W
 
 
-def run_profile(L: int, N: int, K: int, kn: float, steps: int, precision: str, stream=None):
-    """beta_x profile of the paper's Sod tube on L x 1 cells after `steps` steps,
-    and the population updates per second of the run."""
+def problem(L: int, dim: int):
+    """Initial fields and boundary conditions of the paper's 1D (L x 1) or 2D (L x L) problem."""
+    if dim == 1:
+        return W.shock_tube(L, 1, W.PAPER_SOD_LEFT, W.PAPER_SOD_RIGHT), W.BC_COPYOUT, W.BC_PERIODIC
+    return W.riemann_2d(L, L, W.PAPER_SOD2D_STATES), W.BC_COPYOUT, W.BC_COPYOUT
+
+
+def run_profile(L: int, N: int, K: int, kn: float, steps: int, precision: str, dim: int = 1,
+                stream=None):
+    """Velocity field (beta_x, beta_y) [2][ny][nx] of the paper's problem after
+    `steps` steps, and the population updates per second of the run."""
     from . import rlbm as R
     import torch
-    fl = W.shock_tube(L, 1, W.PAPER_SOD_LEFT, W.PAPER_SOD_RIGHT)
-    sim = R.Simulation(L, 1, N, K, W.tau_from_kn(kn, L), precision, W.BC_COPYOUT, W.BC_PERIODIC,
-                       stream=stream)
+    fl, bcx, bcy = problem(L, dim)
+    ny = fl.shape[0]
+    sim = R.Simulation(L, ny, N, K, W.tau_from_kn(kn, L), precision, bcx, bcy, stream=stream)
     try:
         sim.init_fields(fl)
         sim.autotune(2)
@@ -50,12 +65,15 @@ def run_profile(L: int, N: int, K: int, kn: float, steps: int, precision: str, s
         dt = time.perf_counter() - t0
     finally:
         sim.close()
-    return mac[4, 0] / mac[3, 0], L * (N + 1) * K * steps / dt
+    return mac[4:6] / mac[3], L * ny * (N + 1) * K * steps / dt
 
 
-def coarsen(beta_fine: np.ndarray) -> np.ndarray:
-    """Mean of fine cells 2i, 2i+1 (coarse cell i)."""
-    return 0.5 * (beta_fine[0::2] + beta_fine[1::2])
+def coarsen(beta_fine: np.ndarray, s: int, dim: int) -> np.ndarray:
+    """Mean over the s fine cells (1D) or s x s fine cells (2D) of each coarse cell."""
+    c, ny, nx = beta_fine.shape
+    if dim == 1:
+        return beta_fine.reshape(c, ny, nx // s, s).mean(-1)
+    return beta_fine.reshape(c, ny // s, s, nx // s, s).mean((2, 4))
 
 
 def rel_err(beta: np.ndarray, beta_ref: np.ndarray) -> float:
@@ -63,37 +81,44 @@ def rel_err(beta: np.ndarray, beta_ref: np.ndarray) -> float:
     return float(np.linalg.norm(beta - beta_ref) / np.linalg.norm(beta_ref))
 
 
-def sweep(kn_list, k_list, L: int = 2000, N: int = 3, k_ref: int = 600, precision: str = "fp64"):
+def sweep(kn_list, k_list, L: int = 2000, N: int = 3, k_ref: int = 600, precision: str = "fp64",
+          dim: int = 1):
     from .rlbm import Unphysical
+    s = 2 if dim == 1 else 4
     steps = int(round(0.9 * L / 2))
     out = []
     for kn in kn_list:
         try:
-            bref_f, rate_ref = run_profile(2 * L, N, k_ref, kn, 2 * steps, precision)
+            bref_f, rate_ref = run_profile(s * L, N, k_ref, kn, s * steps, precision, dim)
         except Unphysical:
             out.append({"kn": kn, "L": L, "N": N, "steps": steps, "reference": "unstable"})
             continue
-        bref = coarsen(bref_f)
+        bref = coarsen(bref_f, s, dim)
+        if dim == 1:
+            bref = bref[0]  # the tube's velocity is beta_x
         eps, rates = [], []
         for K in k_list:
             try:
-                b, rate = run_profile(L, N, K, kn, steps, precision)
+                b, rate = run_profile(L, N, K, kn, steps, precision, dim)
+                if dim == 1:
+                    b = b[0]
                 eps.append(rel_err(b, bref))
                 rates.append(rate)
             except Unphysical:
                 eps.append("unstable")
                 rates.append(None)
-        out.append({"kn": kn if math.isfinite(kn) else "inf", "L": L, "N": N, "steps": steps,
-                    "K": list(k_list), "npop": [(N + 1) * k for k in k_list], "eps": eps,
-                    "reference": {"L": 2 * L, "K": k_ref, "npop": (N + 1) * k_ref,
-                                  "steps": 2 * steps, "updates_per_s": rate_ref},
+        out.append({"kn": kn if math.isfinite(kn) else "inf", "dim": dim, "L": L, "N": N,
+                    "steps": steps, "K": list(k_list), "npop": [(N + 1) * k for k in k_list], "eps": eps,
+                    "reference": {"L": s * L, "K": k_ref, "npop": (N + 1) * k_ref,
+                                  "steps": s * steps, "updates_per_s": rate_ref},
                     "updates_per_s": rates, "precision": precision})
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--L", type=int, default=2000)
+    ap.add_argument("--dim", type=int, default=1, choices=[1, 2])
+    ap.add_argument("--L", type=int, default=None, help="coarse grid (default 2000 in 1D, 250 in 2D)")
     ap.add_argument("--kn", type=float, nargs="+", default=[0.05, 0.2, 1.0, 10.0])
     ap.add_argument("--K", type=int, nargs="+", default=[12, 24, 48, 96, 120, 240, 480])
     ap.add_argument("--kref", type=int, default=600)
@@ -101,7 +126,8 @@ def main():
     args = ap.parse_args()
     from . import build as B
     B.build()
-    for row in sweep(args.kn, args.K, args.L, 3, args.kref, args.precision):
+    L = args.L or (2000 if args.dim == 1 else 250)
+    for row in sweep(args.kn, args.K, L, 3, args.kref, args.precision, args.dim):
         print(json.dumps(row), flush=True)
 
 

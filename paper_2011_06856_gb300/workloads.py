@@ -123,6 +123,10 @@ def tau_from_kn(kn: float, L: int) -> float:
 PAPER_SOD_LEFT = (1.5, 1.5)
 PAPER_SOD_RIGHT = (0.1, 0.5)
 _PAPER_SOD = {"left": PAPER_SOD_LEFT, "right": PAPER_SOD_RIGHT}
+# The paper's 2D problem (Sec. 3.2, second Eq. initial-cond-macro), (n, T, beta_x, beta_y)
+# per quadrant in the order (x<0,y<0), (x>0,y<0), (x<0,y>0), (x>0,y>0).
+PAPER_SOD2D_STATES = [(0.5, 1.0, 0.0, 0.0), (0.5, 2.0, 0.0, 0.1), (0.5, 2.0, 0.1, 0.0),
+                      (1.0, 1.0, 0.0, 0.0)]
 
 @dataclass
 class Workload:
@@ -168,6 +172,13 @@ WORKLOADS = {
     # t = 0.9 t_max = 1800 steps, three Kn of the figure's range
     "sod1d_4000x1_N3K600": Workload("sod1d_4000x1_N3K600", 4000, 1, 3, 600, (0.05, 1.0, 10.0), 1800,
                                     "fp32", extra=dict(_PAPER_SOD)),
+    # the paper's Fig. 5 runs (2D Sod, copy-out walls, t = 0.9 t_max, t_max = L/2): 500^2 with
+    # K = 12 at the three Kn, and 1000^2 with K = 600 (N_pop = 2400, 19 GB of FP32
+    # populations) at the transition Kn
+    "sod2d_500sq_N3K12": Workload("sod2d_500sq_N3K12", 500, 500, 3, 12, (0.002, 0.1, 100.0), 225, "fp32",
+                                  BC_COPYOUT, BC_COPYOUT, {"states": PAPER_SOD2D_STATES}),
+    "sod2d_1000sq_N3K600": Workload("sod2d_1000sq_N3K600", 1000, 1000, 3, 600, (0.1,), 450, "fp32",
+                                    BC_COPYOUT, BC_COPYOUT, {"states": PAPER_SOD2D_STATES}),
 }
 
 SHOCK_LEFT = (1.0, 1.0)

@@ -240,3 +240,63 @@ def test_ksweep_full_size_kinetic_regime():
     assert e12 > e48 > e120, row["eps"]
     assert e12 > 5 * e120, row["eps"]
 
+
+# ------------------------------------------------------------ the paper's 2D problem (Sec. 3.2)
+
+def test_fp64_paper_2d_states_population_groups():
+    """The four boosted quadrants of Sec. 3.2 with the K = 600 rule (groups of
+    populations), 48x48, copy-out walls, Kn = 0.1: fields and populations."""
+    N, K, L, steps = 3, 600, 48, 5
+    fl = W.riemann_2d(L, L, W.PAPER_SOD2D_STATES)
+    tau = W.tau_from_kn(0.1, L)
+    f_ref, mac_ref = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    sim, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_COPYOUT)
+    assert sim.population_groups > 1
+    assert fields_err(mac, mac_ref) < FP64_TOL
+    assert relerr(sim.get_populations(), f_ref) < FP64_TOL
+
+
+def test_ksweep_2d_matches_oracle():
+    """The 2D sweep (coarse L x L against a 4L x 4L reference with K = 600, 4x4
+    block means, both velocity components) gives the oracle's errors; L = 16."""
+    from paper_2011_06856_gb300 import ksweep
+    L, kn = 16, 1.0
+    steps = int(round(0.9 * L / 2))
+    row = ksweep.sweep([kn], [12, 48], L=L, k_ref=600, precision="fp64", dim=2)[0]
+
+    def beta(Lg, K, st):
+        q = O.Quadrature(3, K)
+        fl = W.riemann_2d(Lg, Lg, W.PAPER_SOD2D_STATES)
+        f, flagged = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), W.tau_from_kn(kn, Lg), st,
+                           W.BC_COPYOUT, W.BC_COPYOUT)
+        assert flagged == 0
+        mac, _ = q.macro(f)
+        return mac[4:6] / mac[3]
+
+    bf = beta(4 * L, 600, 4 * steps)
+    bref = bf.reshape(2, L, 4, L, 4).mean((2, 4))
+    for K, e in zip(row["K"], row["eps"]):
+        b = beta(L, K, steps)
+        e_ref = np.linalg.norm(b - bref) / np.linalg.norm(bref)
+        assert abs(e - e_ref) < 1e-9 * max(1.0, e_ref), (K, e, e_ref)
+
+
+def test_fig5_2d_sod_k12_against_k600():
+    """Sec. 3.2, Fig. 5 (t/t_max = 0.9): the 500^2, K = 12 density agrees with the
+    1000^2, K = 600 one (2x2 block means) in the hydrodynamic regime and departs
+    from it in the almost ballistic one (no parity: the paper prints no values)."""
+    err = {}
+    for kn in (0.002, 100.0):
+        dens = {}
+        for L, K in ((500, 12), (1000, 600)):
+            fl = W.riemann_2d(L, L, W.PAPER_SOD2D_STATES)
+            sim = R.Simulation(L, L, 3, K, W.tau_from_kn(kn, L), "fp32", W.BC_COPYOUT, W.BC_COPYOUT)
+            sim.init_fields(fl)
+            sim.autotune(2)
+            sim.step(int(round(0.9 * L / 2)))
+            dens[L] = sim.moments()[0]
+            sim.close()
+        fine = dens[1000].reshape(500, 2, 500, 2).mean((1, 3))
+        err[kn] = np.linalg.norm(dens[500] - fine) / np.linalg.norm(fine)
+    assert err[100.0] > 3 * err[0.002], err
+
