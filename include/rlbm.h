@@ -184,8 +184,9 @@ int rlbm_tile_populations(const rlbm_t *h);
  * paper's K = 600 reference runs with N = 3).  Then floor(16 / (N+1)) warps
  * per shell own ceil(K / (warps P)) groups each; the streamed values of all
  * but the last group are parked in the output buffer between the two passes
- * (FP32 and FP64 storage; rlbm_create refuses such K in 16-bit storage), and
- * only the per-tile kernel applies.  -1 for a NULL handle. */
+ * (FP32 and FP64 storage; rlbm_create refuses such K in 16-bit storage).
+ * The per-tile kernel and, in FP32 storage with K a multiple of P, the
+ * two-sites-per-lane kernel (without staging) apply.  -1 for a NULL handle. */
 int rlbm_population_groups(const rlbm_t *h);
 
 /* Autotuner: time every compiled tiling of the step kernel (P populations per

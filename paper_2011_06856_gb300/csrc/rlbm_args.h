@@ -139,6 +139,9 @@ RLBM_DECLARE_PAIR(f32)
 RLBM_DECLARE_PAIR(f16)
 RLBM_DECLARE_PAIR(bf16)
 #undef RLBM_DECLARE_PAIR
+// The same kernel with several population groups per warp (FP32 storage, no staging).
+cudaError_t launch_pair_groups_f32(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,
+                                   cudaStream_t st, const KernelArgs &a);
 
 // Batched persistent form (rlbm_batch.cuh).
 constexpr int kBatchWarps = 6;

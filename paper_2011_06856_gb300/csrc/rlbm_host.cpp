@@ -506,13 +506,17 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
 }
 
 // The two-sites-per-lane step kernel applies to FP32 arithmetic with a
-// collision, an even row length, K a multiple of P and P in {8, 12, 16, 24, 32}.
+// collision, N <= 3, an even row length, K a multiple of P and P in
+// {8, 12, 16, 24, 32}; with several population groups per warp (many angles)
+// to FP32 storage only.
 bool pair_possible(const rlbm_t *h, int P)
 {
     if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3) return false;
     if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
     if (!(P == 8 || P == 12 || P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
-    return (h->K / P) * (h->N + 1) <= rlbmk::kMaxWarps;
+    int gs = 0, ng = 0;
+    if (!group_tiling(h->N, h->K, P, gs, ng)) return false;
+    return ng == 1 || h->prec == RLBM_FP32;
 }
 
 // The bulk-staged form copies row segments of whole 16-byte chunks from
@@ -529,6 +533,11 @@ cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
     const bool two_d = h->grid.ny > 1, bulk = h->pair_bulk;
     const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G, bulk, int(storage_size(h->prec)), two_d);
     cudaError_t e;
+    if (h->R > 1) { // several population groups per warp (FP32 storage: pair_possible)
+        e = rlbmk::launch_pair_groups_f32(h->N, h->P, two_d, grid, block, smem, h->stream, a);
+        if (e == cudaSuccess) ++h->launches;
+        return e;
+    }
     switch (h->prec) {
     case RLBM_FP32: e = rlbmk::launch_pair_f32(h->N, h->P, two_d, bulk, grid, block, smem, h->stream, a); break;
     case RLBM_FP16_DEV:
@@ -724,7 +733,7 @@ rlbm_status retile(rlbm_t *h, int P, int kind)
     h->G = h->Gs * (h->N + 1);
     h->no_tma = kind != 1;
     h->use_pair = (kind == 2 || kind == 3) && pair_possible(h, P);
-    h->pair_bulk = h->use_pair && kind == 3 && pair_bulk_possible(h);
+    h->pair_bulk = h->use_pair && kind == 3 && pair_bulk_possible(h) && h->R == 1;
     rlbm_status st = build_tables(h);
     if (st) return st;
     return setup_tma(h);
@@ -1051,15 +1060,16 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
     int gs = 0, ng = 0;
     if (!ok || !group_tiling(h->N, h->K, P, gs, ng))
         return fail(h, RLBM_ERR_UNSUPPORTED, "no compiled tiling with P=%d for N=%d, K=%d", P, h->N, h->K);
-    if (ng > 1 && kind != 0)
-        return fail(h, RLBM_ERR_UNSUPPORTED, "K=%d needs several population groups per warp: per-tile kernel only",
+    if (ng > 1 && kind != 0 && kind != 2)
+        return fail(h, RLBM_ERR_UNSUPPORTED,
+                    "K=%d needs several population groups per warp: per-tile or two-sites-per-lane kernel only",
                     h->K);
     if ((kind == 2 || kind == 3) && !pair_possible(h, P)) {
         rlbm_status st0 = retile(h, P, 0);
         if (st0) return st0;
         return fail(h, RLBM_ERR_UNSUPPORTED,
-                    "two-sites-per-lane kernel needs FP32 arithmetic, tau finite, nx even, P in "
-                    "{8,12,16,24,32} dividing K and at most 16 warps");
+                    "two-sites-per-lane kernel needs FP32 arithmetic, tau finite, N <= 3, nx even, P in "
+                    "{8,12,16,24,32} dividing K, and FP32 storage when K needs several population groups");
     }
     rlbm_status st = retile(h, P, kind);
     if (st) return st;

@@ -6,4 +6,9 @@ cudaError_t launch_pair_f32(int N, int PP, bool two_d, bool bulk, dim3 grid, dim
 {
     return launch_pair_t<float>(N, PP, two_d, bulk, grid, block, smem, st, a);
 }
+cudaError_t launch_pair_groups_f32(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,
+                                   cudaStream_t st, const KernelArgs &a)
+{
+    return launch_pair_groups(N, PP, two_d, grid, block, smem, st, a);
+}
 } // namespace rlbmk

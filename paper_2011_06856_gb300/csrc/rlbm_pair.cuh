@@ -497,6 +497,216 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
     }
 }
 
+// Many angles (K beyond one group of PP populations per warp), FP32 storage:
+// the arithmetic of rlbm_pair_kernel with plain loads, warp (r, q) owning
+// groups rho = 0, 1, ... of PP populations, group rho being virtual warp
+// v = rho Gs + q (populations r K + v PP + k; K is a multiple of PP, so a group
+// is full or empty).  Pass 1 streams the groups one after another and parks
+// the packed f* of all but the warp's last non-empty group in their own output
+// slots; pass 2 handles the last group from registers and reads the others
+// back (the same thread wrote them: no synchronisation).
+template <int N, int PP, bool TWO_D>
+__global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_groups_kernel(const KernelArgs a)
+{
+    constexpr int NC = 2 * N + 1;
+    constexpr int PQ = 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x, g = threadIdx.y, G = blockDim.y;
+    const int x0 = blockIdx.x * kPairSites;
+    const int xl = x0 + 2 * lane;
+    const bool act = xl < a.nx;
+    const int xa = act ? xl : a.nx - 2;
+    const int y = blockIdx.y;
+    const int r = g / a.Gs, q = g % a.Gs;
+    const long long S = a.S;
+    const float *fin = reinterpret_cast<const float *>(a.fin);
+    float *fout = reinterpret_cast<float *>(a.fout);
+    float *red = reinterpret_cast<float *>(smem_raw); // [5][G][64]
+    float *sres = red + 5 * G * kPairSites;           // [(N+1)^2 + 3][64]
+    const float4 *ptab = reinterpret_cast<const float4 *>(a.pairtab);
+    const int xm = bc_index(xa - 1, a.nx, a.bcx), xp = bc_index(xa + 2, a.nx, a.bcx);
+    const int ym = TWO_D ? bc_index(y - 1, a.ny, a.bcy) : y;
+    const int yp = TWO_D ? bc_index(y + 1, a.ny, a.bcy) : y;
+    const long long row = (long long)y * a.nx;
+    const long long dym = (long long)(ym - y) * a.nx, dyp = (long long)(yp - y) * a.nx;
+    const int Gv = a.Gs * a.R;                                      // virtual warps per shell
+    const int nrho = min(a.R, (a.K / PP - q + a.Gs - 1) / a.Gs); // non-empty groups of this warp
+
+    float2 fs[PP];
+    float2 s0 = f2(0.f, 0.f), sc = f2(0.f, 0.f), ss = f2(0.f, 0.f), scc = f2(0.f, 0.f), scs = f2(0.f, 0.f);
+    constexpr int CH = TWO_D ? (PP <= 8 ? PP : (PP == 12 ? 6 : 4)) : (PP <= 16 ? PP : 8);
+    static_assert(PP % CH == 0, "chunking");
+#pragma unroll 1
+    for (int rho = 0; rho < nrho; ++rho) {
+        const int vw = rho * a.Gs + q;
+        const int i0 = r * a.K + vw * PP;
+        const float4 *tb = ptab + size_t(i0) * PQ;
+        const unsigned long long mx = __ldg(a.masks + 2 * (r * Gv + vw));
+        const unsigned long long my = __ldg(a.masks + 2 * (r * Gv + vw) + 1);
+        const float *base = fin + (long long)i0 * S + row;
+#pragma unroll
+        for (int c0 = 0; c0 < PP; c0 += CH) {
+            float2 ca[CH], cb[TWO_D ? CH : 1];
+            float ea[CH], eb[TWO_D ? CH : 1];
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                const int k = c0 + kk;
+                const float *pk = base + (long long)k * S;
+                const int xs = ((mx >> k) & 1ull) ? xm : xp;
+                ca[kk] = PIo<float>::ld2(pk + xa);
+                ea[kk] = PIo<float>::ld1(pk + xs);
+                if (TWO_D) {
+                    const long long dy = ((my >> k) & 1ull) ? dym : dyp;
+                    cb[kk] = PIo<float>::ld2(pk + dy + xa);
+                    eb[kk] = PIo<float>::ld1(pk + dy + xs);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                const int k = c0 + kk;
+                const float4 t0 = __ldg(tb + k * PQ), t1 = __ldg(tb + k * PQ + 1); // (c,c,s,s), (|c|,|c|,|s|,|s|)
+                const bool px = (mx >> k) & 1ull;                                    // v_x >= 0: pull from x - 1
+                const float2 C = ca[kk];
+                const float2 B = px ? f2(ea[kk], C.x) : f2(C.y, ea[kk]);
+                const float2 ac = f2(t1.x, t1.y);
+                float2 v = __ffma2_rn(ac, f2sub(B, C), C);
+                if (TWO_D) {
+                    const float2 C2 = cb[kk];
+                    const float2 B2 = px ? f2(eb[kk], C2.x) : f2(C2.y, eb[kk]);
+                    const float2 hi = __ffma2_rn(ac, f2sub(B2, C2), C2);
+                    v = __ffma2_rn(f2(t1.z, t1.w), f2sub(hi, v), v);
+                }
+                fs[k] = v;
+                const float2 c = f2(t0.x, t0.y), sn = f2(t0.z, t0.w);
+                const float2 cv = __fmul2_rn(c, v);
+                s0 = __fadd2_rn(s0, v);
+                sc = __fadd2_rn(sc, cv);
+                ss = __ffma2_rn(sn, v, ss);
+                scc = __ffma2_rn(c, cv, scc);
+                scs = __ffma2_rn(sn, cv, scs);
+            }
+        }
+        if (rho + 1 < nrho && act) { // park f* of every group but the last
+            float *pb = fout + (long long)i0 * S + row + xa;
+#pragma unroll
+            for (int k = 0; k < PP; ++k) *reinterpret_cast<float2 *>(pb + (long long)k * S) = fs[k];
+        }
+    }
+    float2 *red2 = reinterpret_cast<float2 *>(red);
+    red2[(0 * G + g) * 32 + lane] = s0;
+    red2[(1 * G + g) * 32 + lane] = sc;
+    red2[(2 * G + g) * 32 + lane] = ss;
+    red2[(3 * G + g) * 32 + lane] = scc;
+    red2[(4 * G + g) * 32 + lane] = scs;
+    __syncthreads();
+    if (g < 2) {
+        const int s = g * 32 + lane;
+        pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
+    }
+    __syncthreads();
+
+    // this warp's shell coefficients for its two sites (as in rlbm_pair_kernel)
+    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
+    const float2 *sres2 = reinterpret_cast<const float2 *>(sres);
+    const float *rt = reinterpret_cast<const float *>(a.rtab) + r * (N + 1) * (N + 1);
+    float2 cf[NC];
+    {
+        int rw = 0;
+#pragma unroll
+        for (int mm = 0; mm <= N; ++mm) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float w = __ldg(rt + mm * (N + 1) + k);
+                acc = __ffma2_rn(f2(w, w), sres2[(rw++) * 32 + lane], acc);
+            }
+            if (mm == 0) cf[0] = __fadd2_rn(acc, f2(-a.feq_off_f, -a.feq_off_f));
+            else cf[2 * mm - 1] = acc;
+        }
+#pragma unroll
+        for (int mm = 1; mm <= N; ++mm) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float w = __ldg(rt + mm * (N + 1) + k);
+                acc = __ffma2_rn(f2(w, w), sres2[(rw++) * 32 + lane], acc);
+            }
+            cf[2 * mm] = acc;
+        }
+    }
+    float2 cr[NC];
+    cr[0] = f2sub(cf[0], cf[3]);
+    cr[1] = cf[1];
+    cr[2] = cf[2];
+    cr[3] = __fmul2_rn(f2(2.f, 2.f), cf[3]);
+    cr[4] = __fmul2_rn(f2(2.f, 2.f), cf[4]);
+    if (N == 3) {
+        cr[1] = __ffma2_rn(f2(-3.f, -3.f), cf[NC - 2], cr[1]);
+        cr[2] = f2sub(cr[2], cf[NC - 1]);
+        cr[NC - 2] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 2]);
+        cr[NC - 1] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 1]);
+    }
+    const float2 o0 = sres2[((N + 1) * (N + 1) + 0) * 32 + lane];
+    const float2 o1 = sres2[((N + 1) * (N + 1) + 1) * 32 + lane];
+    const float2 o2 = sres2[((N + 1) * (N + 1) + 2) * 32 + lane];
+    const float2 no1 = f2(-o1.x, -o1.y), no2 = f2(-o2.x, -o2.y);
+#pragma unroll 1
+    for (int rho = nrho - 1; rho >= 0; --rho) {
+        const int vw = rho * a.Gs + q;
+        const int i0 = r * a.K + vw * PP;
+        const float4 *tb = ptab + size_t(i0) * PQ;
+        float *ob = fout + (long long)i0 * S + row + xa;
+        if (rho + 1 < nrho && act) { // a parked group: f* back from its output slots
+#pragma unroll
+            for (int k = 0; k < PP; ++k) fs[k] = *reinterpret_cast<const float2 *>(ob + (long long)k * S);
+        }
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float4 t0 = __ldg(tb + k * PQ);                                       // (c,c,s,s)
+            const float2 wq = __ldg(reinterpret_cast<const float2 *>(tb + k * PQ + 2)); // (w', w')
+            const float2 c = f2(t0.x, t0.y), sn = f2(t0.z, t0.w);
+            const float2 cc = __fmul2_rn(c, c), cs = __fmul2_rn(c, sn);
+            float2 pe = __ffma2_rn(cr[1], c, cr[0]);
+            pe = __ffma2_rn(cr[2], sn, pe);
+            pe = __ffma2_rn(cr[3], cc, pe);
+            pe = __ffma2_rn(cr[4], cs, pe);
+            if (N == 3) {
+                pe = __ffma2_rn(cr[NC - 2], __fmul2_rn(c, cc), pe);
+                pe = __ffma2_rn(cr[NC - 1], __fmul2_rn(sn, cc), pe);
+            }
+            const float2 feq = __fmul2_rn(wq, pe);
+            const float2 om = __ffma2_rn(no2, sn, __ffma2_rn(no1, c, o0));
+            const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
+            if (act) *reinterpret_cast<float2 *>(ob + (long long)k * S) = out;
+        }
+    }
+}
+
+// Several population groups per warp (FP32 storage, plain loads).
+template <int N, int PP>
+static cudaError_t launch_pair_groups_np(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                         const KernelArgs &a)
+{
+    void (*k)(const KernelArgs) = two_d ? rlbm_pair_groups_kernel<N, PP, true> : rlbm_pair_groups_kernel<N, PP, false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static inline cudaError_t launch_pair_groups(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,
+                                             cudaStream_t st, const KernelArgs &a)
+{
+#define RLBM_PAIR_CASE(n, p)                                                                                 \
+    if (N == n && PP == p) return launch_pair_groups_np<n, p>(two_d, grid, block, smem, st, a);
+    RLBM_PAIR_CASE(2, 8) RLBM_PAIR_CASE(2, 12) RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
+    RLBM_PAIR_CASE(3, 8) RLBM_PAIR_CASE(3, 12) RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
+#undef RLBM_PAIR_CASE
+    return cudaErrorInvalidValue;
+}
+
 template <class St, int N, int PP>
 static cudaError_t launch_pair_np(bool two_d, bool bulk, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                   const KernelArgs &a)

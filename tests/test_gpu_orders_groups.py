@@ -51,11 +51,11 @@ def oracle_run(N, K, fl, tau, steps, bcx, bcy):
     return f, mac
 
 
-def gpu_run(N, K, fl, tau, steps, bcx, bcy, precision="fp64", P=None):
+def gpu_run(N, K, fl, tau, steps, bcx, bcy, precision="fp64", P=None, kind="per-tile"):
     ny, nx = fl.shape
     sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
     if P is not None:
-        sim.set_tiling(P, "per-tile")
+        sim.set_tiling(P, kind)
     sim.init_fields(fl)
     sim.step(steps)
     return sim, sim.moments()
@@ -177,9 +177,30 @@ def test_population_groups_refusals_and_autotune():
     fl = W.shock_tube(64, 2, (1.5, 1.5), (0.1, 0.5))
     sim.init_fields(fl)
     sim.autotune(2)
-    assert sim.step_kernel == "per-tile" and sim.population_groups > 1
+    assert sim.step_kernel in ("per-tile", "pair") and sim.population_groups > 1
     sim.step(4)
     sim.moments()
+    with pytest.raises(R.RLBMError) as e:
+        sim.set_tiling(24, "pair-bulk")
+    assert e.value.status == R.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("N,K,nx,ny,P", [(3, 600, 130, 3, 24), (3, 600, 64, 1, 8), (2, 480, 66, 4, 12),
+                                         (3, 384, 128, 2, 32)])
+def test_fp32_pair_kernel_population_groups(N, K, nx, ny, P):
+    """Two sites per lane with several population groups per warp (FP32): the
+    oracle's fields within the FP32 bound; ragged tiles, warps with one group
+    fewer (K = 600, P = 8 and 24), 1D and 2D."""
+    steps, tau = 10, 3.0
+    fl = W.random_fields(nx, ny, seed=K + P)
+    _, mac_ref = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+    sim, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32", P=P, kind="pair")
+    assert sim.step_kernel == "pair" and sim.population_groups > 1
+    tol = max(1e-5, FP32_BIAS * 1.2 / tau * steps)
+    for i in range(4):
+        assert relerr(mac[i], mac_ref[i]) < tol, i
+    us = np.abs(mac_ref[4:6]).max()
+    assert np.abs(mac[4:6] - mac_ref[4:6]).max() / us < tol
 
 
 # ------------------------------------------------------------ the paper's Fig. 2 runs
