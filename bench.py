@@ -443,6 +443,12 @@ def main():
     kernel_names = {"per-tile": "rlbm_kernel<MODE_STEP>", "tma": "rlbm_step_tma",
                     "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
 
+    def kernel_name(sim):
+        if sim.population_groups > 1:
+            return {"pair": "rlbm_pair_groups_kernel",
+                    "per-tile": "rlbm_kernel<MODE_STEP> (population groups)"}[sim.step_kernel]
+        return kernel_names[sim.step_kernel]
+
     def one_step():
         fork = torch.cuda.Event()
         fork.record(stream)
@@ -544,7 +550,7 @@ def main():
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": profiled_traffic(w.name, precision, sims[0].step_kernel,
                                                      sims[0].tile_populations),
-                         "kernel": kernel_names[sims[0].step_kernel],
+                         "kernel": kernel_name(sims[0]),
                          "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes},
             "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": METRIC,

@@ -33,11 +33,12 @@ def main(argv=None):
     ap.add_argument("--kn", type=float, default=0.05)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--riemann", action="store_true")
+    ap.add_argument("--paper2d", action="store_true", help="the paper's 2D four-quadrant states (Sec. 3.2)")
     ap.add_argument("--bcx", type=int, default=W.BC_COPYOUT)
     ap.add_argument("--bcy", type=int, default=None)
     ap.add_argument("--tile-p", type=int, default=None, help="populations per warp")
     ap.add_argument("--per-tile", action="store_true", help="do not use the TMA-staged kernel")
-    ap.add_argument("--kernel", choices=("per-tile", "tma", "pair", "pair-bulk"), default=None,
+    ap.add_argument("--kernel", choices=R.Simulation.KERNELS, default=None,
                     help="step kernel (with --tile-p as its populations per warp)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--out", default=None)
@@ -47,8 +48,10 @@ def main(argv=None):
         os.environ["RLBM_TILE_P"] = str(a.tile_p)
     if a.per_tile:
         os.environ["RLBM_NO_TMA"] = "1"
-    bcy = a.bcy if a.bcy is not None else (W.BC_COPYOUT if a.riemann else W.BC_PERIODIC)
-    if a.riemann:
+    bcy = a.bcy if a.bcy is not None else (W.BC_COPYOUT if (a.riemann or a.paper2d) else W.BC_PERIODIC)
+    if a.paper2d:
+        fl = W.riemann_2d(a.nx, a.ny, W.PAPER_SOD2D_STATES)
+    elif a.riemann:
         fl = W.workload_fields(W.WORKLOADS["riemann2d_2048_N2K48"], a.nx, a.ny)
     else:
         fl = W.shock_tube(a.nx, a.ny)
@@ -68,7 +71,7 @@ def main(argv=None):
     else:
         sim.step(a.steps)
     sim.sync()
-    print(f"tiling P={sim.tile_populations} kernel={sim.step_kernel} "
+    print(f"tiling P={sim.tile_populations} groups={sim.population_groups} kernel={sim.step_kernel} "
           f"steps={sim.steps_done} launches={sim.kernel_launches}")
     if a.out:
         m = sim.moments()
