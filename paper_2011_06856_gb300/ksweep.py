@@ -1,5 +1,6 @@
 """K-sweeps against a finely resolved reference: the 1D Sod tube (Sec. 3.1,
-Fig. 3) and the 2D Sod problem (Sec. 3.2, Fig. 6).
+Fig. 3) and the 2D Sod problem (Sec. 3.2, Fig. 6); and the grid-convergence
+study of the tube (Sec. 3.1, Fig. 4, --convergence).
 
 For each Knudsen number Kn = c tau / L the tube of L x 1 cells is run with the
 N = 3 rule at several K, and compared with a reference on 2L x 1 cells with
@@ -20,6 +21,11 @@ walls), the reference on (4L) x (4L) cells (Fig. 6: 250^2 against 1000^2), the
 coarse run takes round(0.9 L/2) steps and the reference 4x as many, beta_ref is
 the mean over the 4 x 4 fine cells of a coarse cell, and the norm runs over both
 velocity components.
+
+With --convergence the tube runs on several grids L (each dividing the
+reference grid L_ref = 12000, with 0.9 L/2 a whole number of steps) for several
+K, against one L_ref x 1, K = 600 reference per Kn at the same physical time
+(Fig. 4: N_pop = 48, 240, 480 against N_pop = 2400).
 
 Prints one JSON object per Kn.  A run that reaches a cell without a physical
 Landau frame (the library raises Unphysical; at Kn = 0.002 on 2000 x 1, tau = 4,
@@ -115,6 +121,39 @@ def sweep(kn_list, k_list, L: int = 2000, N: int = 3, k_ref: int = 600, precisio
     return out
 
 
+def convergence(kn_list, L_list, k_list, L_ref: int = 12000, N: int = 3, k_ref: int = 600,
+                precision: str = "fp64"):
+    """Fig. 4: eps(L, K) for each Kn against one L_ref x 1 reference."""
+    from .rlbm import Unphysical
+    for L in L_list:
+        if L_ref % L or (9 * L) % 20:
+            raise ValueError(f"L = {L} must divide {L_ref} and make 0.9 L/2 a whole number of steps")
+    ref_steps = 9 * L_ref // 20
+    out = []
+    for kn in kn_list:
+        try:
+            bref_f, rate_ref = run_profile(L_ref, N, k_ref, kn, ref_steps, precision)
+        except Unphysical:
+            out.append({"kn": kn, "L_ref": L_ref, "reference": "unstable"})
+            continue
+        eps = {}
+        for K in k_list:
+            row = []
+            for L in L_list:
+                bref = coarsen(bref_f, L_ref // L, 1)[0]
+                try:
+                    b, _ = run_profile(L, N, K, kn, 9 * L // 20, precision)
+                    row.append(rel_err(b[0], bref))
+                except Unphysical:
+                    row.append("unstable")
+            eps[str(K)] = row
+        out.append({"kn": kn, "N": N, "L": list(L_list), "K": list(k_list),
+                    "npop": [(N + 1) * k for k in k_list], "eps_by_K": eps,
+                    "reference": {"L": L_ref, "K": k_ref, "npop": (N + 1) * k_ref, "steps": ref_steps,
+                                  "updates_per_s": rate_ref}, "precision": precision})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dim", type=int, default=1, choices=[1, 2])
@@ -123,9 +162,17 @@ def main():
     ap.add_argument("--K", type=int, nargs="+", default=[12, 24, 48, 96, 120, 240, 480])
     ap.add_argument("--kref", type=int, default=600)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--convergence", action="store_true", help="Fig. 4 instead of a K-sweep")
+    ap.add_argument("--grids", type=int, nargs="+", default=[500, 1000, 1500, 2000, 3000, 4000, 6000])
+    ap.add_argument("--lref", type=int, default=12000)
     args = ap.parse_args()
     from . import build as B
     B.build()
+    if args.convergence:
+        K = args.K if args.K != ap.get_default("K") else [12, 60, 120]
+        for row in convergence(args.kn, args.grids, K, args.lref, 3, args.kref, args.precision):
+            print(json.dumps(row), flush=True)
+        return
     L = args.L or (2000 if args.dim == 1 else 250)
     for row in sweep(args.kn, args.K, L, 3, args.kref, args.precision, args.dim):
         print(json.dumps(row), flush=True)

@@ -321,3 +321,25 @@ def test_fig5_2d_sod_k12_against_k600():
         err[kn] = np.linalg.norm(dens[500] - fine) / np.linalg.norm(fine)
     assert err[100.0] > 3 * err[0.002], err
 
+
+def test_convergence_driver_matches_oracle():
+    """Fig. 4 driver (grids 40, 80 against a 240x1, K = 600 reference, Kn = 10)
+    gives the oracle's errors."""
+    from paper_2011_06856_gb300 import ksweep
+    Lr, grids, kn = 240, [40, 80], 10.0
+    row = ksweep.convergence([kn], grids, [12, 60], L_ref=Lr, precision="fp64")[0]
+
+    def beta(L, K):
+        q = O.Quadrature(3, K)
+        fl = W.shock_tube(L, 1, W.PAPER_SOD_LEFT, W.PAPER_SOD_RIGHT)
+        f, _ = q.run(q.init(fl.n, fl.T, fl.bx, fl.by), W.tau_from_kn(kn, L), 9 * L // 20)
+        mac, _ = q.macro(f)
+        return mac[4, 0] / mac[3, 0]
+
+    bf = beta(Lr, 600)
+    for K in (12, 60):
+        for L, e in zip(grids, row["eps_by_K"][str(K)]):
+            bref = bf.reshape(L, Lr // L).mean(1)
+            e_ref = np.linalg.norm(beta(L, K) - bref) / np.linalg.norm(bref)
+            assert abs(e - e_ref) < 1e-9 * max(1.0, e_ref), (K, L, e, e_ref)
+

@@ -554,3 +554,26 @@ def test_fig3_ksweep_hydro_flat_kinetic_decaying():
     assert eps[10.0, 48] < eps[10.0, 12]
     assert abs(eps[10.0, 240] - eps[10.0, 120]) < 0.1 * eps[10.0, 120], eps
 
+
+def test_fig4_grid_convergence_plateau_for_few_angles():
+    """Sec. 3.1, Fig. 4 (scaled: grids L = 40 ... 240 against a 480x1, K = 600
+    reference at t = 0.9 t_max): at small Kn the error falls with the grid for
+    every K and hardly depends on it; at large Kn the few-angle rule (K = 12)
+    stops converging while K = 60 and 120 keep converging."""
+    Lr, grids = 480, (40, 80, 240)
+    eps = {}
+    for kn in (0.05, 10.0):
+        bf = sod_beta(Lr, 3, 600, kn, 9 * Lr // 20)
+        for K in (12, 60, 120):
+            for L in grids:
+                bref = bf.reshape(L, Lr // L).mean(1)
+                b = sod_beta(L, 3, K, kn, 9 * L // 20)
+                eps[kn, K, L] = np.linalg.norm(b - bref) / np.linalg.norm(bref)
+    for K in (12, 60, 120):
+        assert eps[0.05, K, 240] < eps[0.05, K, 40] / 4, eps
+        assert abs(eps[0.05, K, 80] - eps[0.05, 120, 80]) < 0.2 * eps[0.05, 120, 80], eps
+    assert eps[10.0, 12, 240] > 0.8 * eps[10.0, 12, 40], eps
+    for K in (60, 120):
+        assert eps[10.0, K, 240] < eps[10.0, K, 40] / 3, eps
+    assert eps[10.0, 12, 240] > 5 * eps[10.0, 120, 240], eps
+
