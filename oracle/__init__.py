@@ -63,6 +63,10 @@ def lib():
         L.orc_angular_integral.argtypes = [ctypes.c_int, ctypes.c_int]
         L.orc_create.restype = ctypes.c_void_p
         L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_create_onlattice.restype = ctypes.c_void_p
+        L.orc_create_onlattice.argtypes = [ctypes.c_int]
+        L.orc_shifts.restype = ctypes.c_int
+        L.orc_shifts.argtypes = [ctypes.c_void_p, _ip, _ip]
         L.orc_destroy.restype = None
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_npop.restype = ctypes.c_int
@@ -148,13 +152,25 @@ def landau(mom):
 
 
 class Quadrature:
-    """Quadrature context of order N with K angles per shell (N_pop = K (N+1))."""
+    """Quadrature context of order N with K angles per shell (N_pop = K (N+1)).
 
-    def __init__(self, N: int, K: int):
-        self.N, self.K = int(N), int(K)
-        self._h = lib().orc_create(self.N, self.K)
-        if not self._h:
-            raise ValueError(f"invalid quadrature N={N}, K={K} (need K >= 2N+1)")
+    With onlattice=True: the on-lattice rule of Sec. 2.3 (N = 3, the 12 integer
+    stencil vectors of length 5 on every shell, N_pop = 48; K is ignored), with
+    perfect streaming; sx, sy hold the integer stencil vectors."""
+
+    def __init__(self, N: int, K: int = 0, onlattice: bool = False):
+        self.N = int(N)
+        self.onlattice = bool(onlattice)
+        if onlattice:
+            self._h = lib().orc_create_onlattice(self.N)
+            if not self._h:
+                raise ValueError(f"no on-lattice rule for N={N} (only N = 3)")
+            self.K = lib().orc_npop(self._h) // (self.N + 1)
+        else:
+            self.K = int(K)
+            self._h = lib().orc_create(self.N, self.K)
+            if not self._h:
+                raise ValueError(f"invalid quadrature N={N}, K={K} (need K >= 2N+1)")
         self.npop = lib().orc_npop(self._h)
         self.nbasis = lib().orc_nbasis(self._h)
         self.p0 = np.zeros(self.npop)
@@ -162,6 +178,11 @@ class Quadrature:
         self.vy = np.zeros(self.npop)
         self.w = np.zeros(self.npop)
         lib().orc_tables(self._h, _p(self.p0), _p(self.vx), _p(self.vy), _p(self.w))
+        self.sx = self.sy = None
+        if onlattice:
+            self.sx = np.zeros(self.npop, dtype=np.int32)
+            self.sy = np.zeros(self.npop, dtype=np.int32)
+            lib().orc_shifts(self._h, self.sx.ctypes.data_as(_ip), self.sy.ctypes.data_as(_ip))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -10,10 +10,13 @@
  * table or constant with the CUDA library, and the library never calls it.
  *
  * Every routine follows one passage of the paper, in the paper's order:
- *   quadrature        Sec. 2.3, Eq. (off-lattice-quad) and the Laguerre rule above it
+ *   quadrature        Sec. 2.3, Eq. (off-lattice-quad) and the Laguerre rule above it;
+ *                     the on-lattice rule of Sec. 2.3 (Eq. mj-orthogonal-conditions,
+ *                     stencil vectors of length 5, Fig. 1 left)
  *   equilibrium       Sec. 2.2, Eqs. (mj-feq-expansion), (mj-projection-coefficients),
  *                     (mj-feq-expansion-truncated); the MJ distribution Eq. (feq_dist)
- *   streaming         Sec. 2.2, Eqs. (streaming), (interpolation)
+ *   streaming         Sec. 2.2, Eqs. (streaming), (interpolation); on-lattice: the
+ *                     exact shift by the stencil vector (Sec. 2.3, perfect streaming)
  *   moments           Sec. 2.2, Eq. (discrete_sum_moments)
  *   Landau frame      Sec. 2.2, the eigenproblem eps U^a = T^{ab} U_b and eps = 2P = 2nT
  *   collision         Sec. 2.2, Eq. (discrete-rbe) (relaxation toward f^eq)
@@ -114,6 +117,8 @@ typedef struct {
     int *be, *ba, *bb;        /* cone monomial p0^e px^a py^b, one per basis function */
     double *Ginv;             /* nb x nb inverse of the continuous Gram matrix */
     double *Bw;               /* npop x nb: w_i * B_m(p_i) */
+    int onlat;                /* on-lattice rule: streaming shifts by (sx, sy) */
+    int *sx, *sy;             /* per population, integer stencil vector (on-lattice only) */
 } orc_quad;
 
 /* Angular integral of cos^a sin^b over [0, 2pi]: zero unless a and b are
@@ -181,7 +186,53 @@ void orc_destroy(orc_quad *q)
     free(q->p0); free(q->vx); free(q->vy); free(q->w);
     free(q->be); free(q->ba); free(q->bb);
     free(q->Ginv); free(q->Bw);
+    free(q->sx); free(q->sy);
     free(q);
+}
+
+/* Projection data of the truncated equilibrium (Eqs. mj-projection-coefficients,
+ * mj-feq-expansion-truncated) for the nodes and weights already in q: the cone
+ * monomial basis, the inverse of its continuous Gram matrix, and w_i B_m(p_i).
+ * Returns 0 on success. */
+static int build_projection(orc_quad *q)
+{
+    const int N = q->N;
+    /* cone monomials of degree k <= N: e in {0,1}, a + b = k - e */
+    q->be = malloc(sizeof(int) * q->nb);
+    q->ba = malloc(sizeof(int) * q->nb);
+    q->bb = malloc(sizeof(int) * q->nb);
+    int m = 0;
+    for (int k = 0; k <= N; ++k)
+        for (int e = 0; e <= 1 && e <= k; ++e)
+            for (int a = k - e; a >= 0; --a) {
+                q->be[m] = e;
+                q->ba[m] = a;
+                q->bb[m] = k - e - a;
+                ++m;
+            }
+
+    /* continuous Gram matrix G_mn = int exp(-p) B_m B_n d^2p/p0
+     *   = (k_m + k_n)! * int cos^(a_m+a_n) sin^(b_m+b_n) dtheta   (d^2p/p0 = dp dtheta) */
+    double *G = malloc(sizeof(double) * q->nb * q->nb);
+    for (int i = 0; i < q->nb; ++i)
+        for (int j = 0; j < q->nb; ++j) {
+            int km = q->be[i] + q->ba[i] + q->bb[i];
+            int kn = q->be[j] + q->ba[j] + q->bb[j];
+            G[i * q->nb + j] = factorial(km + kn) *
+                               orc_angular_integral(q->ba[i] + q->ba[j], q->bb[i] + q->bb[j]);
+        }
+    q->Ginv = malloc(sizeof(double) * q->nb * q->nb);
+    int bad = invert(q->nb, G, q->Ginv);
+    free(G);
+    if (bad) return 1;
+
+    q->Bw = malloc(sizeof(double) * q->npop * q->nb);
+    for (int i = 0; i < q->npop; ++i) {
+        double p = q->p0[i], px = p * q->vx[i], py = p * q->vy[i];
+        for (int b = 0; b < q->nb; ++b)
+            q->Bw[i * q->nb + b] = q->w[i] * ipow(p, q->be[b]) * ipow(px, q->ba[b]) * ipow(py, q->bb[b]);
+    }
+    return 0;
 }
 
 /* Build the quadrature of Eq. (off-lattice-quad):
@@ -218,42 +269,110 @@ orc_quad *orc_create(int N, int K)
         }
     }
 
-    /* cone monomials of degree k <= N: e in {0,1}, a + b = k - e */
-    q->be = malloc(sizeof(int) * q->nb);
-    q->ba = malloc(sizeof(int) * q->nb);
-    q->bb = malloc(sizeof(int) * q->nb);
-    int m = 0;
-    for (int k = 0; k <= N; ++k)
-        for (int e = 0; e <= 1 && e <= k; ++e)
-            for (int a = k - e; a >= 0; --a) {
-                q->be[m] = e;
-                q->ba[m] = a;
-                q->bb[m] = k - e - a;
-                ++m;
-            }
-
-    /* continuous Gram matrix G_mn = int exp(-p) B_m B_n d^2p/p0
-     *   = (k_m + k_n)! * int cos^(a_m+a_n) sin^(b_m+b_n) dtheta   (d^2p/p0 = dp dtheta) */
-    double *G = malloc(sizeof(double) * q->nb * q->nb);
-    for (int i = 0; i < q->nb; ++i)
-        for (int j = 0; j < q->nb; ++j) {
-            int km = q->be[i] + q->ba[i] + q->bb[i];
-            int kn = q->be[j] + q->ba[j] + q->bb[j];
-            G[i * q->nb + j] = factorial(km + kn) *
-                               orc_angular_integral(q->ba[i] + q->ba[j], q->bb[i] + q->bb[j]);
-        }
-    q->Ginv = malloc(sizeof(double) * q->nb * q->nb);
-    int bad = invert(q->nb, G, q->Ginv);
-    free(G);
-    if (bad) { orc_destroy(q); return NULL; }
-
-    q->Bw = malloc(sizeof(double) * q->npop * q->nb);
-    for (int i = 0; i < q->npop; ++i) {
-        double p = q->p0[i], px = p * q->vx[i], py = p * q->vy[i];
-        for (int b = 0; b < q->nb; ++b)
-            q->Bw[i * q->nb + b] = q->w[i] * ipow(p, q->be[b]) * ipow(px, q->ba[b]) * ipow(py, q->bb[b]);
-    }
+    if (build_projection(q)) { orc_destroy(q); return NULL; }
     return q;
+}
+
+/* On-lattice rule of Sec. 2.3 (Fig. 1, left): the stencil vectors n_i are the
+ * integer vectors of length R = 5, (+-5, 0), (0, +-5), (+-3, +-4), (+-4, +-3),
+ * the same 12 on every energy shell; the shells are the roots of the radial
+ * polynomial of degree N+1 (the Gauss-Laguerre nodes, N = 3); momenta
+ * p_i = p_r (1, n_i / |n_i|).  Weights from the orthonormal conditions
+ * (Eq. mj-orthogonal-conditions), which for a product rule are the radial
+ * Gauss-Laguerre conditions (exact to degree 2N+1) times the angular ones
+ * sum_i v_i cos^a sin^b = int cos^a sin^b dtheta for a + b <= 2N.  The angular
+ * weights are taken constant on the two symmetry classes of the stencil (on
+ * the axes, off the axes) and solved by least squares over all those
+ * conditions; the rule is rejected (NULL) unless every condition holds to
+ * 1e-12 and both weights are positive.  Populations are shell-major,
+ * i = r*12 + j, the vectors ordered by angle from 0.  Only N = 3 (a fourth-order
+ * rule needs vectors of length 5 sqrt(13), Sec. 2.3). */
+orc_quad *orc_create_onlattice(int N)
+{
+    if (N != 3) return NULL;
+    const int R2 = 25, K = 12;
+    int vec[12][2], nv = 0;
+    for (int a = -5; a <= 5; ++a)
+        for (int b = -5; b <= 5; ++b)
+            if (a * a + b * b == R2 && nv < 12) { vec[nv][0] = a; vec[nv][1] = b; ++nv; }
+    if (nv != K) return NULL;
+    /* order by angle in [0, 2 pi) (insertion sort) */
+    for (int i = 1; i < nv; ++i)
+        for (int j = i; j > 0; --j) {
+            double t0 = atan2(vec[j - 1][1], vec[j - 1][0]), t1 = atan2(vec[j][1], vec[j][0]);
+            if (t0 < 0) t0 += 2.0 * ORC_PI;
+            if (t1 < 0) t1 += 2.0 * ORC_PI;
+            if (t1 < t0) {
+                int ta = vec[j][0], tb = vec[j][1];
+                vec[j][0] = vec[j - 1][0]; vec[j][1] = vec[j - 1][1];
+                vec[j - 1][0] = ta; vec[j - 1][1] = tb;
+            }
+        }
+    /* angular weights: class 0 on the axes, class 1 off the axes */
+    int cls[12];
+    double c[12], sn[12];
+    for (int j = 0; j < K; ++j) {
+        cls[j] = (vec[j][0] == 0 || vec[j][1] == 0) ? 0 : 1;
+        c[j] = vec[j][0] / 5.0;
+        sn[j] = vec[j][1] / 5.0;
+    }
+    double A[4] = {0, 0, 0, 0}, rhs[2] = {0, 0};
+    double Mrow[64][2], brow[64];
+    int nc = 0;
+    for (int a = 0; a <= 2 * N; ++a)
+        for (int b = 0; a + b <= 2 * N; ++b) {
+            Mrow[nc][0] = Mrow[nc][1] = 0.0;
+            for (int j = 0; j < K; ++j) Mrow[nc][cls[j]] += ipow(c[j], a) * ipow(sn[j], b);
+            brow[nc] = orc_angular_integral(a, b);
+            ++nc;
+        }
+    for (int k = 0; k < nc; ++k)
+        for (int u = 0; u < 2; ++u) {
+            rhs[u] += Mrow[k][u] * brow[k];
+            for (int v = 0; v < 2; ++v) A[u * 2 + v] += Mrow[k][u] * Mrow[k][v];
+        }
+    double Ai[4];
+    if (invert(2, A, Ai)) return NULL;
+    double vw[2] = {Ai[0] * rhs[0] + Ai[1] * rhs[1], Ai[2] * rhs[0] + Ai[3] * rhs[1]};
+    for (int k = 0; k < nc; ++k)
+        if (fabs(Mrow[k][0] * vw[0] + Mrow[k][1] * vw[1] - brow[k]) > 1e-12) return NULL;
+    if (!(vw[0] > 0.0) || !(vw[1] > 0.0)) return NULL;
+
+    orc_quad *q = calloc(1, sizeof(orc_quad));
+    q->N = N;
+    q->K = K;
+    q->npop = K * (N + 1);
+    q->nb = (N + 1) * (N + 1);
+    q->onlat = 1;
+    q->p0 = malloc(sizeof(double) * q->npop);
+    q->vx = malloc(sizeof(double) * q->npop);
+    q->vy = malloc(sizeof(double) * q->npop);
+    q->w = malloc(sizeof(double) * q->npop);
+    q->sx = malloc(sizeof(int) * q->npop);
+    q->sy = malloc(sizeof(int) * q->npop);
+    double pr[16], wpr[16];
+    if (orc_radial_rule(N, pr, wpr) != N + 1) { orc_destroy(q); return NULL; }
+    for (int r = 0; r <= N; ++r)
+        for (int j = 0; j < K; ++j) {
+            int i = r * K + j;
+            q->p0[i] = pr[r];
+            q->vx[i] = c[j];
+            q->vy[i] = sn[j];
+            q->w[i] = wpr[r] * vw[cls[j]];
+            q->sx[i] = vec[j][0];
+            q->sy[i] = vec[j][1];
+        }
+    if (build_projection(q)) { orc_destroy(q); return NULL; }
+    return q;
+}
+
+/* Integer stencil vectors of an on-lattice rule (0 for an off-lattice one). */
+int orc_shifts(const orc_quad *q, int *sx, int *sy)
+{
+    if (!q->onlat) return 0;
+    memcpy(sx, q->sx, sizeof(int) * q->npop);
+    memcpy(sy, q->sy, sizeof(int) * q->npop);
+    return 1;
 }
 
 int orc_npop(const orc_quad *q) { return q->npop; }
@@ -479,6 +598,17 @@ static int src_index(int i, int L, int bc)
 void orc_stream(const orc_quad *q, int nx, int ny, int bcx, int bcy, const double *f, double *fs)
 {
     long S = (long)nx * ny;
+    if (q->onlat) { /* perfect streaming: f*_i(x) = f_i(x - n_i) */
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y)
+            for (int i = 0; i < q->npop; ++i) {
+                int ys = src_index(y - q->sy[i], ny, bcy);
+                for (int x = 0; x < nx; ++x)
+                    fs[(long)i * S + (long)y * nx + x] =
+                        f[(long)i * S + (long)ys * nx + src_index(x - q->sx[i], nx, bcx)];
+            }
+        return;
+    }
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
         for (int i = 0; i < q->npop; ++i) {

@@ -577,3 +577,83 @@ def test_fig4_grid_convergence_plateau_for_few_angles():
         assert eps[10.0, K, 240] < eps[10.0, K, 40] / 3, eps
     assert eps[10.0, 12, 240] > 5 * eps[10.0, 120, 240], eps
 
+
+# --------------------------------------------------------------- on-lattice rule (Sec. 2.3)
+
+def test_onlattice_stencil_and_shells():
+    """Fig. 1 (left): the 12 integer vectors of length 5 on each of the N+1 = 4
+    shells, the shells at the roots of the degree-4 Laguerre polynomial."""
+    q = O.Quadrature(3, onlattice=True)
+    assert q.npop == 48 and q.K == 12
+    vec = set(zip(q.sx[:12].tolist(), q.sy[:12].tolist()))
+    assert vec == {(a, b) for a in range(-5, 6) for b in range(-5, 6) if a * a + b * b == 25}
+    for r in range(4):
+        assert (q.sx[12 * r:12 * r + 12] == q.sx[:12]).all() and (q.sy[12 * r:12 * r + 12] == q.sy[:12]).all()
+    np.testing.assert_allclose(q.vx, q.sx / 5.0, atol=1e-15)
+    np.testing.assert_allclose(q.vy, q.sy / 5.0, atol=1e-15)
+    nodes, _ = np.polynomial.laguerre.laggauss(4)
+    np.testing.assert_allclose(np.unique(q.p0), nodes, rtol=1e-12)
+    assert (q.w > 0).all()
+
+
+def test_onlattice_orthonormal_conditions():
+    """Eq. (mj-orthogonal-conditions) in the cone-monomial basis up to N = 3:
+    sum_i w_i B_m(p_i) B_n(p_i) equals the continuous Gram matrix, whose
+    angular factors come here from a dense uniform rule (exact for these degrees)."""
+    q = O.Quadrature(3, onlattice=True)
+    e, a, b = q.basis()
+    th = 2 * math.pi * np.arange(128) / 128
+    ang = lambda A, B: (np.cos(th) ** A * np.sin(th) ** B).sum() * 2 * math.pi / 128
+    P = np.stack([q.p0 ** ee * (q.p0 * q.vx) ** aa * (q.p0 * q.vy) ** bb for ee, aa, bb in zip(e, a, b)], 1)
+    disc = P.T @ (q.w[:, None] * P)
+    k = e + a + b
+    G = np.array([[math.factorial(int(k[m] + k[n])) * ang(a[m] + a[n], b[m] + b[n])
+                   for n in range(len(e))] for m in range(len(e))])
+    np.testing.assert_allclose(disc, G, atol=1e-10 * np.abs(G).max())
+
+
+def test_onlattice_streaming_is_an_exact_shift():
+    """Perfect streaming: one free-streaming step moves population i by its
+    stencil vector (periodic: a roll; copy-out: clamped source indices)."""
+    q = O.Quadrature(3, onlattice=True)
+    ny, nx = 11, 13
+    f0 = W.random_populations(q.npop, ny, nx, seed=4)
+    f1, _ = q.run(f0, math.inf, 1, O.BC_PERIODIC, O.BC_PERIODIC)
+    for i in range(q.npop):
+        np.testing.assert_array_equal(f1[i], np.roll(f0[i], (q.sy[i], q.sx[i]), axis=(0, 1)))
+    f3, _ = q.run(f0, math.inf, 3, O.BC_PERIODIC, O.BC_PERIODIC)
+    for i in range(q.npop):
+        np.testing.assert_array_equal(f3[i], np.roll(f0[i], (3 * q.sy[i], 3 * q.sx[i]), axis=(0, 1)))
+    fc, _ = q.run(f0, math.inf, 1, O.BC_COPYOUT, O.BC_COPYOUT)
+    ys, xs = np.arange(ny), np.arange(nx)
+    for i in range(q.npop):
+        src_y = np.clip(ys - q.sy[i], 0, ny - 1)
+        src_x = np.clip(xs - q.sx[i], 0, nx - 1)
+        np.testing.assert_array_equal(fc[i], f0[i][np.ix_(src_y, src_x)])
+
+
+def test_onlattice_feq_moments_to_rank3_and_conservation():
+    """The on-lattice rule of order 3 carries the MJ moments up to rank 3 exactly
+    and the collision conserves N^0 and T^0nu."""
+    q = O.Quadrature(3, onlattice=True)
+    n, T, bx, by = 0.8, 0.9, 0.35, -0.3
+    U = U_of(bx, by)
+    f = q.feq(n, T, U[1], U[2])
+    Nd, Td = moments9_to_tensors(q.moments(f))
+    Nr, Tr = mj_tensors(n, T, U)
+    np.testing.assert_allclose(Nd, Nr, atol=5e-14)
+    np.testing.assert_allclose(Td, Tr, atol=5e-13)
+    ref = np.zeros((3, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                ref[i, j, k] = O.mj_moment((i, j, k), n, T, U[1], U[2])
+    np.testing.assert_allclose(rank3(f, q), ref, atol=1e-12)
+    fr = W.random_populations(q.npop, 3, 4, seed=8) * q.w[:, None, None]
+    fn, flagged = q.collide(fr, tau=1.3)
+    assert flagged == 0
+    d = (fn - fr).reshape(q.npop, -1)
+    for wgt in [q.p0, q.p0 * q.p0, q.p0 * q.p0 * q.vx, q.p0 * q.p0 * q.vy]:
+        scale = (np.abs(wgt)[:, None] * fr.reshape(q.npop, -1)).sum(0)
+        assert (np.abs((wgt[:, None] * d).sum(0)) / scale).max() < 5e-14
+
