@@ -187,17 +187,17 @@ def cpu_baseline(w: W.Workload, kn_list, budget_s: float = 12.0):
     """Time the FP64 oracle (as it stands) on the host cores on a bounded sample:
     the full grid and quadrature of the workload, a few time steps per Kn."""
     import oracle as O
-    q = O.Quadrature(w.N, w.K)
+    q = O.Quadrature(w.N, w.K, onlattice=bool(w.extra.get("onlattice")))
     fl = W.workload_fields(w)
     f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
     # calibrate with one step, then fill the budget
     t0 = time.perf_counter()
-    q.run(f0, W.tau_from_kn(kn_list[0], w.nx), 1, w.bcx, w.bcy)
+    q.run(f0, W.tau_from_kn(kn_list[0], w.nx, W.light_speed(w)), 1, w.bcx, w.bcy)
     t1 = time.perf_counter() - t0
     steps = max(1, int(budget_s / max(t1, 1e-6) / len(kn_list)))
     t0 = time.perf_counter()
     for kn in kn_list:
-        q.run(f0, W.tau_from_kn(kn, w.nx), steps, w.bcx, w.bcy)
+        q.run(f0, W.tau_from_kn(kn, w.nx, W.light_speed(w)), steps, w.bcx, w.bcy)
     dt = time.perf_counter() - t0
     updates = w.sites * w.npop * steps * len(kn_list)
     return {"value": updates / dt, "unit": METRIC, "cores": O.max_threads(), "kind": "oracle",
@@ -213,19 +213,19 @@ def run_reference(args, w: W.Workload, precision: str):
     cb = cpu_baseline(w, kn_list, budget_s=8.0)
     # timed steps: each a bounded sample of the workload
     import oracle as O
-    q = O.Quadrature(w.N, w.K)
+    q = O.Quadrature(w.N, w.K, onlattice=bool(w.extra.get("onlattice")))
     fl = W.workload_fields(w)
     f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
     t0 = time.perf_counter()
-    q.run(f0, W.tau_from_kn(kn_list[0], w.nx), 1, w.bcx, w.bcy)
+    q.run(f0, W.tau_from_kn(kn_list[0], w.nx, W.light_speed(w)), 1, w.bcx, w.bcy)
     per = time.perf_counter() - t0
     steps_per = max(1, int(6.0 / max(per, 1e-6) / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        q.run(f0, W.tau_from_kn(kn_list[0], w.nx), steps_per, w.bcx, w.bcy)
+        q.run(f0, W.tau_from_kn(kn_list[0], w.nx, W.light_speed(w)), steps_per, w.bcx, w.bcy)
     times = []
     for s in range(args.steps):
         t0 = time.perf_counter()
-        q.run(f0, W.tau_from_kn(kn_list[s % len(kn_list)], w.nx), steps_per, w.bcx, w.bcy)
+        q.run(f0, W.tau_from_kn(kn_list[s % len(kn_list)], w.nx, W.light_speed(w)), steps_per, w.bcx, w.bcy)
         times.append(time.perf_counter() - t0)
     upd = w.sites * w.npop * steps_per
     value = upd * len(times) / sum(times)
@@ -426,8 +426,9 @@ def main():
     # joined back to the timing stream, so their (latency-bound) kernels overlap
     stream = torch.cuda.Stream(device=dev)
     pstreams = [torch.cuda.Stream(device=dev) for _ in kn_list]
-    sims = [R.Simulation(w.nx, w.ny, w.N, w.K, W.tau_from_kn(kn, w.nx), precision, w.bcx, w.bcy,
-                         stream=ps) for kn, ps in zip(kn_list, pstreams)]
+    sims = [R.Simulation(w.nx, w.ny, w.N, w.K, W.tau_from_kn(kn, w.nx, W.light_speed(w)), precision, w.bcx, w.bcy,
+                         stream=ps, onlattice=bool(w.extra.get("onlattice")))
+            for kn, ps in zip(kn_list, pstreams)]
     outs = [torch.empty((6, w.ny, w.nx), dtype=torch.float64, device=dev) for _ in kn_list]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     # tiling chosen by the library's autotuner (cached per problem shape)
@@ -444,6 +445,8 @@ def main():
                     "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
 
     def kernel_name(sim):
+        if sim.onlattice:
+            return "rlbm_kernel<MODE_STEP_LATTICE>"
         if sim.population_groups > 1:
             return {"pair": "rlbm_pair_groups_kernel",
                     "per-tile": "rlbm_kernel<MODE_STEP> (population groups)"}[sim.step_kernel]
@@ -537,6 +540,8 @@ def main():
                       "bf16n": "bf16-storage/f32"}[precision],
             "data": "synthetic",
             "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
+                       "quadrature": "on-lattice, stencil vectors of length 5" if w.extra.get("onlattice")
+                       else "off-lattice product rule",
                        "npop": w.npop, "kn": kn_json(kn_list), "time_steps_per_problem": steps_pp,
                        "problems_per_step": len(kn_list), "precision": precision,
                        "bc": ["copy-out" if w.bcx else "periodic", "copy-out" if w.bcy else "periodic"],

@@ -102,6 +102,27 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
                         int precision, void *cuda_stream, void *dev_buffers,
                         size_t dev_buffer_bytes);
 
+/* Create a handle for the on-lattice rule of Sec. 2.3 (Fig. 1, left; the
+ * quadrature with prescribed abscissas): order N = 3, the 12 integer stencil
+ * vectors n of length 5 ((+-5,0), (0,+-5), (+-3,+-4), (+-4,+-3)) on each of the 4
+ * Gauss-Laguerre energy shells, N_pop = 48, momenta p_r (1, n/5), weights
+ * satisfying the orthonormal conditions (Eq. mj-orthogonal-conditions) as a
+ * product of the radial Gauss-Laguerre weights and two angular weights (axis and
+ * off-axis vectors).  Populations are shell-major, i = 12 r + j, the vectors
+ * ordered by angle from 0.  Streaming is perfect: population i moves by its
+ * stencil vector n_i, 5 cells per step, with no interpolation (so the speed of
+ * light is 5 cells per step; boundary conditions as for rlbm_create: periodic
+ * wrap or copy-out clamp of the source cell).  Equilibrium, Landau frame and
+ * collision are those of rlbm_create.  FP32 and FP64 storage only
+ * (RLBM_ERR_UNSUPPORTED otherwise: the 16-bit forms scale by one weight per
+ * shell); the per-tile kernel with 12 populations per warp only (rlbm_set_tiling
+ * refuses anything else).  Other arguments and errors as for rlbm_create. */
+rlbm_status rlbm_create_onlattice(rlbm_t **out, rlbm_grid grid, double tau, int precision,
+                                  void *cuda_stream, void *dev_buffers, size_t dev_buffer_bytes);
+
+/* 1 if the handle uses the on-lattice rule, 0 if the off-lattice one, -1 for NULL. */
+int rlbm_is_onlattice(const rlbm_t *h);
+
 void rlbm_destroy(rlbm_t *h);
 
 /* Message of the most recent failure on h (or of the last failed create when

@@ -7,7 +7,9 @@
 
 namespace rlbmk {
 
-enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_MOMENTS = 2 };
+// MODE_STEP_LATTICE: a step of the on-lattice rule (perfect streaming by the
+// integer stencil vector of each population, no interpolation).
+enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_MOMENTS = 2, MODE_STEP_LATTICE = 3 };
 
 constexpr int kMaxN = 5;
 constexpr int kMaxWarps = 16;
@@ -39,6 +41,7 @@ struct KernelArgs {
     double *out[6];                            // MODE_MOMENTS fields
     const unsigned long long *masks; // per warp: bit k = (v_x >= 0), (v_y >= 0) of its population k (k < 64)
     const void *pairtab; // npop x 3 float4: paired constants of the two-sites-per-lane kernel (FP32 arithmetic)
+    const int2 *shifts;  // npop: integer stencil vectors of the on-lattice rule (else NULL)
     long long wait_cycles; // bound of every mbarrier wait of the bulk-staged pair kernel (SM cycles)
     unsigned extra_tx;     // test hook: bytes expected on top of the copies (makes the waits run out)
     int *status;
@@ -121,6 +124,11 @@ cudaError_t launch_f16(int mode, int N, int P, bool two_d, bool full, dim3 grid,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_bf16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t st, const KernelArgs &a);
+// A step of the on-lattice rule (per-tile kernel, N = 3, P = 12), FP64 and FP32 storage.
+cudaError_t launch_lattice_f64(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               const KernelArgs &a);
+cudaError_t launch_lattice_f32(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               const KernelArgs &a);
 // The same per-tile kernel for N = 4, 5, with FP64 per-site arithmetic in every storage type.
 cudaError_t launch_f64_n45(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                            size_t smem, cudaStream_t st, const KernelArgs &a);

@@ -171,6 +171,13 @@ __device__ __forceinline__ int bc_index(int i, int L, int bc)
     return i < 0 ? 0 : (i >= L ? L - 1 : i);
 }
 
+// The same for any offset (shifts of several cells, grids smaller than the shift).
+__device__ __forceinline__ int bc_any(int i, int L, int bc)
+{
+    if (bc == 0) return ((i % L) + L) % L;
+    return i < 0 ? 0 : (i >= L ? L - 1 : i);
+}
+
 template <class R>
 __device__ __forceinline__ void ld4(const R *p, R &x, R &y, R &z, R &w);
 template <>
@@ -377,8 +384,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     LR *red = reinterpret_cast<LR *>(smem_raw); // [5][G][32]
 
     R fs[P];
-    const bool stream = (MODE == MODE_STEP);
-    const bool need_site = (MODE != MODE_STEP) || a.collide;
+    constexpr bool LATTICE = (MODE == MODE_STEP_LATTICE); // on-lattice rule: exact shifts
+    constexpr bool STEP = (MODE == MODE_STEP) || LATTICE;
+    const bool stream = (MODE == MODE_STEP); // bilinear pull
+    const bool need_site = !STEP || a.collide;
 
     if (MODE != MODE_INIT) {
         // two partial sums per moment (even / odd populations) halve the add chains
@@ -409,7 +418,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
             for (int kk = 0; kk < CH; ++kk) {
                 const int k = c0 + kk;
                 const St *pk = base + (long long)k * S;
-                if (k < pc) {
+                if (k < pc && LATTICE) { // perfect streaming: f_i(x - n_i), Sec. 2.3
+                    const int2 sh = __ldg(a.shifts + i0 + k);
+                    const int xs = bc_any(x - sh.x, a.nx, a.bcx), ys = bc_any(y - sh.y, a.ny, a.bcy);
+                    fa[kk] = Io<St, R>::ld(fin + (long long)(i0 + k) * S + (long long)ys * a.nx + xs);
+                } else if (k < pc) {
                     fa[kk] = Io<St, R>::ld(pk + x);
                     if (stream) {
                         const int xs = ((mx >> k) & 1ull) ? xm : xp; // pull from x - sgn(v_x)
@@ -446,7 +459,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
             }
         }
         // free streaming stores every group now; a collision parks all groups but the last
-        if (MODE == MODE_STEP && (!need_site || rho + 1 < NR) && act) {
+        if (STEP && (!need_site || rho + 1 < NR) && act) {
             St *ob = fout + (long long)i0 * S + site;
 #pragma unroll
             for (int k = 0; k < P; ++k)
@@ -499,7 +512,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
     const LR itau = Par<LR>::inv_tau(a);
     const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
-    constexpr bool kSR = (sizeof(St) == 2) && (MODE == MODE_STEP);
+    constexpr bool kSR = (sizeof(St) == 2) && STEP;
     unsigned rng = 0;
     if (kSR) rng = mix32(unsigned(site) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
 #pragma unroll 1
@@ -509,7 +522,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     const int pc = FULL ? P : min(a.P, a.K - vw * a.P);
     const R *tab = reinterpret_cast<const R *>(a.poptab) + (long long)i0 * TW;
     St *obase = fout + (long long)i0 * S + site;
-    if (MODE == MODE_STEP && rho + 1 < NR && act) { // parked group: f* back from its output slot
+    if (STEP && rho + 1 < NR && act) { // parked group: f* back from its output slot
 #pragma unroll
         for (int k = 0; k < P; ++k)
             if (k < pc) fs[k] = Io<St, R>::lds(obase + (long long)k * S);

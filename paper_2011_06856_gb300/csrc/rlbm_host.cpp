@@ -129,6 +129,8 @@ struct Quad {
     int N = 0, K = 0, npop = 0;
     std::vector<double> pr, wr;            // radial nodes / weights (N+1)
     std::vector<double> p0, vx, vy, w;     // per population
+    bool onlat = false;                    // on-lattice rule: perfect streaming by (sx, sy)
+    std::vector<int> sx, sy;               // per population integer stencil vector (on-lattice)
 };
 
 bool make_quadrature(int N, int K, Quad &q)
@@ -159,6 +161,53 @@ bool make_quadrature(int N, int K, Quad &q)
             q.vx[i] = c;
             q.vy[i] = s;
             q.w[i] = q.wr[r] * (2.0 * kPi / K);
+        }
+    return true;
+}
+
+// On-lattice rule of Sec. 2.3 (Fig. 1, left), order N = 3: the 12 integer
+// vectors of length 5 on each of the 4 Gauss-Laguerre shells,
+// p = p_r (1, n / 5).  A product rule satisfies the orthonormal conditions
+// (Eq. mj-orthogonal-conditions) when its radial part integrates p^k exactly
+// for k <= 2N (the Gauss-Laguerre rule does to 2N+1) and its angular part
+// integrates trigonometric polynomials of degree <= 2N = 6.  The stencil is
+// invariant under rotations by 90 degrees, so every harmonic m not divisible by
+// 4 sums to zero over it; with one weight v_a on the 4 axis vectors and one v_o
+// on the 8 others, what remains is sum v = 2 pi (m = 0) and
+// sum v cos 4 theta = 0 (m = 4):  4 v_a + 8 v_o = 2 pi,  4 v_a + S v_o = 0 with
+// S = sum over the off-axis vectors of cos 4 theta (= 8 cos 4 atan(4/3)).
+// Populations shell-major, i = 12 r + j, the vectors ordered by angle from 0.
+bool make_onlattice_quadrature(Quad &q)
+{
+    const int N = 3, K = 12;
+    if (!make_quadrature(N, K, q)) return false; // radial nodes and weights
+    std::vector<std::pair<double, std::pair<int, int>>> vec;
+    for (int a = -5; a <= 5; ++a)
+        for (int b = -5; b <= 5; ++b)
+            if (a * a + b * b == 25) {
+                double th = std::atan2(double(b), double(a));
+                if (th < 0.0) th += 2.0 * kPi;
+                vec.push_back({th, {a, b}});
+            }
+    if (int(vec.size()) != K) return false;
+    std::sort(vec.begin(), vec.end());
+    double S = 0.0;
+    for (auto &v : vec)
+        if (v.second.first != 0 && v.second.second != 0) S += std::cos(4.0 * v.first);
+    const double vo = 2.0 * kPi / (8.0 - S), va = -S * vo / 4.0;
+    if (!(vo > 0.0) || !(va > 0.0)) return false;
+    q.onlat = true;
+    q.sx.assign(q.npop, 0);
+    q.sy.assign(q.npop, 0);
+    for (int r = 0; r <= N; ++r)
+        for (int j = 0; j < K; ++j) {
+            const int i = r * K + j;
+            const int a = vec[j].second.first, b = vec[j].second.second;
+            q.vx[i] = a / 5.0;
+            q.vy[i] = b / 5.0;
+            q.w[i] = q.wr[r] * ((a == 0 || b == 0) ? va : vo);
+            q.sx[i] = a;
+            q.sy[i] = b;
         }
     return true;
 }
@@ -415,13 +464,19 @@ rlbm_status build_tables(rlbm_t *h)
         }
     }
     const size_t o_pair = o_mask + align256(masks.size() * sizeof(unsigned long long));
-    const size_t total = o_pair + align256(ptab.size() * 4);
+    // on-lattice rule: per population integer stencil vector (sx, sy)
+    std::vector<int> shifts;
+    if (q.onlat)
+        for (int i = 0; i < npop; ++i) { shifts.push_back(q.sx[i]); shifts.push_back(q.sy[i]); }
+    const size_t o_shift = o_pair + align256(ptab.size() * 4);
+    const size_t total = o_shift + align256(shifts.size() * sizeof(int));
     std::vector<unsigned char> blob(total, 0);
     if (r64) put<double>(blob, o_pop, pop); else put<float>(blob, o_pop, pop);
     if (l64) { put<double>(blob, o_shell, shell); put<double>(blob, o_rt, rt); }
     else { put<float>(blob, o_shell, shell); put<float>(blob, o_rt, rt); }
     std::memcpy(blob.data() + o_mask, masks.data(), masks.size() * sizeof(unsigned long long));
     put<float>(blob, o_pair, ptab);
+    if (!shifts.empty()) std::memcpy(blob.data() + o_shift, shifts.data(), shifts.size() * sizeof(int));
 
     if (h->d_tabs) { // re-tiling: replace the tables
         RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -469,6 +524,7 @@ rlbm_status build_tables(rlbm_t *h)
     a.rtab = (const unsigned char *)h->d_tabs + o_rt;
     a.masks = reinterpret_cast<const unsigned long long *>((const unsigned char *)h->d_tabs + o_mask);
     a.pairtab = ptab.empty() ? nullptr : (const unsigned char *)h->d_tabs + o_pair;
+    a.shifts = shifts.empty() ? nullptr : reinterpret_cast<const int2 *>((const unsigned char *)h->d_tabs + o_shift);
     a.status = h->d_status;
     a.ctr = reinterpret_cast<unsigned *>(h->d_status + 1);
     a.wait_cycles = h->wait_cycles;
@@ -492,6 +548,12 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     const bool two_d = h->grid.ny > 1;
     const bool full = h->K == h->R * h->Gs * h->P;
     cudaError_t e;
+    if (mode == rlbmk::MODE_STEP && h->q.onlat) { // perfect streaming (FP32/FP64, P = 12: create, set_tiling)
+        e = h->prec == RLBM_FP64 ? rlbmk::launch_lattice_f64(two_d, grid, block, smem, h->stream, a)
+                                 : rlbmk::launch_lattice_f32(two_d, grid, block, smem, h->stream, a);
+        if (e == cudaSuccess) ++h->launches;
+        return e;
+    }
     switch (h->prec) {
     case RLBM_FP64: e = rlbmk::launch_f64(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a); break;
     case RLBM_FP32:
@@ -511,7 +573,7 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
 // to FP32 storage only.
 bool pair_possible(const rlbm_t *h, int P)
 {
-    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3) return false;
+    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3 || h->q.onlat) return false;
     if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
     if (!(P == 8 || P == 12 || P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
     int gs = 0, ng = 0;
@@ -602,7 +664,7 @@ rlbm_status setup_tma(rlbm_t *h)
     delete[] h->tma;
     h->tma = nullptr;
     const char *off = std::getenv("RLBM_NO_TMA");
-    if ((off && off[0] == '1') || h->no_tma || h->N > 3 || h->R > 1) return RLBM_OK;
+    if ((off && off[0] == '1') || h->no_tma || h->N > 3 || h->R > 1 || h->q.onlat) return RLBM_OK;
     const size_t es = storage_size(h->prec);
     const int HX = int(16 / es), BW = 32 + 2 * HX;
     const int nx = h->grid.nx, ny = h->grid.ny, npop = h->npop;
@@ -786,8 +848,9 @@ size_t rlbm_population_bytes(rlbm_grid grid, int order_N, int angles_K, int prec
            size_t(grid.ny);
 }
 
-rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K, double tau,
-                        int precision, void *cuda_stream, void *dev_buffers, size_t dev_buffer_bytes)
+static rlbm_status create_impl(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K, double tau,
+                               int precision, void *cuda_stream, void *dev_buffers, size_t dev_buffer_bytes,
+                               bool onlat)
 {
     if (!out) return fail(nullptr, RLBM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -808,6 +871,9 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
     if (order_N > rlbmk::kMaxN)
         return fail(nullptr, RLBM_ERR_UNSUPPORTED, "kernels are built for N = 2..%d (got N=%d)", rlbmk::kMaxN,
                     order_N);
+    if (onlat && precision != RLBM_FP32 && precision != RLBM_FP64)
+        return fail(nullptr, RLBM_ERR_UNSUPPORTED,
+                    "the on-lattice rule is built for FP32 and FP64 storage (its weights differ within a shell)");
 
     rlbm_t *h = new (std::nothrow) rlbm();
     if (!h) return fail(nullptr, RLBM_ERR_OOM, "host allocation failed");
@@ -823,7 +889,7 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
     // runs in FP64 for every storage type
     h->site_fp64 = (precision != RLBM_FP64) &&
                    (order_N >= 4 || ((precision == RLBM_FP32) && env && env[0] == '1'));
-    if (!make_quadrature(order_N, angles_K, h->q)) {
+    if (!(onlat ? make_onlattice_quadrature(h->q) : make_quadrature(order_N, angles_K, h->q))) {
         delete h;
         return fail(nullptr, RLBM_ERR_ARG, "quadrature construction failed");
     }
@@ -838,7 +904,7 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
                     "(at most %d angles with N=%d in 16-bit storage)",
                     angles_K, single_group_capacity(order_N), order_N);
     }
-    if (const char *ep = std::getenv("RLBM_TILE_P")) { // experiment hook: force P if it fits
+    if (const char *ep = onlat ? nullptr : std::getenv("RLBM_TILE_P")) { // experiment hook: force P if it fits
         const int P = std::atoi(ep);
         const int gs = (angles_K + P - 1) / P;
         if ((P == 8 || P == 12 || P == 16 || P == 24 || P == 32 || P == 48 || P == 64) &&
@@ -884,6 +950,21 @@ rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K,
     *out = h;
     return RLBM_OK;
 }
+
+rlbm_status rlbm_create(rlbm_t **out, rlbm_grid grid, int order_N, int angles_K, double tau,
+                        int precision, void *cuda_stream, void *dev_buffers, size_t dev_buffer_bytes)
+{
+    return create_impl(out, grid, order_N, angles_K, tau, precision, cuda_stream, dev_buffers,
+                       dev_buffer_bytes, false);
+}
+
+rlbm_status rlbm_create_onlattice(rlbm_t **out, rlbm_grid grid, double tau, int precision, void *cuda_stream,
+                                  void *dev_buffers, size_t dev_buffer_bytes)
+{
+    return create_impl(out, grid, 3, 12, tau, precision, cuda_stream, dev_buffers, dev_buffer_bytes, true);
+}
+
+int rlbm_is_onlattice(const rlbm_t *h) { return h ? (h->q.onlat ? 1 : 0) : -1; }
 
 void rlbm_destroy(rlbm_t *h)
 {
@@ -1060,6 +1141,8 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
     int gs = 0, ng = 0;
     if (!ok || !group_tiling(h->N, h->K, P, gs, ng))
         return fail(h, RLBM_ERR_UNSUPPORTED, "no compiled tiling with P=%d for N=%d, K=%d", P, h->N, h->K);
+    if (h->q.onlat && (P != 12 || kind != 0))
+        return fail(h, RLBM_ERR_UNSUPPORTED, "the on-lattice rule runs the per-tile kernel with P=12 only");
     if (ng > 1 && kind != 0 && kind != 2)
         return fail(h, RLBM_ERR_UNSUPPORTED,
                     "K=%d needs several population groups per warp: per-tile or two-sites-per-lane kernel only",
@@ -1091,7 +1174,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
     if (launches_per_trial < 1) return fail(h, RLBM_ERR_ARG, "launches_per_trial must be >= 1");
     const TuneKey key{h->grid.nx, h->grid.ny, h->N, h->K, h->prec, h->grid.bc_x, h->grid.bc_y,
-                      h->site_fp64 ? 1 : 0};
+                      (h->site_fp64 ? 1 : 0) | (h->q.onlat ? 2 : 0)};
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = tune_cache().find(key);
@@ -1111,6 +1194,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
     for (int P : sizes) {
         int gs = 0, ng = 0;
         if (!group_tiling(h->N, h->K, P, gs, ng)) continue;
+        if (h->q.onlat && P != 12) continue; // the on-lattice kernel is built for P = 12
         if (P > 2 * h->K) continue;
         for (int kind = 3; kind >= 0 && st == RLBM_OK; --kind) {
             st = retile(h, P, kind);

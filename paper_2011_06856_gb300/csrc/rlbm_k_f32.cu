@@ -13,4 +13,9 @@ cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool full, bool site_
         return launch_t<float, float, double>(mode, N, P, two_d, full, grid, block, smem, st, a);
     return launch_t<float, float, float>(mode, N, P, two_d, full, grid, block, smem, st, a);
 }
+cudaError_t launch_lattice_f32(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               const KernelArgs &a)
+{
+    return launch_lattice_t<float, float, float>(two_d, grid, block, smem, st, a);
+}
 } // namespace rlbmk

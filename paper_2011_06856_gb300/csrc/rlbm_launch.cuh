@@ -71,4 +71,20 @@ static cudaError_t launch_t_hi(int mode, int N, int P, bool two_d, bool full, di
     }
 }
 
+// The on-lattice rule (Sec. 2.3): N = 3, 12 stencil vectors per shell, one warp
+// of P = 12 populations per shell, perfect streaming.
+template <class St, class R, class LR>
+static cudaError_t launch_lattice_t(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    const KernelArgs &a)
+{
+    void (*k)(const KernelArgs) = two_d ? rlbm_kernel<St, R, LR, 3, 12, true, MODE_STEP_LATTICE, true>
+                                        : rlbm_kernel<St, R, LR, 3, 12, false, MODE_STEP_LATTICE, true>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 } // namespace rlbmk

@@ -26,7 +26,8 @@ BC_PERIODIC, BC_COPYOUT = 0, 1
 
 # Symbols declared in include/rlbm.h (checked by the CPU test suite).
 EXPORTS = [
-    "rlbm_quadrature", "rlbm_population_bytes", "rlbm_create", "rlbm_destroy",
+    "rlbm_quadrature", "rlbm_population_bytes", "rlbm_create", "rlbm_create_onlattice",
+    "rlbm_is_onlattice", "rlbm_destroy",
     "rlbm_last_error", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
@@ -89,6 +90,11 @@ def lib(path: str = LIB_PATH):
     L.rlbm_create.restype = st
     L.rlbm_create.argtypes = [ctypes.POINTER(_vp), Grid, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                               ctypes.c_int, _vp, _vp, ctypes.c_size_t]
+    L.rlbm_create_onlattice.restype = st
+    L.rlbm_create_onlattice.argtypes = [ctypes.POINTER(_vp), Grid, ctypes.c_double, ctypes.c_int, _vp, _vp,
+                                        ctypes.c_size_t]
+    L.rlbm_is_onlattice.restype = ctypes.c_int
+    L.rlbm_is_onlattice.argtypes = [_vp]
     L.rlbm_destroy.restype = None
     L.rlbm_destroy.argtypes = [_vp]
     L.rlbm_last_error.restype = ctypes.c_char_p
@@ -236,10 +242,17 @@ class Simulation:
 
     def __init__(self, nx: int, ny: int, N: int, K: int, tau: float, precision: str = "fp64",
                  bcx: int = BC_COPYOUT, bcy: int = BC_PERIODIC, stream=None,
-                 own_buffers: bool = False):
+                 own_buffers: bool = False, onlattice: bool = False):
+        """onlattice: the on-lattice rule of Sec. 2.3 (rlbm_create_onlattice;
+        needs N = 3, and K is set to its 12 stencil vectors)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("librlbm needs a CUDA GPU")
+        if onlattice:
+            if int(N) != 3:
+                raise ValueError("the on-lattice rule has order N = 3")
+            K = 12
+        self.onlattice = bool(onlattice)
         self.nx, self.ny, self.N, self.K = int(nx), int(ny), int(N), int(K)
         self.npop = self.K * (self.N + 1)
         self.precision = precision
@@ -253,9 +266,13 @@ class Simulation:
             self._buf = torch.empty(2 * self.pop_bytes, dtype=torch.uint8, device="cuda")
             ptr, nbytes = self._buf.data_ptr(), 2 * self.pop_bytes
         h = _vp()
-        status = lib().rlbm_create(ctypes.byref(h), grid, self.N, self.K, self.tau,
-                                   PRECISIONS[precision], _vp(self.stream.cuda_stream), _vp(ptr),
-                                   nbytes)
+        if onlattice:
+            status = lib().rlbm_create_onlattice(ctypes.byref(h), grid, self.tau, PRECISIONS[precision],
+                                                 _vp(self.stream.cuda_stream), _vp(ptr), nbytes)
+        else:
+            status = lib().rlbm_create(ctypes.byref(h), grid, self.N, self.K, self.tau,
+                                       PRECISIONS[precision], _vp(self.stream.cuda_stream), _vp(ptr),
+                                       nbytes)
         _check(status, None)
         self._h = h
 

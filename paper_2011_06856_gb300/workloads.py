@@ -109,9 +109,10 @@ def random_populations(npop: int, ny: int, nx: int, seed: int, lo=0.05, hi=1.0) 
     return np.random.default_rng(seed).uniform(lo, hi, (npop, ny, nx))
 
 
-def tau_from_kn(kn: float, L: int) -> float:
-    """Kn = c tau / L (Sec. 3.1) with c = 1 in lattice units."""
-    return math.inf if math.isinf(kn) else kn * L
+def tau_from_kn(kn: float, L: int, c: float = 1.0) -> float:
+    """Kn = c tau / L (Sec. 3.1); c = 1 cell per step off lattice, 5 cells per
+    step for the on-lattice rule (stencil vectors of length 5)."""
+    return math.inf if math.isinf(kn) else kn * L / c
 
 
 # --------------------------------------------------------------------------
@@ -179,7 +180,18 @@ WORKLOADS = {
                                   BC_COPYOUT, BC_COPYOUT, {"states": PAPER_SOD2D_STATES}),
     "sod2d_1000sq_N3K600": Workload("sod2d_1000sq_N3K600", 1000, 1000, 3, 600, (0.1,), 450, "fp32",
                                     BC_COPYOUT, BC_COPYOUT, {"states": PAPER_SOD2D_STATES}),
+    # the on-lattice rule of Sec. 2.3 (N = 3, 12 stencil vectors of length 5, N_pop = 48, perfect
+    # streaming at 5 cells per step) on the paper's 2D problem: t = 0.9 t_max, t_max = L/10 steps;
+    # tau = Kn L / 5, so the hydrodynamic end is Kn = 0.02 (tau = 4; Kn = 0.002 would over-relax)
+    "onlattice2d_1000sq_N3": Workload("onlattice2d_1000sq_N3", 1000, 1000, 3, 12, (0.02, 0.1, 100.0), 90,
+                                      "fp32", BC_COPYOUT, BC_COPYOUT,
+                                      {"states": PAPER_SOD2D_STATES, "onlattice": True}),
 }
+
+
+def light_speed(w: Workload) -> float:
+    """Cells per time step a massless particle moves (5 for the on-lattice rule)."""
+    return 5.0 if w.extra.get("onlattice") else 1.0
 
 SHOCK_LEFT = (1.0, 1.0)
 SHOCK_RIGHT = (0.2, 0.5)
