@@ -183,9 +183,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_baseline_statistics(w: W.Workload, kn_list, budget_s: float = 12.0):
+    """The quantum-statistics oracle (Python, one site at a time) on a bounded
+    sample: a strip of 8 sites of the workload's first row, time steps until the
+    budget is spent."""
+    import oracle as O
+    from oracle import statistics as S
+    kind, g = W.statistics(w)
+    eps = {"fd": S.FD, "be": S.BE}[kind]
+    q = O.Quadrature(w.N, w.K)
+    fl = W.workload_fields(w)
+    sl = (slice(0, 1), slice(0, 8))
+    f = S.init(q, fl.n[sl], fl.T[sl], fl.bx[sl], fl.by[sl], eps, g)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        f = S.run(q, f, W.tau_from_kn(kn_list[steps % len(kn_list)], w.nx), 1, w.bcx, w.bcy, eps, g)
+        steps += 1
+    dt = time.perf_counter() - t0
+    updates = 8 * w.npop * steps
+    return {"value": updates / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"8 sites of {w.nx}x{w.ny} N={w.N} K={w.K}, {kind} statistic, {steps} time steps "
+                      f"({updates:.3e} updates, {dt:.1f} s, FP64, Python per site)"}
+
+
 def cpu_baseline(w: W.Workload, kn_list, budget_s: float = 12.0):
     """Time the FP64 oracle (as it stands) on the host cores on a bounded sample:
     the full grid and quadrature of the workload, a few time steps per Kn."""
+    if W.statistics(w)[0] != "mj":
+        return cpu_baseline_statistics(w, kn_list, budget_s)
     import oracle as O
     q = O.Quadrature(w.N, w.K, onlattice=bool(w.extra.get("onlattice")))
     fl = W.workload_fields(w)
@@ -211,6 +237,16 @@ def run_reference(args, w: W.Workload, precision: str):
         return
     kn_list = list(w.kn)
     cb = cpu_baseline(w, kn_list, budget_s=8.0)
+    if W.statistics(w)[0] != "mj":  # the Python statistics oracle: the baseline's sample is the timed work
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC,
+                "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K, "npop": w.npop,
+                           "kn": kn_json(kn_list), "precision": "fp64", "device": "host (oracle)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     # timed steps: each a bounded sample of the workload
     import oracle as O
     q = O.Quadrature(w.N, w.K, onlattice=bool(w.extra.get("onlattice")))
@@ -432,8 +468,11 @@ def main():
     outs = [torch.empty((6, w.ny, w.nx), dtype=torch.float64, device=dev) for _ in kn_list]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     # tiling chosen by the library's autotuner (cached per problem shape)
+    kind, gdeg = W.statistics(w)
     with torch.cuda.stream(stream):
         for sim in sims:
+            if kind != "mj":
+                sim.set_statistics(kind, gdeg)
             sim.init_device(*d_fields)
             if args.kernel:
                 sim.set_tiling(args.tile_p or sim.tile_populations, args.kernel)
@@ -445,6 +484,8 @@ def main():
                     "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
 
     def kernel_name(sim):
+        if sim.statistics != "mj":
+            return "rlbm_kernel<MODE_STEP | MODE_Q>"
         if sim.onlattice:
             return "rlbm_kernel<MODE_STEP_LATTICE>"
         if sim.population_groups > 1:
@@ -542,6 +583,8 @@ def main():
             "config": {"workload": w.name, "grid": [w.nx, w.ny], "N": w.N, "K": w.K,
                        "quadrature": "on-lattice, stencil vectors of length 5" if w.extra.get("onlattice")
                        else "off-lattice product rule",
+                       "statistics": {"mj": "Maxwell-Juttner", "fd": "Fermi-Dirac", "be": "Bose-Einstein"}[kind]
+                       + ("" if kind == "mj" else f", g = {gdeg}"),
                        "npop": w.npop, "kn": kn_json(kn_list), "time_steps_per_problem": steps_pp,
                        "problems_per_step": len(kn_list), "precision": precision,
                        "bc": ["copy-out" if w.bcx else "periodic", "copy-out" if w.bcy else "periodic"],

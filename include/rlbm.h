@@ -123,6 +123,30 @@ rlbm_status rlbm_create_onlattice(rlbm_t **out, rlbm_grid grid, double tau, int 
 /* 1 if the handle uses the on-lattice rule, 0 if the off-lattice one, -1 for NULL. */
 int rlbm_is_onlattice(const rlbm_t *h);
 
+/* Equilibrium statistic of Eq. (feq_dist), f^eq = g / (z^-1 exp(U.p/T) + s):
+ * statistics s = 0 Maxwell-Juttner (the default; g unused), +1 Fermi-Dirac,
+ * -1 Bose-Einstein (Sec. 2.1: the quadratures apply unchanged).  For s != 0 the
+ * Landau frame gives n and the energy density e, and the per-site step solves
+ * n = 2 pi g T^2 phi_2(z), e = 4 pi g T^3 phi_3(z) for (T, z) (phi_s = -Li_s(-z)
+ * or Li_s(z)); the projection weights of the truncated equilibrium use the
+ * radial moments 2 pi g T^(k+1) phi_{k+1}(z).  rlbm_init takes (n, T) and finds z
+ * from n; rlbm_moments reports this T.  A Bose-Einstein state beyond
+ * condensation (no z < 1) is RLBM_ERR_UNPHYSICAL, as a failed Landau frame.
+ * Needs g > 0 (RLBM_ERR_ARG); FP64 or FP32 storage, N = 2 or 3 and the
+ * off-lattice rule (RLBM_ERR_UNSUPPORTED otherwise).  The per-site part runs in
+ * FP64 and the per-tile kernel is used.  Synchronises the stream; the stored
+ * populations are kept (call rlbm_init afterwards to start from an equilibrium
+ * of the new statistic). */
+rlbm_status rlbm_set_statistics(rlbm_t *h, int statistics, double g);
+
+/* The handle's statistic (0, 1, -1), or -2 for NULL. */
+int rlbm_statistics(const rlbm_t *h);
+
+/* Host evaluation of the routine the kernels use for the quantum statistics:
+ * phi_s(z) at eta = ln z, s = 0..6, statistics +1 (-Li_s(-z)) or -1 (Li_s(z),
+ * eta < 0).  NaN for arguments outside that range.  No GPU needed. */
+double rlbm_quantum_phi(int s, double eta, int statistics);
+
 void rlbm_destroy(rlbm_t *h);
 
 /* Message of the most recent failure on h (or of the last failed create when

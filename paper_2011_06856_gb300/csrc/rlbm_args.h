@@ -9,7 +9,8 @@ namespace rlbmk {
 
 // MODE_STEP_LATTICE: a step of the on-lattice rule (perfect streaming by the
 // integer stencil vector of each population, no interpolation).
-enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_MOMENTS = 2, MODE_STEP_LATTICE = 3 };
+// MODE_Q (a bit added to STEP, INIT, MOMENTS): the quantum statistics.
+enum Mode { MODE_STEP = 0, MODE_INIT = 1, MODE_MOMENTS = 2, MODE_STEP_LATTICE = 3, MODE_Q = 4 };
 
 constexpr int kMaxN = 5;
 constexpr int kMaxWarps = 16;
@@ -25,6 +26,8 @@ struct KernelArgs {
     int R;          // groups of P populations per warp (many angles); 0 or 1: one group
     int bcx, bcy;   // 0 periodic, 1 copy-out
     int collide;    // 0 for tau = +inf (free streaming)
+    int stat;       // equilibrium statistic: 0 Maxwell-Juttner, +1 Fermi-Dirac, -1 Bose-Einstein
+    double gdeg;    // normalisation g of f^eq = g / (z^-1 exp(U.p/T) + stat) (quantum statistics)
     double inv_tau;
     double beta;    // stored-unit offset: f = alpha (s + beta)
     double feq_off; // beta / (w_i / alpha_i): subtracted from the m = 0 coefficient
@@ -129,6 +132,12 @@ cudaError_t launch_lattice_f64(bool two_d, dim3 grid, dim3 block, size_t smem, c
                                const KernelArgs &a);
 cudaError_t launch_lattice_f32(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                const KernelArgs &a);
+// The per-tile kernel with a quantum statistic (N = 2, 3; FP64 per-site arithmetic), FP64 and
+// FP32 storage; mode is MODE_STEP, MODE_INIT or MODE_MOMENTS.
+cudaError_t launch_quant_f64(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_quant_f32(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t st, const KernelArgs &a);
 // The same per-tile kernel for N = 4, 5, with FP64 per-site arithmetic in every storage type.
 cudaError_t launch_f64_n45(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                            size_t smem, cudaStream_t st, const KernelArgs &a);

@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include "rlbm_args.h"
+#include "rlbm_stat.cuh"
 
 namespace rlbmk {
 
@@ -301,9 +302,12 @@ __device__ __forceinline__ bool landau_fast(const LR *m, LR &n, LR &eps, LR &U0,
 //   C_{r,m} = sum_k R'[r][m][k] n T^(k-1) acc_{m,k},  acc = sum_j q0^(k-m) z^m.
 // This returns the coefficients of one energy shell r in stored units:
 // cr[0] = Re C_{r,0} - feq_off, cr[2m-1], cr[2m] = Re, Im C_{r,m}.
+// shell_coefficients_tk takes the radial weights tk[k] as given (n T^(k-1) for
+// Maxwell-Juttner, 2 pi g T^(k+1) phi_{k+1}(z) for the quantum statistics,
+// rlbm_stat.cuh); shell_coefficients forms the Maxwell-Juttner ones.
 template <int N, class LR, class R>
-__device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, LR n, LR T, LR U0,
-                                                   LR Ux, LR Uy, R *cr)
+__device__ __forceinline__ void shell_coefficients_tk(const KernelArgs &a, int r, const LR *tk, LR U0,
+                                                      LR Ux, LR Uy, R *cr)
 {
     LR accr[N + 1][N + 1], acci[N + 1][N + 1];
 #pragma unroll
@@ -336,10 +340,6 @@ __device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, L
                 acci[m][k] += qp[k - m] * pi[m];
             }
     }
-    LR tk[N + 1];
-    tk[0] = n / T;
-#pragma unroll
-    for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
     const LR *rt = reinterpret_cast<const LR *>(a.rtab) + r * (N + 1) * (N + 1);
 #pragma unroll
     for (int m = 0; m <= N; ++m) {
@@ -359,13 +359,29 @@ __device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, L
     }
 }
 
+template <int N, class LR, class R>
+__device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, LR n, LR T, LR U0,
+                                                   LR Ux, LR Uy, R *cr)
+{
+    LR tk[N + 1];
+    tk[0] = n / T;
+#pragma unroll
+    for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
+    shell_coefficients_tk<N, LR, R>(a, r, tk, U0, Ux, Uy, cr);
+}
+
 // St: storage type; R: per-population arithmetic; LR: per-site arithmetic
 // (moment sums, Landau frame, equilibrium coefficients); N: quadrature order;
 // P: populations per thread (compile-time upper bound); TWO_D: ny > 1;
 // FULL: every warp owns exactly P populations (no per-population guard).
-template <class St, class R, class LR, int N, int P, bool TWO_D, int MODE, bool FULL>
+// MODEQ: a Mode, with the bit MODE_Q for the quantum statistics (Fermi-Dirac or
+// Bose-Einstein per a.stat; FP64 per-site arithmetic only).
+template <class St, class R, class LR, int N, int P, bool TWO_D, int MODEQ, bool FULL>
 __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a)
 {
+    constexpr int MODE = MODEQ & ~MODE_Q;
+    constexpr bool QUANT = (MODEQ & MODE_Q) != 0;
+    static_assert(!QUANT || sizeof(LR) == 8, "quantum statistics: FP64 per-site arithmetic");
     constexpr int NC = 2 * N + 1;
     constexpr int TW = tab_width(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -497,6 +513,30 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         T = eps / (LR(2) * n);
         if (!ok && act && g == 0) atomicOr(a.status, 1);
     }
+    // quantum statistics: (T, z) of the equilibrium with these (n, eps), or z of (n, T) at init.
+    // Warp 0 solves for its 32 sites and passes (eta, T) on through shared memory
+    // (after the angular sums: qsh = [2][32] doubles); in the moments pass only warp 0 runs.
+    LR tkq[N + 1];
+    if constexpr (QUANT) {
+        double qeta = 0.0, qT = T;
+        double *qsh = reinterpret_cast<double *>(smem_raw + size_t(5) * G * 32 * sizeof(LR));
+        if (g == 0) {
+            const bool ok = (MODE == MODE_INIT) ? stat_fugacity(n, T, a.gdeg, a.stat, qeta)
+                                                : stat_solve(n, eps, a.gdeg, a.stat, qeta, qT);
+            if (!ok && act) atomicOr(a.status, 1);
+            if (MODE != MODE_MOMENTS) {
+                qsh[lane] = qeta;
+                qsh[32 + lane] = qT;
+            }
+        }
+        if (MODE != MODE_MOMENTS) {
+            __syncthreads();
+            qeta = qsh[lane];
+            qT = qsh[32 + lane];
+        }
+        T = qT;
+        stat_radial<N>(T, qeta, a.gdeg, a.stat, tkq);
+    }
     if (MODE == MODE_MOMENTS) {
         if (act) {
             a.out[0][site] = double(n);
@@ -509,7 +549,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         return;
     }
     R cr[NC];
-    shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
+    if constexpr (QUANT)
+        shell_coefficients_tk<N, LR, R>(a, r, tkq, U0, Ux, Uy, cr);
+    else
+        shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
     const LR itau = Par<LR>::inv_tau(a);
     const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
     constexpr bool kSR = (sizeof(St) == 2) && STEP;

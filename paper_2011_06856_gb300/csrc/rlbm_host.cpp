@@ -7,6 +7,7 @@
 // steps on L_{N+1}; weights use the closed form printed in Sec. 2.3.
 #include "rlbm.h"
 #include "rlbm_args.h"
+#include "rlbm_stat.cuh"
 
 #include <cmath>
 #include <cstdarg>
@@ -247,6 +248,8 @@ struct rlbm {
     rlbmk::KernelArgs base{};
     int P = 0, Gs = 0, G = 0;
     int R = 1; // groups of P populations per warp (K beyond one group per warp)
+    int stat = 0;       // equilibrium statistic: 0 Maxwell-Juttner, +1 Fermi-Dirac, -1 Bose-Einstein
+    double gdeg = 1.0;  // normalisation g of the quantum statistics
     bool site_fp64 = false;
     // CUDA graphs of kGraphSteps steps starting from buffer 0 / buffer 1
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -503,6 +506,8 @@ rlbm_status build_tables(rlbm_t *h)
     a.bcx = h->grid.bc_x;
     a.bcy = h->grid.bc_y;
     a.collide = std::isinf(h->tau) ? 0 : 1;
+    a.stat = h->stat;
+    a.gdeg = h->gdeg;
     a.inv_tau = std::isinf(h->tau) ? 0.0 : 1.0 / h->tau;
     a.beta = beta;
     a.inv_tau_f = float(a.inv_tau);
@@ -537,7 +542,8 @@ void *buffer(rlbm_t *h, int which) { return (unsigned char *)h->buf + size_t(whi
 size_t smem_bytes(const rlbm_t *h)
 {
     const size_t ls = (h->prec == RLBM_FP64 || h->site_fp64) ? 8 : 4;
-    return ls * 5 * size_t(h->G) * 32;
+    // angular sums [5][G][32]; quantum statistics: (eta, T) of the 32 sites after them
+    return ls * 5 * size_t(h->G) * 32 + (h->stat ? 2 * 32 * sizeof(double) : 0);
 }
 
 cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
@@ -548,6 +554,13 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     const bool two_d = h->grid.ny > 1;
     const bool full = h->K == h->R * h->Gs * h->P;
     cudaError_t e;
+    if (h->stat) { // quantum statistics (FP64 per-site part; rlbm_set_statistics checks the rest)
+        e = h->prec == RLBM_FP64
+                ? rlbmk::launch_quant_f64(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a)
+                : rlbmk::launch_quant_f32(mode, h->N, h->P, two_d, full, grid, block, smem, h->stream, a);
+        if (e == cudaSuccess) ++h->launches;
+        return e;
+    }
     if (mode == rlbmk::MODE_STEP && h->q.onlat) { // perfect streaming (FP32/FP64, P = 12: create, set_tiling)
         e = h->prec == RLBM_FP64 ? rlbmk::launch_lattice_f64(two_d, grid, block, smem, h->stream, a)
                                  : rlbmk::launch_lattice_f32(two_d, grid, block, smem, h->stream, a);
@@ -573,7 +586,8 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
 // to FP32 storage only.
 bool pair_possible(const rlbm_t *h, int P)
 {
-    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3 || h->q.onlat) return false;
+    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3 || h->q.onlat || h->stat)
+        return false;
     if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
     if (!(P == 8 || P == 12 || P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
     int gs = 0, ng = 0;
@@ -664,7 +678,7 @@ rlbm_status setup_tma(rlbm_t *h)
     delete[] h->tma;
     h->tma = nullptr;
     const char *off = std::getenv("RLBM_NO_TMA");
-    if ((off && off[0] == '1') || h->no_tma || h->N > 3 || h->R > 1 || h->q.onlat) return RLBM_OK;
+    if ((off && off[0] == '1') || h->no_tma || h->N > 3 || h->R > 1 || h->q.onlat || h->stat) return RLBM_OK;
     const size_t es = storage_size(h->prec);
     const int HX = int(16 / es), BW = 32 + 2 * HX;
     const int nx = h->grid.nx, ny = h->grid.ny, npop = h->npop;
@@ -966,6 +980,35 @@ rlbm_status rlbm_create_onlattice(rlbm_t **out, rlbm_grid grid, double tau, int 
 
 int rlbm_is_onlattice(const rlbm_t *h) { return h ? (h->q.onlat ? 1 : 0) : -1; }
 
+rlbm_status rlbm_set_statistics(rlbm_t *h, int statistics, double g)
+{
+    if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
+    if (statistics < -1 || statistics > 1) return fail(h, RLBM_ERR_ARG, "statistics must be 0, 1 or -1");
+    if (statistics != 0 && !(g > 0.0 && std::isfinite(g))) return fail(h, RLBM_ERR_ARG, "g must be > 0");
+    if (statistics != 0) {
+        if (h->prec != RLBM_FP64 && h->prec != RLBM_FP32)
+            return fail(h, RLBM_ERR_UNSUPPORTED, "quantum statistics are built for FP64 and FP32 storage");
+        if (h->N > 3) return fail(h, RLBM_ERR_UNSUPPORTED, "quantum statistics are built for N = 2, 3");
+        if (h->q.onlat) return fail(h, RLBM_ERR_UNSUPPORTED, "quantum statistics use the off-lattice rule");
+    }
+    h->stat = statistics;
+    h->gdeg = statistics != 0 ? g : 1.0;
+    // the quantum per-site part runs in FP64 (FP32 storage: FP64 site tables)
+    const char *env = std::getenv("RLBM_FP32_SITE_FP64");
+    h->site_fp64 = (h->prec != RLBM_FP64) &&
+                   (statistics != 0 || h->N >= 4 || ((h->prec == RLBM_FP32) && env && env[0] == '1'));
+    return retile(h, h->P, 0);
+}
+
+int rlbm_statistics(const rlbm_t *h) { return h ? h->stat : -2; }
+
+double rlbm_quantum_phi(int s, double eta, int statistics)
+{
+    if (s < 0 || s > 6 || (statistics != 1 && statistics != -1) || (statistics < 0 && !(eta < 0.0)))
+        return std::nan("");
+    return rlbmk::stat_phi(s, eta, statistics);
+}
+
 void rlbm_destroy(rlbm_t *h)
 {
     if (!h) return;
@@ -1174,7 +1217,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
     if (launches_per_trial < 1) return fail(h, RLBM_ERR_ARG, "launches_per_trial must be >= 1");
     const TuneKey key{h->grid.nx, h->grid.ny, h->N, h->K, h->prec, h->grid.bc_x, h->grid.bc_y,
-                      (h->site_fp64 ? 1 : 0) | (h->q.onlat ? 2 : 0)};
+                      (h->site_fp64 ? 1 : 0) | (h->q.onlat ? 2 : 0) | (h->stat ? (h->stat > 0 ? 4 : 8) : 0)};
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = tune_cache().find(key);

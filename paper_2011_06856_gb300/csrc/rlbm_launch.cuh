@@ -6,22 +6,23 @@
 
 namespace rlbmk {
 
-template <class St, class R, class LR, int N, int P>
+// QB: 0, or MODE_Q for the quantum statistics.
+template <class St, class R, class LR, int N, int P, int QB = 0>
 static cudaError_t launch_np(int mode, bool two_d, bool full, dim3 grid, dim3 block, size_t smem,
                             cudaStream_t st, const KernelArgs &a)
 {
     void (*k)(const KernelArgs);
     if (mode == MODE_STEP) {
         if (full)
-            k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP, true>
-                      : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP, true>;
+            k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP | QB, true>
+                      : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP | QB, true>;
         else
-            k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP, false>
-                      : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP, false>;
+            k = two_d ? rlbm_kernel<St, R, LR, N, P, true, MODE_STEP | QB, false>
+                      : rlbm_kernel<St, R, LR, N, P, false, MODE_STEP | QB, false>;
     } else if (mode == MODE_INIT) {
-        k = rlbm_kernel<St, R, LR, N, P, false, MODE_INIT, false>;
+        k = rlbm_kernel<St, R, LR, N, P, false, MODE_INIT | QB, false>;
     } else {
-        k = rlbm_kernel<St, R, LR, N, P, false, MODE_MOMENTS, false>;
+        k = rlbm_kernel<St, R, LR, N, P, false, MODE_MOMENTS | QB, false>;
     }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -32,18 +33,18 @@ static cudaError_t launch_np(int mode, bool two_d, bool full, dim3 grid, dim3 bl
     return cudaGetLastError();
 }
 
-template <class St, class R, class LR, int N>
+template <class St, class R, class LR, int N, int QB = 0>
 static cudaError_t launch_n(int mode, int P, bool two_d, bool full, dim3 grid, dim3 block,
                            size_t smem, cudaStream_t st, const KernelArgs &a)
 {
     switch (P) {
-    case 8: return launch_np<St, R, LR, N, 8>(mode, two_d, full, grid, block, smem, st, a);
-    case 12: return launch_np<St, R, LR, N, 12>(mode, two_d, full, grid, block, smem, st, a);
-    case 16: return launch_np<St, R, LR, N, 16>(mode, two_d, full, grid, block, smem, st, a);
-    case 24: return launch_np<St, R, LR, N, 24>(mode, two_d, full, grid, block, smem, st, a);
-    case 32: return launch_np<St, R, LR, N, 32>(mode, two_d, full, grid, block, smem, st, a);
-    case 48: return launch_np<St, R, LR, N, 48>(mode, two_d, full, grid, block, smem, st, a);
-    case 64: return launch_np<St, R, LR, N, 64>(mode, two_d, full, grid, block, smem, st, a);
+    case 8: return launch_np<St, R, LR, N, 8, QB>(mode, two_d, full, grid, block, smem, st, a);
+    case 12: return launch_np<St, R, LR, N, 12, QB>(mode, two_d, full, grid, block, smem, st, a);
+    case 16: return launch_np<St, R, LR, N, 16, QB>(mode, two_d, full, grid, block, smem, st, a);
+    case 24: return launch_np<St, R, LR, N, 24, QB>(mode, two_d, full, grid, block, smem, st, a);
+    case 32: return launch_np<St, R, LR, N, 32, QB>(mode, two_d, full, grid, block, smem, st, a);
+    case 48: return launch_np<St, R, LR, N, 48, QB>(mode, two_d, full, grid, block, smem, st, a);
+    case 64: return launch_np<St, R, LR, N, 64, QB>(mode, two_d, full, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -67,6 +68,18 @@ static cudaError_t launch_t_hi(int mode, int N, int P, bool two_d, bool full, di
     switch (N) {
     case 4: return launch_n<St, R, LR, 4>(mode, P, two_d, full, grid, block, smem, st, a);
     case 5: return launch_n<St, R, LR, 5>(mode, P, two_d, full, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// The quantum statistics (N = 2, 3).
+template <class St, class R, class LR>
+static cudaError_t launch_tq(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t st, const KernelArgs &a)
+{
+    switch (N) {
+    case 2: return launch_n<St, R, LR, 2, MODE_Q>(mode, P, two_d, full, grid, block, smem, st, a);
+    case 3: return launch_n<St, R, LR, 3, MODE_Q>(mode, P, two_d, full, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
     }
 }

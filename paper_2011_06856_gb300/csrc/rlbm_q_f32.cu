@@ -1,0 +1,9 @@
+// Per-tile step kernel with a quantum statistic (Fermi-Dirac or Bose-Einstein), FP32 storage, FP64 per-site arithmetic.
+#include "rlbm_launch.cuh"
+namespace rlbmk {
+cudaError_t launch_quant_f32(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t st, const KernelArgs &a)
+{
+    return launch_tq<float, float, double>(mode, N, P, two_d, full, grid, block, smem, st, a);
+}
+} // namespace rlbmk

@@ -1,0 +1,173 @@
+// Fermi-Dirac and Bose-Einstein equilibria (Eq. feq_dist with eps = +1, -1),
+// FP64, for the per-site part of the per-tile kernel and for host checks.
+//
+// f^eq = g / (z^-1 exp(U.p / T) + eps).  Its rest-frame radial integrals are
+//   int_0^inf f p^k dp = g T^(k+1) k! phi_{k+1}(z),
+//   phi_s = -Li_s(-z) (Fermi-Dirac),  Li_s(z) (Bose-Einstein, z < 1),
+// so n = 2 pi g T^2 phi_2, e = 4 pi g T^3 phi_3 (massless, 2+1 dimensions) and
+// the projection weights of the truncated equilibrium take
+// 2 pi g T^(k+1) phi_{k+1}(z) where Maxwell-Juttner has n T^(k-1).
+// Everything is a function of eta = ln z; d phi_s / d eta = phi_{s-1}.
+#pragma once
+
+#include <math.h>
+
+// RLBM_HD: small helpers, inlined; RLBM_HDX: the solvers, called (one copy per
+// translation unit instead of one per kernel instance).
+#ifdef __CUDACC__
+#define RLBM_HD __host__ __device__ __forceinline__
+#define RLBM_HDX static __host__ __device__ __noinline__
+#else
+#define RLBM_HD inline
+#define RLBM_HDX static inline
+#endif
+
+namespace rlbmk {
+
+
+RLBM_HD double stat_ipow(double x, int e)
+{
+    double r = 1.0;
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+
+// sum_{j>=1} (-1)^(j+1) x^j / j^s for 0 < x <= 1 (= -Li_s(-x)), by the
+// convergence acceleration of Cohen, Rodriguez Villegas and Zagier (Exp. Math.
+// 9 (2000), Algorithm 1): the terms x^(k+1)/(k+1)^s form a totally monotone
+// sequence, and 24 terms leave an error below 2 (3 + sqrt 8)^-24 ~ 1e-18 of the first.
+RLBM_HDX double stat_alt_series(int s, double x)
+{
+    const int n = 24;
+    double d = stat_ipow(3.0 + sqrt(8.0), n);
+    d = 0.5 * (d + 1.0 / d);
+    double b = -1.0, c = -d, sum = 0.0, xk = x;
+    for (int k = 0; k < n; ++k) {
+        c = b - c;
+        sum += c * (xk / stat_ipow(k + 1.0, s));
+        b = (double(k) + n) * (double(k) - n) * b / ((k + 0.5) * (k + 1.0));
+        xk *= x;
+    }
+    return sum / d;
+}
+
+// Fermi-Dirac F_s(eta) = -Li_s(-e^eta), s >= 1.  eta <= 0: the alternating series
+// at x = e^eta; eta > 0: the inversion identity for integer s,
+//   F_s(eta) = (-1)^(s+1) F_s(-eta) + 2 sum_{j=0}^{s/2} eta_D(2j) eta^(s-2j) / (s-2j)!,
+// with the Dirichlet eta values eta_D(0) = 1/2, eta_D(2) = pi^2/12,
+// eta_D(4) = 7 pi^4/720, eta_D(6) = 31 pi^6/30240.
+RLBM_HDX double stat_fd(int s, double eta)
+{
+    if (s == 0) return 1.0 / (1.0 + exp(-eta)); // d F_1 / d eta
+    if (eta <= 0.0) return stat_alt_series(s, exp(eta));
+    const double pi2 = 9.8696044010893586188; // pi^2
+    const double etaD[4] = {0.5, pi2 / 12.0, 7.0 * pi2 * pi2 / 720.0, 31.0 * pi2 * pi2 * pi2 / 30240.0};
+    double poly = 0.0;
+    for (int j = 0; 2 * j <= s; ++j) {
+        const int m = s - 2 * j;
+        double fact = 1.0;
+        for (int i = 2; i <= m; ++i) fact *= i;
+        poly += etaD[j] * stat_ipow(eta, m) / fact;
+    }
+    const double mirror = stat_alt_series(s, exp(-eta));
+    return ((s & 1) ? mirror : -mirror) + 2.0 * poly;
+}
+
+// Bose-Einstein Li_s(e^eta), eta < 0, s >= 1.  z <= 1/2: the defining series;
+// above, the duplication formula Li_s(z) = 2^(1-s) Li_s(z^2) + F_s(ln z) (from
+// Li_s(z) + Li_s(-z) = 2^(1-s) Li_s(z^2)), applied until z^(2^m) <= 1/2.
+RLBM_HDX double stat_be(int s, double eta)
+{
+    if (s == 0) return 1.0 / (exp(-eta) - 1.0); // d Li_1 / d eta
+    if (s == 1) return -log1p(-exp(eta));
+    double scale = 1.0, acc = 0.0, e = eta;
+    const double half = -0.69314718055994530942; // ln 1/2
+    int guard = 0;
+    while (e > half && guard < 64) {
+        acc += scale * stat_fd(s, e);
+        scale *= stat_ipow(0.5, s - 1);
+        e *= 2.0;
+        ++guard;
+    }
+    const double z = exp(e);
+    double term = z, sum = 0.0;
+    for (int k = 1; k <= 64; ++k) {
+        sum += term / stat_ipow(double(k), s);
+        term *= z;
+    }
+    return acc + scale * sum;
+}
+
+// phi_s(eta) of the statistic (+1 Fermi-Dirac, -1 Bose-Einstein), s = 0..6.
+RLBM_HD double stat_phi(int s, double eta, int stat) { return stat > 0 ? stat_fd(s, eta) : stat_be(s, eta); }
+
+// (eta, T) of the equilibrium with density n and energy density e:
+// ln phi_3 - 3/2 ln phi_2 = ln(e sqrt(2 pi g) / (2 n^1.5)) =: L is decreasing in eta
+// (Maxwell-Boltzmann limit: -eta/2), solved by Newton steps kept inside a
+// bisection bracket (at most 100 iterations).  Returns false for a Bose-Einstein
+// state beyond condensation (no z < 1), or bad input; eta then sits at the bracket end.
+RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, double &T)
+{
+    const double twopi = 6.283185307179586477;
+    if (!(n > 0.0) || !(e > 0.0)) { eta = -30.0; T = 1.0; return false; }
+    const double L = log(e * sqrt(twopi * g) / (2.0 * n * sqrt(n)));
+    double lo = -60.0, hi = stat > 0 ? 700.0 : -1e-13;
+    double x = -2.0 * L; // Maxwell-Boltzmann start
+    if (x <= lo) x = lo + 1.0;
+    if (x >= hi) x = stat > 0 ? hi - 1.0 : -1e-3;
+    bool ok = false;
+    for (int it = 0; it < 100; ++it) {
+        const double p1 = stat_phi(1, x, stat), p2 = stat_phi(2, x, stat), p3 = stat_phi(3, x, stat);
+        const double H = log(p3) - 1.5 * log(p2) - L;
+        if (H > 0.0) lo = x; else hi = x;
+        const double dH = p2 / p3 - 1.5 * p1 / p2;
+        double xn = x - H / dH;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (fabs(xn - x) <= 1e-15 * (1.0 + fabs(x))) { x = xn; ok = true; break; }
+        x = xn;
+        if (hi - lo < 1e-15 * (1.0 + fabs(x))) { ok = true; break; }
+    }
+    if (stat < 0 && !(x < -1e-12)) ok = false; // condensation: no Bose-Einstein equilibrium
+    eta = x;
+    T = sqrt(n / (twopi * g * stat_phi(2, x, stat)));
+    return ok;
+}
+
+// eta of the equilibrium with density n at temperature T: phi_2(eta) = n / (2 pi g T^2).
+RLBM_HDX bool stat_fugacity(double n, double T, double g, int stat, double &eta)
+{
+    const double twopi = 6.283185307179586477;
+    const double target = log(n / (twopi * g * T * T));
+    double lo = -60.0, hi = stat > 0 ? 700.0 : -1e-13;
+    double x = target; // Maxwell-Boltzmann start (phi_2 = z)
+    if (x <= lo) x = lo + 1.0;
+    if (x >= hi) x = stat > 0 ? hi - 1.0 : -1e-3;
+    bool ok = false;
+    for (int it = 0; it < 100; ++it) {
+        const double p1 = stat_phi(1, x, stat), p2 = stat_phi(2, x, stat);
+        const double H = log(p2) - target; // increasing in eta
+        if (H < 0.0) lo = x; else hi = x;
+        double xn = x - H * p2 / p1;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (fabs(xn - x) <= 1e-15 * (1.0 + fabs(x))) { x = xn; ok = true; break; }
+        x = xn;
+        if (hi - lo < 1e-15 * (1.0 + fabs(x))) { ok = true; break; }
+    }
+    if (stat < 0 && !(x < -1e-12)) ok = false;
+    eta = x;
+    return ok;
+}
+
+// Radial weights tk[k] = 2 pi g T^(k+1) phi_{k+1}(eta), k = 0..N.
+template <int N>
+RLBM_HD void stat_radial(double T, double eta, double g, int stat, double *tk)
+{
+    const double twopi = 6.283185307179586477;
+    double Tp = T;
+    for (int k = 0; k <= N; ++k) {
+        tk[k] = twopi * g * Tp * stat_phi(k + 1, eta, stat);
+        Tp *= T;
+    }
+}
+
+} // namespace rlbmk

@@ -27,7 +27,7 @@ BC_PERIODIC, BC_COPYOUT = 0, 1
 # Symbols declared in include/rlbm.h (checked by the CPU test suite).
 EXPORTS = [
     "rlbm_quadrature", "rlbm_population_bytes", "rlbm_create", "rlbm_create_onlattice",
-    "rlbm_is_onlattice", "rlbm_destroy",
+    "rlbm_is_onlattice", "rlbm_set_statistics", "rlbm_statistics", "rlbm_quantum_phi", "rlbm_destroy",
     "rlbm_last_error", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
@@ -95,6 +95,12 @@ def lib(path: str = LIB_PATH):
                                         ctypes.c_size_t]
     L.rlbm_is_onlattice.restype = ctypes.c_int
     L.rlbm_is_onlattice.argtypes = [_vp]
+    L.rlbm_set_statistics.restype = st
+    L.rlbm_set_statistics.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
+    L.rlbm_statistics.restype = ctypes.c_int
+    L.rlbm_statistics.argtypes = [_vp]
+    L.rlbm_quantum_phi.restype = ctypes.c_double
+    L.rlbm_quantum_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
     L.rlbm_destroy.restype = None
     L.rlbm_destroy.argtypes = [_vp]
     L.rlbm_last_error.restype = ctypes.c_char_p
@@ -228,6 +234,13 @@ def quadrature(N: int, K: int):
     out = [np.zeros(n) for _ in range(4)]
     _check(lib().rlbm_quadrature(N, K, *[_dptr(a) for a in out]))
     return tuple(out)
+
+
+def quantum_phi(s: int, z: float, statistics: str) -> float:
+    """phi_s(z) as the kernels evaluate it (rlbm_quantum_phi): -Li_s(-z) for 'fd',
+    Li_s(z) for 'be'; runs on the host."""
+    import math
+    return lib().rlbm_quantum_phi(int(s), math.log(z), {"fd": 1, "be": -1}[statistics])
 
 
 def population_bytes(nx, ny, N, K, precision="fp64", bcx=BC_COPYOUT, bcy=BC_PERIODIC) -> int:
@@ -368,6 +381,19 @@ class Simulation:
     @property
     def tile_populations(self) -> int:
         return lib().rlbm_tile_populations(self._h)
+
+    STATISTICS = {"mj": 0, "fd": 1, "be": -1}
+
+    def set_statistics(self, kind: str, g: float = 1.0):
+        """Equilibrium statistic: 'mj' (Maxwell-Juttner), 'fd' (Fermi-Dirac) or
+        'be' (Bose-Einstein), f^eq = g / (z^-1 exp(U.p/T) + eps); see
+        rlbm_set_statistics."""
+        _check(lib().rlbm_set_statistics(self._h, self.STATISTICS[kind], float(g)), self._h)
+
+    @property
+    def statistics(self) -> str:
+        v = lib().rlbm_statistics(self._h)
+        return {0: "mj", 1: "fd", -1: "be"}[v]
 
     @property
     def population_groups(self) -> int:

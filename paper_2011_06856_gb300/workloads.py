@@ -186,7 +186,17 @@ WORKLOADS = {
     "onlattice2d_1000sq_N3": Workload("onlattice2d_1000sq_N3", 1000, 1000, 3, 12, (0.02, 0.1, 100.0), 90,
                                       "fp32", BC_COPYOUT, BC_COPYOUT,
                                       {"states": PAPER_SOD2D_STATES, "onlattice": True}),
+    # the Fermi-Dirac statistic (Eq. feq_dist, eps = +1) on the paper's 2D problem; g = 0.1 puts
+    # the fugacity near 1 (between the classical and the degenerate gas)
+    "fermi2d_500sq_N3K12": Workload("fermi2d_500sq_N3K12", 500, 500, 3, 12, (0.1,), 225, "fp32",
+                                    BC_COPYOUT, BC_COPYOUT,
+                                    {"states": PAPER_SOD2D_STATES, "statistics": "fd", "g": 0.1}),
 }
+
+
+def statistics(w: Workload):
+    """(kind, g) of the workload's equilibrium statistic ('mj' unless it names another)."""
+    return w.extra.get("statistics", "mj"), w.extra.get("g", 1.0)
 
 
 def light_speed(w: Workload) -> float:

@@ -127,3 +127,21 @@ def test_batch_arena_and_validation(lib):
     assert lib.rlbm_batch_create(R.ctypes.byref(h), bad, 1, 2, 1, None, None, 0) == R.ERR_ARG
     assert lib.rlbm_batch_create(R.ctypes.byref(h), arr, 2, 2, 2, None, None, 0) == R.ERR_UNSUPPORTED
     assert not h.value
+
+
+def test_quantum_phi_matches_oracle(lib):
+    """The kernels' Fermi-Dirac / Bose-Einstein integrals phi_s (rlbm_stat.cuh,
+    compiled into the host library) against the oracle's integral definition."""
+    from oracle import statistics as S
+    worst = 0.0
+    for s in range(1, 7):
+        for z in (1e-6, 0.02, 0.4, 0.5, 0.6, 0.95, 1.0, 3.0, 80.0, 1e5):
+            for stat in (S.FD, S.BE):
+                if stat == S.BE and z >= 1.0:
+                    continue
+                got = R.quantum_phi(s, z, "fd" if stat == S.FD else "be")
+                ref = S.phi(s, z, stat)
+                worst = max(worst, abs(got - ref) / abs(ref))
+    assert worst < 1e-13, worst
+    assert math.isnan(lib.rlbm_quantum_phi(2, 0.1, -1))  # Bose-Einstein needs z < 1
+    assert math.isnan(lib.rlbm_quantum_phi(9, -0.1, 1))
