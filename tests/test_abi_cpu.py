@@ -145,3 +145,32 @@ def test_quantum_phi_matches_oracle(lib):
     assert worst < 1e-13, worst
     assert math.isnan(lib.rlbm_quantum_phi(2, 0.1, -1))  # Bose-Einstein needs z < 1
     assert math.isnan(lib.rlbm_quantum_phi(9, -0.1, 1))
+
+
+@pytest.mark.parametrize("args,status,needle", [
+    ((R.Grid(8, 1, 0, 0), 6, 16, 1.0, 0), R.ERR_UNSUPPORTED, "N = 2..5"),
+    ((R.Grid(8, 1, 0, 0), 5, 10, 1.0, 0), R.ERR_ARG, "K must be"),
+    ((R.Grid(8, 1, 0, 0), 3, 600, 1.0, 2), R.ERR_UNSUPPORTED, "population groups"),
+    ((R.Grid(8, 1, 0, 0), 2, 400, 1.0, 3), R.ERR_UNSUPPORTED, "population groups"),
+])
+def test_create_refuses_unbuilt_forms_without_touching_the_gpu(lib, args, status, needle):
+    """N > 5, and K beyond one population group per warp in 16-bit storage."""
+    h = R._vp()
+    assert lib.rlbm_create(R.ctypes.byref(h), *args, None, None, 0) == status
+    assert not h.value
+    assert needle in lib.rlbm_last_error(None).decode()
+
+
+def test_onlattice_and_statistics_validation_without_gpu(lib):
+    h = R._vp()
+    for prec in (2, 3, 4, 5):  # the 16-bit forms
+        assert lib.rlbm_create_onlattice(R.ctypes.byref(h), R.Grid(8, 8, 0, 0), 2.0, prec, None, None, 0) \
+            == R.ERR_UNSUPPORTED
+        assert "FP32 and FP64" in lib.rlbm_last_error(None).decode()
+    assert lib.rlbm_create_onlattice(R.ctypes.byref(h), R.Grid(0, 8, 0, 0), 2.0, 0, None, None, 0) == R.ERR_ARG
+    assert lib.rlbm_create_onlattice(R.ctypes.byref(h), R.Grid(8, 8, 0, 0), -1.0, 0, None, None, 0) == R.ERR_ARG
+    assert not h.value
+    assert lib.rlbm_set_statistics(None, 1, 1.0) == R.ERR_ARG
+    assert lib.rlbm_statistics(None) == -2
+    assert lib.rlbm_is_onlattice(None) == -1
+    assert lib.rlbm_population_groups(None) == -1
