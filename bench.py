@@ -129,6 +129,24 @@ def profiled_traffic(workload: str, precision: str, kernel: str, tile_p: int):
     return float(m.group(1))
 
 
+def fp64_roof():
+    """Measured FP64 TFLOP/s from profiles/fp64_dgemm_gb300.md, or the nominal 1.25."""
+    path = os.path.join(ROOT, "profiles", "fp64_dgemm_gb300.md")
+    if os.path.exists(path):
+        m = re.search(r"fp64_tflops:\s*([0-9.]+)", open(path).read())
+        if m:
+            return float(m.group(1)), "measured cuBLAS DGEMM (profiles/fp64_dgemm_gb300.md)"
+    return 1.25, "nominal FP64 rate"
+
+
+def fp64_flops_per_update(N: int, two_d: bool, warps: int, npop: int) -> float:
+    """FP64 FLOPs (FMA = 2) per population update of the per-tile FP64 step:
+    streaming 9 (2D) or 3 (1D), angular sums 9, equilibrium 1 + 4N, omega 4,
+    relaxation 3; plus about 500 per site and warp for the per-site part (every
+    warp repeats it), shared by the site's npop populations."""
+    return (9 if two_d else 3) + 9 + (1 + 4 * N) + 4 + 3 + 500.0 * warps / npop
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -571,6 +589,20 @@ def main():
     e2e_value = upd_per_step * world / e2e_s
     S = w.sites
     working_set = 2 * storage * S * w.npop
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": profiled_traffic(w.name, precision, sims[0].step_kernel, sims[0].tile_populations),
+                "kernel": kernel_name(sims[0]), "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes}
+    if precision == "fp64" and sims[0].step_kernel == "per-tile":
+        # FP64 storage: bound by the FP64 pipe, reported against the measured FP64 rate
+        warps = -(-w.K // sims[0].tile_populations) * (w.N + 1)
+        fpu = fp64_flops_per_update(w.N, w.ny > 1, min(warps, 16), w.npop)
+        tf_peak, tf_src = fp64_roof()
+        tf = w.sites * w.npop / (kernel_ms * 1e-3) * fpu / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": tf_peak, "unit": "TFLOP/s", "frac": tf / tf_peak,
+                    "peak_source": tf_src, "flops_per_update": fpu, "kernel": roofline["kernel"],
+                    "kernel_ms": kernel_ms, "traffic": roofline["traffic"], "hbm": {
+                        k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "alg_bytes_per_launch")}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
@@ -594,12 +626,7 @@ def main():
                        "parallelism": f"replicas x{world} (independent problems)",
                        "concurrency": f"the {len(kn_list)} Kn problems on {len(kn_list)} streams",
                        "tiling": tiling},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": profiled_traffic(w.name, precision, sims[0].step_kernel,
-                                                     sims[0].tile_populations),
-                         "kernel": kernel_name(sims[0]),
-                         "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes},
+            "roofline": roofline,
             "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": METRIC,
                     "h2d_bytes_per_step": 4 * 8 * S * len(kn_list),
