@@ -1,13 +1,19 @@
 #!/usr/bin/env python
 """Benchmark: population updates per second of the fused RLBM step on GB300.
 
-Default workload (one benchmark step): the scaled 1D relativistic shock tube,
-grid 8192 x 4 (copy-out in x, periodic in y), quadrature N = 3 (4 radial
-Gauss-Laguerre nodes) x K = 64 angles = 256 populations per site, run for
-4000 time steps at each Kn in {0.01, 0.1, 1, 10} (tau = Kn * 8192): four
-independent problems, 1.34e11 population updates.  FP32 storage and
-arithmetic.  Inputs are synthetic (piecewise-constant MJ states, u = 0, left
-n = 1, T = 1, right n = 0.2, T = 0.5).
+Default workload (one benchmark step): the 2D Riemann problem on a 2048 x 2048
+grid (copy-out walls), quadrature N = 2 (3 radial Gauss-Laguerre nodes) x
+K = 48 angles = 144 populations per site, Kn = 0.05 (tau = 102.4), 2000 time
+steps: 1.21e12 population updates.  Populations are stored in FP16 relative to
+the rest equilibrium (s = f / f_rest, stochastic rounding), accumulated in
+FP32, with the Landau frame solved in double-float.  The 2.4 GB of
+populations are far above the 129 MB L2, so the step kernel streams from HBM.
+Inputs are synthetic: four quadrant states (n, T) = (1, 1), (0.5, 0.8),
+(0.25, 0.6), (0.5, 0.8), u = 0, each jittered by 1 % from the seed.
+
+The scaled 1D shock tube (8192 x 4, N = 3 x K = 64, four Kn, 4000 steps, FP32)
+is `--workload shock1d_8192x4_N3K64`; its 67 MB working set stays in the L2,
+and its line says so ("bound": "l2").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--precision fp32|fp64|fp16|bf16] [--impl ours|reference]
@@ -39,6 +45,7 @@ from paper_2011_06856_gb300 import workloads as W  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "population-updates/s"
+L2_BYTES = 129e6
 
 
 def kn_json(kn_list):
@@ -52,7 +59,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="shock1d_8192x4_N3K64",
+    ap.add_argument("--workload", default="riemann2d_2048_N2K48",
                     choices=sorted(W.WORKLOADS) + ["batch256", "closure4096"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16", "bf16", "fp16n", "bf16n"])
     ap.add_argument("--timesteps", type=int, default=None,
@@ -105,7 +112,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h", "rlbm_pair.cuh"):
+    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h", "rlbm_pair.cuh", "rlbm_df64.cuh"):
         with open(os.path.join(ROOT, "paper_2011_06856_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -129,22 +136,35 @@ def profiled_traffic(workload: str, precision: str, kernel: str, tile_p: int):
     return float(m.group(1))
 
 
-def fp64_roof():
-    """Measured FP64 TFLOP/s from profiles/fp64_dgemm_gb300.md, or the nominal 1.25."""
-    path = os.path.join(ROOT, "profiles", "fp64_dgemm_gb300.md")
-    if os.path.exists(path):
-        m = re.search(r"fp64_tflops:\s*([0-9.]+)", open(path).read())
-        if m:
-            return float(m.group(1)), "measured cuBLAS DGEMM (profiles/fp64_dgemm_gb300.md)"
-    return 1.25, "nominal FP64 rate"
+def fp64_roof(dev):
+    """The FP64 rate of this GPU, measured here: a cuBLAS DGEMM (torch.matmul of
+    two 4096 x 4096 FP64 matrices, best of 5, CUDA events).  MEASURED_PEAKS.json
+    carries no FP64 figure."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12, "measured here: cuBLAS DGEMM 4096^3, best of 5"
 
 
-def fp64_flops_per_update(N: int, two_d: bool, warps: int, npop: int) -> float:
-    """FP64 FLOPs (FMA = 2) per population update of the per-tile FP64 step:
+def fp64_flops_per_update(N: int, two_d: bool, npop: int) -> float:
+    """FP64 FLOPs (FMA = 2) the method needs per population update in FP64:
     streaming 9 (2D) or 3 (1D), angular sums 9, equilibrium 1 + 4N, omega 4,
-    relaxation 3; plus about 500 per site and warp for the per-site part (every
-    warp repeats it), shared by the site's npop populations."""
-    return (9 if two_d else 3) + 9 + (1 + 4 * N) + 4 + 3 + 500.0 * warps / npop
+    relaxation 3; plus about 500 per site for the per-site part (moment fold,
+    Landau frame, equilibrium coefficients), counted once per site and shared
+    by its npop populations (the per-tile kernel repeats it in every warp:
+    that repetition is not the method's work and is not counted)."""
+    return (9 if two_d else 3) + 9 + (1 + 4 * N) + 4 + 3 + 500.0 / npop
 
 
 class ClockSampler:
@@ -511,17 +531,33 @@ def main():
                     "per-tile": "rlbm_kernel<MODE_STEP> (population groups)"}[sim.step_kernel]
         return kernel_names[sim.step_kernel]
 
-    def one_step():
-        fork = torch.cuda.Event()
+    # the step launches are timed inside the timed region, on the streams they
+    # are issued on: events before and after every problem's run of steps; the
+    # span from the first start to the last end covers all step launches of
+    # the bench step (the problems run concurrently)
+    kspans = []
+
+    def one_step(timed=False):
+        fork = torch.cuda.Event(enable_timing=timed)
         fork.record(stream)
+        marks = []
         for sim, ps, out in zip(sims, pstreams, outs):
             ps.wait_event(fork)
             sim.init_device(*d_fields)
+            if timed:
+                k0 = torch.cuda.Event(enable_timing=True)
+                k1 = torch.cuda.Event(enable_timing=True)
+                k0.record(ps)
             sim.step(steps_pp)
+            if timed:
+                k1.record(ps)
+                marks.append((k0, k1))
             sim.moments_device(out)
             join = torch.cuda.Event()
             join.record(ps)
             stream.wait_event(join)
+        if timed:
+            kspans.append((fork, marks))
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -543,7 +579,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            one_step()
+            one_step(timed=True)
             e1.record(stream)
             ev.append((e0, e1))
         barrier()
@@ -552,19 +588,13 @@ def main():
         launches = sum(s.kernel_launches for s in sims) - l0
         ms = [a.elapsed_time(b) for a, b in ev]
 
-        # dominant kernel alone: a run of step launches timed on its stream
-        sim0 = sims[0]
-        barrier()
-        sim0.init_device(*d_fields)
-        sim0.step(64)
-        k0 = torch.cuda.Event(enable_timing=True)
-        k1 = torch.cuda.Event(enable_timing=True)
-        nk = 1024
-        k0.record(pstreams[0])
-        sim0.step(nk)
-        k1.record(pstreams[0])
-        k1.synchronize()
-        kernel_ms = k0.elapsed_time(k1) / nk
+        # time per step launch over the timed region: the span of the step
+        # launches of every bench step over the launches in it
+        span_ms = 0.0
+        for fork, marks in kspans:
+            span_ms += (max(fork.elapsed_time(k1) for _, k1 in marks) -
+                        min(fork.elapsed_time(k0) for k0, _ in marks))
+        kernel_ms = span_ms / (len(kspans) * steps_pp * len(sims))
 
         # end to end through the public API with host buffers
         host_fields = [np.ascontiguousarray(a) for a in (fl.n, fl.T, fl.bx, fl.by)]
@@ -589,15 +619,21 @@ def main():
     e2e_value = upd_per_step * world / e2e_s
     S = w.sites
     working_set = 2 * storage * S * w.npop
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    l2_resident = working_set < L2_BYTES
+    roofline = {"bound": "l2" if l2_resident else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": profiled_traffic(w.name, precision, sims[0].step_kernel, sims[0].tile_populations),
-                "kernel": kernel_name(sims[0]), "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes}
+                "kernel": kernel_name(sims[0]), "kernel_ms": kernel_ms,
+                "kernel_timing": f"CUDA events around every problem's {steps_pp} steps on its own stream, "
+                                 f"inside each timed step: span of the step launches / launches in it",
+                "alg_bytes_per_launch": alg_bytes}
+    if l2_resident:
+        roofline["note"] = (f"working set {working_set / 1e6:.0f} MB stays in the 129 MB L2 within a step: "
+                            f"frac is the algorithmic rate over the HBM peak, not an HBM measurement")
     if precision == "fp64" and sims[0].step_kernel == "per-tile":
-        # FP64 storage: bound by the FP64 pipe, reported against the measured FP64 rate
-        warps = -(-w.K // sims[0].tile_populations) * (w.N + 1)
-        fpu = fp64_flops_per_update(w.N, w.ny > 1, min(warps, 16), w.npop)
-        tf_peak, tf_src = fp64_roof()
+        # FP64 storage: bound by the FP64 pipe, reported against the FP64 rate measured here
+        fpu = fp64_flops_per_update(w.N, w.ny > 1, w.npop)
+        tf_peak, tf_src = fp64_roof(dev)
         tf = w.sites * w.npop / (kernel_ms * 1e-3) * fpu / 1e12
         roofline = {"bound": "alu", "achieved": tf, "peak": tf_peak, "unit": "TFLOP/s", "frac": tf / tf_peak,
                     "peak_source": tf_src, "flops_per_update": fpu, "kernel": roofline["kernel"],

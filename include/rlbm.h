@@ -58,9 +58,20 @@ typedef enum {
     RLBM_ERR_UNSUPPORTED = 6 /* valid but not built (e.g. an (N, K) with no kernel) */
 } rlbm_status;
 
+/* Storage precision and the arithmetic that goes with it.  The per-site part
+ * of a step is the moment fold (Eq. discrete_sum_moments), the Landau frame
+ * (Sec. 2.2) and the equilibrium coefficients (Eq. mj-feq-expansion-truncated).
+ *  - RLBM_FP64: FP64 throughout.
+ *  - RLBM_FP32: FP32 per-population arithmetic; the per-site part at FP64-class
+ *    accuracy (double-float, pairs of FP32, in the two-sites-per-lane kernels;
+ *    FP64 in the others).  In FP32 it would carry the conserved moments to a
+ *    relative bias of about 4e-7 per step, which the collision accumulates.
+ *  - 16-bit forms: FP32 per-population arithmetic and moment accumulation,
+ *    the Landau frame solved in double-float (the storage rounding, about
+ *    3e-4 over a run, sets their error). */
 typedef enum {
     RLBM_FP64 = 0,      /* FP64 storage and arithmetic */
-    RLBM_FP32 = 1,      /* FP32 storage and arithmetic */
+    RLBM_FP32 = 1,      /* FP32 storage and per-population arithmetic */
     RLBM_FP16_DEV = 2,  /* FP16 s = f / f^rest - 1 (deviation from the rest equilibrium) */
     RLBM_BF16_DEV = 3,  /* BF16 s = f / f^rest - 1 */
     RLBM_FP16_NORM = 4, /* FP16 s = f / f^rest (normalised by the rest equilibrium) */
@@ -207,16 +218,23 @@ long long rlbm_kernel_launches(const rlbm_t *h);
  * nx even, K a multiple of P in {8, 12, 16, 24, 32}, at most 16 warps),
  * 3 = the same with its first pass staged through shared memory by
  * cp.async.bulk on interior tiles (row pitch a multiple of 16 bytes; bounded
- * mbarrier waits), 0 = per-tile kernel. */
+ * mbarrier waits), 4 = the same arithmetic with the whole 64-site tile staged
+ * into shared memory by TMA at the CTA's start (cp.async.bulk.tensor: the
+ * centre row and the upwind pull row of every population, the pull rows in
+ * chunks of 4 or 8 populations that share sgn(v_y); row pitch a multiple of
+ * 16 bytes, nx >= 64 + 32 bytes of halo, one population group; bounded
+ * mbarrier wait; 16-bit stores round stochastically with cvt.rs),
+ * 0 = per-tile kernel. */
 int rlbm_step_kernel_variant(const rlbm_t *h);
 
 /* Select the tiling and step kernel directly (no counterpart in the paper:
  * a performance choice that does not change what a step computes beyond
  * rounding).  P = populations per warp (one of 8, 12, 16, 24, 32, 48, 64 that
  * fits K and N); kind = 0 per-tile, 1 persistent TMA-staged, 2 two sites per
- * lane, 3 two sites per lane with bulk-staged loads.  RLBM_ERR_UNSUPPORTED if
- * the kernel is not possible for this handle (the handle then keeps tiling P
- * with the per-tile kernel); RLBM_ERR_ARG for a kind outside 0..3.
+ * lane, 3 two sites per lane with bulk-staged loads, 4 two sites per lane
+ * with the tile staged by TMA.  RLBM_ERR_UNSUPPORTED if the kernel is not
+ * possible for this handle (the handle then keeps tiling P with the per-tile
+ * kernel); RLBM_ERR_ARG for a kind outside 0..4.
  * Synchronises the stream; the state is kept. */
 rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind);
 
@@ -235,9 +253,9 @@ int rlbm_tile_populations(const rlbm_t *h);
 int rlbm_population_groups(const rlbm_t *h);
 
 /* Autotuner: time every compiled tiling of the step kernel (P populations per
- * warp in {8,12,16,24,32,48,64} that fits K and N, each with the two-sites-
- * per-lane kernel and the persistent TMA-staged kernel where possible and
- * with the per-tile kernel) on this
+ * warp in {8,12,16,24,32,48,64} that fits K and N, each with the four
+ * two-sites-per-lane forms and the persistent TMA-staged kernel where
+ * possible and with the per-tile kernel) on this
  * handle's own problem, launches_per_trial launches each, and keep the
  * fastest.  The populations of the current state are not modified (trials
  * read the current buffer and write the other one).  Results are cached per
@@ -246,8 +264,8 @@ int rlbm_population_groups(const rlbm_t *h);
  * tiling.  Synchronises the stream. */
 rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms);
 
-/* Bound, in SM clock cycles, of every mbarrier wait in the TMA-staged and the
- * bulk-staged step kernels (default 4e9, about 2 s).  A wait that runs out
+/* Bound, in SM clock cycles, of every mbarrier wait in the TMA-staged, the
+ * tile-staged and the bulk-staged step kernels (default 4e9, about 2 s).  A wait that runs out
  * makes the kernel record RLBM_ERR_TIMEOUT, drain its own copies (bounded) and
  * skip its stores; the next synchronising call reports it.  cycles >= 1000. */
 rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles);
@@ -411,7 +429,9 @@ rlbm_status rlbm_closure_set_train_path(rlbm_closure_t *c, int tensor_cores);
 
 /* One fused time step (the same step as rlbm_step) from d_fin to d_fout,
  * caller-owned device buffers of N_pop * nx * ny elements each (FP64 or FP32
- * storage, f[i][y][x]), on cuda_stream (NULL: the default stream).  This entry
+ * storage, f[i][y][x]; the two byte ranges must not overlap, else
+ * RLBM_ERR_ARG), on cuda_stream (NULL: the default stream).  The per-site part
+ * runs in FP64 for both storages, as in a handle's per-tile kernel.  This entry
  * point has no counterpart in the paper: it exists for callers that cannot
  * let a library allocate device memory -- their memory comes from their own
  * pool or framework allocator, or they run under a fixed budget -- so it calls
@@ -422,8 +442,9 @@ rlbm_status rlbm_closure_set_train_path(rlbm_closure_t *c, int tensor_cores);
  * device current, so make the first call on each device before any stream
  * capture.  Limits: N in {2, 3}, K (N+1) <= 256 populations; larger sizes
  * return RLBM_ERR_ARG.  Every call rewrites the array and clears its status
- * word, so calls that overlap on the GPU race: serialise them.  The call
- * synchronises the stream and returns RLBM_ERR_UNPHYSICAL if a cell had no
+ * word, so calls that overlap on the GPU race: serialise them.  Every call
+ * copies the tables in from host memory and synchronises the stream to read
+ * the status word back; it returns RLBM_ERR_UNPHYSICAL if a cell had no
  * physical Landau frame.  rlbm_noalloc_last_error() gives the message of the
  * calling thread's latest failure. */
 rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles_K, double tau, int precision,

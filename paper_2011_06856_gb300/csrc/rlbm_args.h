@@ -37,9 +37,16 @@ struct KernelArgs {
     float inv_tau_f, feq_off_f;
     float off_f[8];
     float smp_cf[kMaxN + 1], smp_sf[kMaxN + 1];
+    // low parts of the double-float forms (value = FP32 copy + low part) of
+    // the scalars above, for the double-float per-site part (rlbm_df64.cuh)
+    float feq_off_l;
+    float off_l[8];
+    float smp_cl[kMaxN + 1], smp_sl[kMaxN + 1];
     const void *poptab;   // npop x tab_width(N), compute type
     const void *shelltab; // (N+1) x 2: alpha_r p_r, alpha_r p_r^2 (site type)
     const void *rtab;     // (N+1)^3 projection weights R'[r][m][k] (site type)
+    const float2 *shell2; // the shell folds as double-floats (hi, lo): (N+1) x 2
+    const float2 *rtab2;  // R'[r][m][k] as double-floats (hi, lo): (N+1)^3
     const double *in_n, *in_T, *in_bx, *in_by; // MODE_INIT fields
     double *out[6];                            // MODE_MOMENTS fields
     const unsigned long long *masks; // per warp: bit k = (v_x >= 0), (v_y >= 0) of its population k (k < 64)
@@ -54,16 +61,18 @@ struct KernelArgs {
 __host__ __device__ constexpr int tab_width(int N) { return ((2 * N + 5) + 3) / 4 * 4; }
 
 // Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory:
-// angular sums [5][G][64] and per-site coefficients [(N+1)(2N+1) + 3][64]
-// (FP32); for the bulk-staged form then, per warp, kPairDepth mbarriers and
-// kPairDepth slots of kPairChunk populations x rows x (64 sites + 16 bytes of
-// halo on each side).
+// angular sums [5][G][64] and the per-site results [2 (N+1)^2 + 3][64] (FP32;
+// the (N+1)^2 shell-independent equilibrium sums as double-floats, hi and lo
+// rows, then U^a / tau); for the bulk-staged form then, per warp, kPairDepth
+// mbarriers and kPairDepth slots of kPairChunk populations x rows x (64 sites
+// + 16 bytes of halo on each side).
 constexpr int kPairSites = 64;
 constexpr int kPairChunk = 4;
 constexpr int kPairDepth = 3;
+__host__ __device__ constexpr int pair_site_rows(int N) { return 2 * (N + 1) * (N + 1) + 3; }
 __host__ __device__ constexpr size_t pair_bars_offset(int N, int G)
 {
-    return ((size_t(5) * G + size_t(N + 1) * (2 * N + 1) + 3) * kPairSites * 4 + 15) / 16 * 16;
+    return ((size_t(5) * G + size_t(pair_site_rows(N))) * kPairSites * 4 + 15) / 16 * 16;
 }
 __host__ __device__ constexpr size_t pair_slots_offset(int N, int G)
 {
@@ -149,16 +158,91 @@ cudaError_t launch_bf16_n45(int mode, int N, int P, bool two_d, bool full, dim3 
                             size_t smem, cudaStream_t st, const KernelArgs &a);
 // Two-sites-per-lane step kernel (rlbm_pair.cuh): 64-site tiles, PP in {8, 12, 16, 24, 32};
 // bulk: interior tiles staged through shared memory by cp.async.bulk.
+// Two-sites-per-lane kernels: one compile unit per storage, order N and form
+// (p plain, b bulk-staged first pass), compiled in parallel; the dispatchers
+// below pick the unit.
 #define RLBM_DECLARE_PAIR(name)                                                                          \
-    cudaError_t launch_pair_##name(int N, int PP, bool two_d, bool bulk, dim3 grid, dim3 block,          \
-                                   size_t smem, cudaStream_t st, const KernelArgs &a);
+    cudaError_t launch_pair_##name##_n2p(int PP, bool two_d, dim3 grid, dim3 block, size_t smem,         \
+                                         cudaStream_t st, const KernelArgs &a);                          \
+    cudaError_t launch_pair_##name##_n2b(int PP, bool two_d, dim3 grid, dim3 block, size_t smem,         \
+                                         cudaStream_t st, const KernelArgs &a);                          \
+    cudaError_t launch_pair_##name##_n3p(int PP, bool two_d, dim3 grid, dim3 block, size_t smem,         \
+                                         cudaStream_t st, const KernelArgs &a);                          \
+    cudaError_t launch_pair_##name##_n3b(int PP, bool two_d, dim3 grid, dim3 block, size_t smem,         \
+                                         cudaStream_t st, const KernelArgs &a);                          \
+    inline cudaError_t launch_pair_##name(int N, int PP, bool two_d, bool bulk, dim3 grid, dim3 block,   \
+                                          size_t smem, cudaStream_t st, const KernelArgs &a)             \
+    {                                                                                                    \
+        if (N == 2)                                                                                      \
+            return bulk ? launch_pair_##name##_n2b(PP, two_d, grid, block, smem, st, a)                  \
+                        : launch_pair_##name##_n2p(PP, two_d, grid, block, smem, st, a);                 \
+        if (N == 3)                                                                                      \
+            return bulk ? launch_pair_##name##_n3b(PP, two_d, grid, block, smem, st, a)                  \
+                        : launch_pair_##name##_n3p(PP, two_d, grid, block, smem, st, a);                 \
+        return cudaErrorInvalidValue;                                                                    \
+    }
 RLBM_DECLARE_PAIR(f32)
 RLBM_DECLARE_PAIR(f16)
 RLBM_DECLARE_PAIR(bf16)
 #undef RLBM_DECLARE_PAIR
-// The same kernel with several population groups per warp (FP32 storage, no staging).
-cudaError_t launch_pair_groups_f32(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,
-                                   cudaStream_t st, const KernelArgs &a);
+// several population groups per warp (FP32 storage)
+cudaError_t launch_pair_groups_f32_n2(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                      const KernelArgs &a);
+cudaError_t launch_pair_groups_f32_n3(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                      const KernelArgs &a);
+inline cudaError_t launch_pair_groups_f32(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,
+                                          cudaStream_t st, const KernelArgs &a)
+{
+    if (N == 2) return launch_pair_groups_f32_n2(PP, two_d, grid, block, smem, st, a);
+    if (N == 3) return launch_pair_groups_f32_n3(PP, two_d, grid, block, smem, st, a);
+    return cudaErrorInvalidValue;
+}
+
+// Arguments of the tile-staged two-sites-per-lane kernel (rlbm_pair_tma.cuh).
+struct alignas(128) PairTmaArgs {
+    CUtensorMap cmap; // 3D map over the input buffer {nx, ny, npop}, box {BW, 1, CB}: centre rows
+    CUtensorMap pmap; // the same map with box {BW, 1, DB}: pull rows
+    KernelArgs a;
+    int CB, ncbox;    // populations per centre box, boxes per tile (CB ncbox = npop)
+    int DB, npbox;    // populations per pull-row chunk, chunks per tile (DB npbox = npop)
+    unsigned long long chunk_up[4]; // bit c: chunk c pulls from row y - 1 (its v_y >= 0), else y + 1
+};
+
+// Shared-memory layout of rlbm_pair_tma_kernel: the staged tile (centre rows,
+// then pull rows in 2D: [rows][npop][BW] storage elements, BW = 64 sites +
+// 16 bytes of halo on each side), the pair table [npop][3] float4, the
+// angular sums [5][G][64], the per-site results [pair_site_rows(N)][64], the
+// mbarrier; + 1 KB of slack to align the base for the TMA.
+struct PairTmaSmem {
+    size_t stage, tab, red, sres, bar, total;
+    __host__ __device__ PairTmaSmem(int N, int G, int npop, int es, bool two_d)
+    {
+        const size_t BW = size_t(kPairSites) + 2 * size_t(16 / es);
+        stage = 0;
+        tab = align_up(size_t(two_d ? 2 : 1) * size_t(npop) * BW * size_t(es), 128);
+        red = align_up(tab + size_t(npop) * 3 * 16, 16);
+        sres = red + size_t(5) * G * kPairSites * 4;
+        bar = align_up(sres + size_t(pair_site_rows(N)) * kPairSites * 4, 16);
+        total = bar + 16 + 1024;
+    }
+};
+
+#define RLBM_DECLARE_PAIR_TMA(name)                                                                      \
+    cudaError_t launch_pair_tma_##name##_n2(int PP, bool two_d, dim3 grid, dim3 block, size_t smem,      \
+                                            cudaStream_t st, const PairTmaArgs &ta);                     \
+    cudaError_t launch_pair_tma_##name##_n3(int PP, bool two_d, dim3 grid, dim3 block, size_t smem,      \
+                                            cudaStream_t st, const PairTmaArgs &ta);                     \
+    inline cudaError_t launch_pair_tma_##name(int N, int PP, bool two_d, dim3 grid, dim3 block,          \
+                                              size_t smem, cudaStream_t st, const PairTmaArgs &ta)       \
+    {                                                                                                    \
+        if (N == 2) return launch_pair_tma_##name##_n2(PP, two_d, grid, block, smem, st, ta);            \
+        if (N == 3) return launch_pair_tma_##name##_n3(PP, two_d, grid, block, smem, st, ta);            \
+        return cudaErrorInvalidValue;                                                                    \
+    }
+RLBM_DECLARE_PAIR_TMA(f32)
+RLBM_DECLARE_PAIR_TMA(f16)
+RLBM_DECLARE_PAIR_TMA(bf16)
+#undef RLBM_DECLARE_PAIR_TMA
 
 // Batched persistent form (rlbm_batch.cuh).
 constexpr int kBatchWarps = 6;
@@ -185,5 +269,7 @@ struct BatchArgs {
 
 cudaError_t launch_batch(int prec, int N, const BatchArgs &b, int grid, cudaStream_t st,
                          int *blocks_per_sm);
+// Advance every problem's launch counter by nsteps (after a batched launch).
+cudaError_t launch_batch_advance(const KernelArgs *probs, int n, int nsteps, cudaStream_t st);
 
 } // namespace rlbmk

@@ -1,4 +1,5 @@
-// Batched persistent kernel instances (FP64 and FP32 storage, N = 2, 3).
+// Batched persistent kernel instances (FP64 and FP32 storage, N = 2, 3; the
+// per-site part in FP64 for both).
 #include "rlbm_batch.cuh"
 
 namespace rlbmk {
@@ -32,10 +33,17 @@ cudaError_t launch_batch(int prec, int N, const BatchArgs &b, int grid, cudaStre
         if (N == 2) return launch_b<double, double, double, 2>(b, grid, st, bps);
         if (N == 3) return launch_b<double, double, double, 3>(b, grid, st, bps);
     } else if (prec == 1) {
-        if (N == 2) return launch_b<float, float, float, 2>(b, grid, st, bps);
-        if (N == 3) return launch_b<float, float, float, 3>(b, grid, st, bps);
+        // FP32 storage: FP32 per-population arithmetic, FP64 per-site part
+        if (N == 2) return launch_b<float, float, double, 2>(b, grid, st, bps);
+        if (N == 3) return launch_b<float, float, double, 3>(b, grid, st, bps);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_advance(const KernelArgs *probs, int n, int nsteps, cudaStream_t st)
+{
+    batch_advance_kernel<<<(n + 255) / 256, 256, 0, st>>>(probs, n, nsteps);
+    return cudaGetLastError();
 }
 
 } // namespace rlbmk

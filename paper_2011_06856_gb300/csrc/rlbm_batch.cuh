@@ -14,7 +14,7 @@
 // bilinear pull from global memory (L2-coherent loads, since the values were
 // written by other CTAs earlier in the same launch), per-warp angular sums,
 // every warp solving the Landau frame and its own shell's equilibrium, and
-// relaxation (Sec. 2.2).
+// relaxation (Sec. 2.2); FP32 stores round stochastically (relax_store).
 #pragma once
 
 #include "rlbm_device.cuh"
@@ -25,7 +25,7 @@ namespace rlbmk {
 template <class St, class R, class LR, int N, bool TWO_D>
 __device__ __forceinline__ void batch_tile(const KernelArgs &a, const St *fin, St *fout, int tile,
                                            int ntiles_x, bool valid, int gw, int G, int lane,
-                                           LR *red)
+                                           LR *red, unsigned seed)
 {
     constexpr int P = 32;
     constexpr int NC = 2 * N + 1;
@@ -93,13 +93,14 @@ __device__ __forceinline__ void batch_tile(const KernelArgs &a, const St *fin, S
     LR m[8];
     fold_moments<N, LR>(a, red, G, lane, m);
     LR n, eps, U0, Ux, Uy;
-    const bool ok = landau_fast<LR>(m, n, eps, U0, Ux, Uy);
+    const bool ok = site_landau<St, LR>(m, n, eps, U0, Ux, Uy);
     const LR T = eps / (LR(2) * n);
     if (!ok && act && gw == 0) atomicOr(a.status, 1);
     R cr[NC];
     shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
     const LR itau = Par<LR>::inv_tau(a);
     const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
+    unsigned rng = mix32(unsigned(y * a.nx + x) * 64u + unsigned(gw) ^ seed);
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         if (k < pc) {
@@ -113,7 +114,7 @@ __device__ __forceinline__ void batch_tile(const KernelArgs &a, const St *fin, S
 #pragma unroll
             for (int t2 = 1; t2 < NC; ++t2) feq += cr[t2] * E[t2];
             const R om = o0 - o1 * c - o2 * s;
-            if (act) Io<St, R>::st(obase + (long long)k * S, fs[k] + om * (feq - fs[k]));
+            if (act) relax_store<St, R>(obase + (long long)k * S, fs[k], om, feq, rng);
         }
     }
     __syncthreads(); // red is reused by the next unit
@@ -179,13 +180,27 @@ __global__ void __launch_bounds__(kBatchWarps * 32) rlbm_batch_kernel(const Batc
             const St *fin = reinterpret_cast<const St *>(par ? a.fout : a.fin);
             St *fout = reinterpret_cast<St *>(par ? const_cast<void *>(a.fin) : a.fout);
             LR *red = red_all + grp * (G * 5 * 32);
+            // stochastic rounding of FP32 stores: seeded by the problem's launch
+            // counter plus the step (the host advances the counters by nsteps after
+            // the launch, batch_advance_kernel)
+            const unsigned seed = mix32((__ldcg(a.ctr) + unsigned(step)) * 0x9E3779B9u + 1u);
             if (a.ny > 1)
-                batch_tile<St, R, LR, N, true>(a, fin, fout, tile, b.ntiles_x[bu.prob], valid, gw, G, lane, red);
+                batch_tile<St, R, LR, N, true>(a, fin, fout, tile, b.ntiles_x[bu.prob], valid, gw, G, lane, red,
+                                               seed);
             else
-                batch_tile<St, R, LR, N, false>(a, fin, fout, tile, b.ntiles_x[bu.prob], valid, gw, G, lane, red);
+                batch_tile<St, R, LR, N, false>(a, fin, fout, tile, b.ntiles_x[bu.prob], valid, gw, G, lane, red,
+                                                seed);
         }
         if (step + 1 < b.nsteps && !batch_grid_barrier(b, step + 1)) return;
     }
+}
+
+// After a launch of nsteps steps: every problem's launch counter (the seed of
+// its stochastic rounding) advances by nsteps, as nsteps single launches would.
+__global__ void batch_advance_kernel(const KernelArgs *probs, int n, int nsteps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) probs[i].ctr[0] += unsigned(nsteps);
 }
 
 } // namespace rlbmk

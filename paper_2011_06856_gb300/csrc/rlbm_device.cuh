@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include "rlbm_args.h"
+#include "rlbm_df64.cuh"
 #include "rlbm_stat.cuh"
 
 namespace rlbmk {
@@ -136,6 +137,47 @@ template <> struct SR<float> {
 template <> struct SR<double> {
     static __device__ __forceinline__ void st(double *p, double v, unsigned &) { *p = v; }
 };
+
+// Stochastic rounding of the FP32 relaxation out = f* + om (f^eq - f*): the
+// FMA's result r (round to nearest) and its exact residual e = f* + om d - r
+// (d = f^eq - f*; f* - r is exact whenever the two are within a factor 2)
+// give the exact value r + e; adding a uniform noise of +-ulp(r)/2 to e
+// before the final rounding r + (e + noise) rounds it up or down with
+// probabilities proportional to the distance -- stochastic rounding.  With
+// round to nearest, FP32 stores repeat the same rounding error step after
+// step wherever the flow changes slowly, and the conserved moments drift
+// (1e-5 after ~3500 steps of the 8192 x 4 shock tube at tau = 82); with it
+// the error only random-walks (3e-7).  u16: 16 random bits.
+__device__ __forceinline__ float ulp_of(float r)
+{
+    return __uint_as_float(__float_as_uint(r) & 0x7f800000u) * 1.1920928955078125e-7f; // 2^-23
+}
+__device__ __forceinline__ float noise16(unsigned u16)
+{
+    return __uint_as_float(0x3f800000u | ((u16 & 0xffffu) << 7)) - 1.5f; // uniform in [-1/2, 1/2)
+}
+__device__ __forceinline__ float relax_sr(float fs, float om, float feq, unsigned u16)
+{
+    const float d = __fsub_rn(feq, fs);
+    const float r = __fmaf_rn(om, d, fs);
+    const float e = __fmaf_rn(om, d, __fsub_rn(fs, r));
+    return __fadd_rn(r, __fmaf_rn(noise16(u16), ulp_of(r), e));
+}
+
+// The relaxation (Eq. discrete-rbe) and its store in storage St: FP64 rounds
+// to nearest; FP32 and the 16-bit forms round stochastically (their random
+// bits from the per-thread stream rng).
+template <class St, class R>
+__device__ __forceinline__ void relax_store(St *p, R fs, R om, R feq, unsigned &rng)
+{
+    if constexpr (sizeof(St) == 8) {
+        *p = fs + om * (feq - fs);
+    } else if constexpr (sizeof(St) == 4) {
+        *p = relax_sr(fs, om, feq, lcg_next(rng) >> 16);
+    } else {
+        SR<St>::st(p, fs + om * (feq - fs), rng);
+    }
+}
 
 // The last CTA of a step launch advances the launch counter that seeds the
 // rounding of the next launch (graph replays keep their parameters fixed).
@@ -286,6 +328,88 @@ __device__ __forceinline__ bool landau_fast(const LR *m, LR &n, LR &eps, LR &U0,
         if (!(eps > LR(0))) eps = E > LR(0) ? E : LR(1e-30);
     }
     return ok;
+}
+
+// The Landau frame in double-float arithmetic (rlbm_df64.cuh), for moments m
+// given as double-floats.  The FP32 root of landau_fast is polished by two
+// Newton steps on the trace-free characteristic cubic whose coefficients c1,
+// c0 are formed in double-float; then the eigenvector (the cross product of
+// the last two rows of A - eps I), its Minkowski norm and n = U_a N^a.  Where
+// T^ab is close to degenerate (a strongly boosted or strongly anisotropic
+// state) the cross product and the norm cancel many digits: the FP32 frame
+// loses them, the double-float one keeps about 48 bits.
+__device__ __forceinline__ bool landau_dd(const df64 *m, df64 &n, df64 &eps, df64 &U0, df64 &Ux, df64 &Uy)
+{
+    float mf[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) mf[u] = to_float(m[u]);
+    float nf, ef, u0f, uxf, uyf;
+    landau_fast<float>(mf, nf, ef, u0f, uxf, uyf);
+    const df64 Nt = m[0], Nx = m[1], Ny = m[2];
+    const df64 E = m[3], Ttx = m[4], Tty = m[5], Txx = m[6], Txy = m[7];
+    const df64 Tyy = E - Txx;
+    const df64 tx2 = Ttx * Ttx, ty2 = Tty * Tty, xy2 = Txy * Txy, xxyy = Txx * Tyy;
+    const df64 c1 = tx2 + ty2 + xxyy - xy2 - E * E;
+    const df64 c0 = E * (xxyy - xy2) - tx2 * Tyy + (Ttx * Tty * Txy) * 2.f - ty2 * Txx;
+    df64 lam = dd(ef);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const df64 P = (lam * lam + c1) * lam - c0;
+        const float dP = __fmaf_rn(3.f * lam.hi, lam.hi, c1.hi);
+        if (!(dP > 0.f)) break;
+        lam = lam - __fdiv_rn(P.hi, dP);
+    }
+    eps = lam;
+    const df64 bx = Txx + lam, by = Tyy + lam;
+    const df64 v0 = bx * by - xy2;
+    const df64 v1 = Ttx * by - Txy * Tty;
+    const df64 v2 = bx * Tty - Ttx * Txy;
+    const df64 mink = v0 * v0 - v1 * v1 - v2 * v2;
+    bool ok = (c1.hi < 0.f) && (v0.hi > 0.f) && (mink.hi > 0.f);
+    if (ok) {
+        const df64 s = dd_rsqrt(mink);
+        U0 = v0 * s;
+        Ux = v1 * s;
+        Uy = v2 * s;
+    } else {
+        U0 = dd(1.f);
+        Ux = dd(0.f);
+        Uy = dd(0.f);
+    }
+    n = U0 * Nt - Ux * Nx - Uy * Ny;
+    if (!(n.hi > 0.f) || !(eps.hi > 0.f)) {
+        ok = false;
+        n = Nt.hi > 0.f ? Nt : dd(1e-30f);
+        if (!(eps.hi > 0.f)) eps = E.hi > 0.f ? E : dd(1e-30f);
+    }
+    return ok;
+}
+
+// FP32 moments in, FP32 frame out, the frame solved in double-float: the form
+// of the kernels that store 16-bit populations and accumulate in FP32.
+__device__ __forceinline__ bool landau_f32dd(const float *m, float &n, float &eps, float &U0, float &Ux, float &Uy)
+{
+    df64 md[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) md[u] = dd(m[u]);
+    df64 nd, ed, u0, ux, uy;
+    const bool ok = landau_dd(md, nd, ed, u0, ux, uy);
+    n = to_float(nd);
+    eps = to_float(ed);
+    U0 = to_float(u0);
+    Ux = to_float(ux);
+    Uy = to_float(uy);
+    return ok;
+}
+
+// The Landau solve of a kernel with storage St and per-site type LR: 16-bit
+// storage with FP32 per-site arithmetic solves the frame in double-float, every
+// other combination in LR itself (FP64, or FP32 where nothing else applies).
+template <class St, class LR>
+__device__ __forceinline__ bool site_landau(const LR *m, LR &n, LR &eps, LR &U0, LR &Ux, LR &Uy)
+{
+    if constexpr (sizeof(St) == 2 && sizeof(LR) == 4) return landau_f32dd(m, n, eps, U0, Ux, Uy);
+    else return landau_fast<LR>(m, n, eps, U0, Ux, Uy);
 }
 
 // Truncated equilibrium (Eqs. mj-feq-expansion, mj-projection-coefficients,
@@ -509,7 +633,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     } else {
         LR m[8];
         fold_moments<N, LR>(a, red, G, lane, m);
-        const bool ok = landau_fast<LR>(m, n, eps, U0, Ux, Uy);
+        const bool ok = site_landau<St, LR>(m, n, eps, U0, Ux, Uy);
         T = eps / (LR(2) * n);
         if (!ok && act && g == 0) atomicOr(a.status, 1);
     }
@@ -555,7 +679,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
     const LR itau = Par<LR>::inv_tau(a);
     const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
-    constexpr bool kSR = (sizeof(St) == 2) && STEP;
+    constexpr bool kSR = (sizeof(St) <= 4) && STEP; // FP32 and 16-bit stores round stochastically
     unsigned rng = 0;
     if (kSR) rng = mix32(unsigned(site) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
 #pragma unroll 1
@@ -582,17 +706,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
             R feq = cr[0] * E[0];
 #pragma unroll
             for (int t2 = 1; t2 < NC; ++t2) feq += cr[t2] * E[t2];
-            R out;
             if (MODE == MODE_INIT) {
-                out = feq;
+                if (act) Io<St, R>::st(obase + (long long)k * S, feq);
             } else {
                 const R om = o0 - o1 * c - o2 * s;
-                out = fs[k] + om * (feq - fs[k]);
-            }
-            if (kSR) {
-                if (act) SR<St>::st(obase + (long long)k * S, out, rng);
-            } else if (act) {
-                Io<St, R>::st(obase + (long long)k * S, out);
+                if (act) relax_store<St, R>(obase + (long long)k * S, fs[k], om, feq, rng);
             }
         }
     }

@@ -215,6 +215,22 @@ bool make_onlattice_quadrature(Quad &q)
 
 // ---------------------------------------------------------------- handle
 
+// FP64 per-site tables (moment folds, projection weights) for the per-tile,
+// TMA-staged and batched kernels of non-FP64 storage, whose per-site part then
+// runs in FP64 (the two-sites-per-lane kernels run it in double-float):
+//  - FP32 storage: an FP32 per-site part carries the conserved moments to a
+//    relative bias of about 4e-7 per step, which the collision accumulates
+//    linearly (1e-5 after a few hundred steps at tau ~ 4);
+//  - N >= 4: the radial projection weights (inverse of a factorial Gram
+//    matrix) cancel too many digits for FP32;
+//  - the quantum statistics: the (T, z) solve.
+// 16-bit storage accumulates in FP32 and solves the Landau frame in
+// double-float (site_landau): its error is set by the storage rounding.
+bool site_fp64_for(int prec, int N, int stat)
+{
+    return prec != RLBM_FP64 && (prec == RLBM_FP32 || N >= 4 || stat != 0);
+}
+
 size_t storage_size(int prec)
 {
     switch (prec) {
@@ -263,6 +279,9 @@ struct rlbm {
     bool no_tma = false;     // tiling choice: per-tile kernel even where TMA is possible
     bool use_pair = false;   // two-sites-per-lane step kernel (rlbm_pair.cuh)
     bool pair_bulk = false;  // ... with its first pass staged by cp.async.bulk on interior tiles
+    bool use_pair_tma = false;          // ... with the whole tile staged by TMA (rlbm_pair_tma.cuh)
+    rlbmk::PairTmaArgs *ptma = nullptr; // [2]: input buffer 0 / 1
+    size_t ptma_smem = 0;
     long long wait_cycles = 4000000000LL; // bound of the device waits (about 2 s at the maximum clock)
     std::string err;
 };
@@ -466,7 +485,21 @@ rlbm_status build_tables(rlbm_t *h)
             for (int u = 0; u < 12; ++u) o[u] = v[u];
         }
     }
-    const size_t o_pair = o_mask + align256(masks.size() * sizeof(unsigned long long));
+    const size_t o_pair0 = o_mask + align256(masks.size() * sizeof(unsigned long long));
+    // double-float (hi, lo) copies of the shell folds and projection weights
+    // for the double-float per-site part of the two-sites-per-lane kernels
+    auto split = [](const std::vector<double> &v) {
+        std::vector<float> o(2 * v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            o[2 * i] = float(v[i]);
+            o[2 * i + 1] = float(v[i] - double(o[2 * i]));
+        }
+        return o;
+    };
+    const std::vector<float> shell2 = split(shell), rt2 = split(rt);
+    const size_t o_shell2 = o_pair0;
+    const size_t o_rt2 = o_shell2 + align256(shell2.size() * 4);
+    const size_t o_pair = o_rt2 + align256(rt2.size() * 4);
     // on-lattice rule: per population integer stencil vector (sx, sy)
     std::vector<int> shifts;
     if (q.onlat)
@@ -479,6 +512,8 @@ rlbm_status build_tables(rlbm_t *h)
     else { put<float>(blob, o_shell, shell); put<float>(blob, o_rt, rt); }
     std::memcpy(blob.data() + o_mask, masks.data(), masks.size() * sizeof(unsigned long long));
     put<float>(blob, o_pair, ptab);
+    std::memcpy(blob.data() + o_shell2, shell2.data(), shell2.size() * 4);
+    std::memcpy(blob.data() + o_rt2, rt2.data(), rt2.size() * 4);
     if (!shifts.empty()) std::memcpy(blob.data() + o_shift, shifts.data(), shifts.size() * sizeof(int));
 
     if (h->d_tabs) { // re-tiling: replace the tables
@@ -513,9 +548,11 @@ rlbm_status build_tables(rlbm_t *h)
     a.inv_tau_f = float(a.inv_tau);
     a.feq_off = scaled ? beta / (2.0 * kPi) : 0.0;
     a.feq_off_f = float(a.feq_off);
+    a.feq_off_l = float(a.feq_off - double(a.feq_off_f));
     for (int t = 0; t < 8; ++t) {
         a.off[t] = off[t];
         a.off_f[t] = float(off[t]);
+        a.off_l[t] = float(off[t] - double(a.off_f[t]));
     }
     for (int j = 0; j <= N; ++j) {
         const double ph = 2.0 * kPi * j / (N + 1);
@@ -523,10 +560,14 @@ rlbm_status build_tables(rlbm_t *h)
         a.smp_s[j] = std::sin(ph);
         a.smp_cf[j] = float(a.smp_c[j]);
         a.smp_sf[j] = float(a.smp_s[j]);
+        a.smp_cl[j] = float(a.smp_c[j] - double(a.smp_cf[j]));
+        a.smp_sl[j] = float(a.smp_s[j] - double(a.smp_sf[j]));
     }
     a.poptab = (const unsigned char *)h->d_tabs + o_pop;
     a.shelltab = (const unsigned char *)h->d_tabs + o_shell;
     a.rtab = (const unsigned char *)h->d_tabs + o_rt;
+    a.shell2 = reinterpret_cast<const float2 *>((const unsigned char *)h->d_tabs + o_shell2);
+    a.rtab2 = reinterpret_cast<const float2 *>((const unsigned char *)h->d_tabs + o_rt2);
     a.masks = reinterpret_cast<const unsigned long long *>((const unsigned char *)h->d_tabs + o_mask);
     a.pairtab = ptab.empty() ? nullptr : (const unsigned char *)h->d_tabs + o_pair;
     a.shifts = shifts.empty() ? nullptr : reinterpret_cast<const int2 *>((const unsigned char *)h->d_tabs + o_shift);
@@ -580,14 +621,14 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
     return e;
 }
 
-// The two-sites-per-lane step kernel applies to FP32 arithmetic with a
-// collision, N <= 3, an even row length, K a multiple of P and P in
-// {8, 12, 16, 24, 32}; with several population groups per warp (many angles)
-// to FP32 storage only.
+// The two-sites-per-lane step kernel applies to FP32 per-population arithmetic
+// (FP32 storage with a double-float per-site part, 16-bit storage with FP32
+// accumulation and a double-float Landau solve) with a collision, N <= 3, an
+// even row length, K a multiple of P and P in {8, 12, 16, 24, 32}; with
+// several population groups per warp (many angles) to FP32 storage only.
 bool pair_possible(const rlbm_t *h, int P)
 {
-    if (h->prec == RLBM_FP64 || h->site_fp64 || std::isinf(h->tau) || h->N > 3 || h->q.onlat || h->stat)
-        return false;
+    if (h->prec == RLBM_FP64 || std::isinf(h->tau) || h->N > 3 || h->q.onlat || h->stat) return false;
     if (h->grid.nx < 2 || h->grid.nx % 2 != 0) return false;
     if (!(P == 8 || P == 12 || P == 16 || P == 24 || P == 32) || h->K % P != 0) return false;
     int gs = 0, ng = 0;
@@ -626,6 +667,24 @@ cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
     return e;
 }
 
+cudaError_t launch_pair_tma(rlbm_t *h, const rlbmk::PairTmaArgs &ta)
+{
+    const dim3 grid((h->grid.nx + rlbmk::kPairSites - 1) / rlbmk::kPairSites, h->grid.ny);
+    const dim3 block(32, h->G);
+    const bool two_d = h->grid.ny > 1;
+    cudaError_t e;
+    switch (h->prec) {
+    case RLBM_FP32: e = rlbmk::launch_pair_tma_f32(h->N, h->P, two_d, grid, block, h->ptma_smem, h->stream, ta); break;
+    case RLBM_FP16_DEV:
+    case RLBM_FP16_NORM:
+        e = rlbmk::launch_pair_tma_f16(h->N, h->P, two_d, grid, block, h->ptma_smem, h->stream, ta);
+        break;
+    default: e = rlbmk::launch_pair_tma_bf16(h->N, h->P, two_d, grid, block, h->ptma_smem, h->stream, ta); break;
+    }
+    if (e == cudaSuccess) ++h->launches;
+    return e;
+}
+
 cudaError_t launch_tma(rlbm_t *h, const rlbmk::TmaArgs &ta, int grid, int *bps)
 {
     const dim3 block(32, h->G);
@@ -651,6 +710,16 @@ cudaError_t launch_step(rlbm_t *h, int from)
         cudaError_t e = launch_tma(h, ta, h->tma_grid, nullptr);
         ta.extra_tx = 0;
         if (e == cudaSuccess) ++h->launches;
+        return e;
+    }
+    if (h->use_pair_tma) {
+        rlbmk::PairTmaArgs &ta = h->ptma[from];
+        ta.a.fin = buffer(h, from);
+        ta.a.fout = buffer(h, 1 - from);
+        ta.a.extra_tx = h->stall_next ? 16u : 0u;
+        h->stall_next = false;
+        cudaError_t e = launch_pair_tma(h, ta);
+        ta.a.extra_tx = 0;
         return e;
     }
     rlbmk::KernelArgs a = h->base;
@@ -748,6 +817,105 @@ rlbm_status setup_tma(rlbm_t *h)
     return RLBM_OK;
 }
 
+// Pull-row chunks of the tile-staged pair kernel: the largest DB in {8, 4}
+// dividing npop for which every chunk of DB consecutive populations shares
+// sgn(v_y) (a population with v_y = 0 gives its pull row the weight 0 and
+// joins either side); bit c of up: chunk c pulls from row y - 1.  0 if none.
+int pull_chunking(const Quad &q, int npop, unsigned long long *up)
+{
+    for (int db : {8, 4}) {
+        if (npop % db || npop / db > 256) continue;
+        unsigned long long m[4] = {0, 0, 0, 0};
+        bool ok = true;
+        for (int c = 0; c < npop / db && ok; ++c) {
+            int sgn = 0;
+            for (int i = c * db; i < (c + 1) * db; ++i) {
+                const int si = q.vy[i] > 0.0 ? 1 : (q.vy[i] < 0.0 ? -1 : 0);
+                if (si == 0) continue;
+                if (sgn == 0) sgn = si;
+                else if (si != sgn) { ok = false; break; }
+            }
+            if (sgn >= 0) m[c >> 6] |= 1ull << (c & 63);
+        }
+        if (ok) {
+            std::memcpy(up, m, sizeof(m));
+            return db;
+        }
+    }
+    return 0;
+}
+
+// Set up the tile-staged two-sites-per-lane kernel for the current tiling, if
+// the pair kernel applies with one population group, the rows are whole
+// 16-byte chunks (the TMA's pitch rule), nx covers one box, the pull rows
+// chunk by sgn(v_y) and the shared memory fits.  Otherwise use_pair_tma stays
+// false.
+rlbm_status setup_pair_tma(rlbm_t *h)
+{
+    h->use_pair_tma = false;
+    delete[] h->ptma;
+    h->ptma = nullptr;
+    const size_t es = storage_size(h->prec);
+    const int BW = rlbmk::kPairSites + 2 * int(16 / es);
+    const int nx = h->grid.nx, ny = h->grid.ny, npop = h->npop;
+    if (!pair_possible(h, h->P) || h->R != 1) return RLBM_OK;
+    if ((size_t(nx) * es) % 16 != 0 || nx < BW || reinterpret_cast<uintptr_t>(h->buf) % 16 != 0) return RLBM_OK;
+    unsigned long long up[4];
+    const int DB = pull_chunking(h->q, npop, up);
+    if (!DB) return RLBM_OK;
+    const int ncbox = (npop + 255) / 256;
+    const int CB = npop / ncbox;
+    if (CB * ncbox != npop || CB % 4 != 0) return RLBM_OK; // whole boxes, 128-byte aligned destinations
+    const bool two_d = ny > 1;
+    const rlbmk::PairTmaSmem L(h->N, h->G, npop, int(es), two_d);
+    int dev = 0, max_smem = 0;
+    RLBM_CUDA(h, cudaGetDevice(&dev));
+    RLBM_CUDA(h, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (L.total > size_t(max_smem)) return RLBM_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qres;
+    RLBM_CUDA(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qres));
+    if (!fn || qres != cudaDriverEntryPointSuccess) return fail(h, RLBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+    CUtensorMapDataType dt;
+    switch (h->prec) {
+    case RLBM_FP32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case RLBM_FP16_DEV:
+    case RLBM_FP16_NORM: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    default: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    }
+    h->ptma = new (std::nothrow) rlbmk::PairTmaArgs[2];
+    if (!h->ptma) return fail(h, RLBM_ERR_OOM, "host allocation failed");
+    const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(npop)};
+    const cuuint64_t strides[2] = {cuuint64_t(nx) * es, cuuint64_t(nx) * ny * es};
+    const cuuint32_t cbox[3] = {cuuint32_t(BW), 1u, cuuint32_t(CB)};
+    const cuuint32_t pbox[3] = {cuuint32_t(BW), 1u, cuuint32_t(DB)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    for (int b = 0; b < 2; ++b) {
+        rlbmk::PairTmaArgs &ta = h->ptma[b];
+        std::memset(&ta, 0, sizeof(ta));
+        for (int m = 0; m < 2; ++m) {
+            CUresult r = encode(m == 0 ? &ta.cmap : &ta.pmap, dt, 3, buffer(h, b), dims, strides, m == 0 ? cbox : pbox,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                delete[] h->ptma;
+                h->ptma = nullptr;
+                return fail(h, RLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+            }
+        }
+        ta.a = h->base;
+        ta.CB = CB;
+        ta.ncbox = ncbox;
+        ta.DB = DB;
+        ta.npbox = npop / DB;
+        std::memcpy(ta.chunk_up, up, sizeof(up));
+    }
+    h->ptma_smem = L.total;
+    h->use_pair_tma = true;
+    return RLBM_OK;
+}
+
 rlbm_status check_status(rlbm_t *h)
 {
     int st = 0;
@@ -808,15 +976,24 @@ rlbm_status retile(rlbm_t *h, int P, int kind)
     }
     h->G = h->Gs * (h->N + 1);
     h->no_tma = kind != 1;
-    h->use_pair = (kind == 2 || kind == 3) && pair_possible(h, P);
+    h->use_pair = (kind == 2 || kind == 3 || kind == 4) && pair_possible(h, P);
     h->pair_bulk = h->use_pair && kind == 3 && pair_bulk_possible(h) && h->R == 1;
     rlbm_status st = build_tables(h);
     if (st) return st;
-    return setup_tma(h);
+    st = setup_tma(h);
+    if (st) return st;
+    h->use_pair_tma = false;
+    if (h->use_pair && kind == 4) {
+        st = setup_pair_tma(h);
+        if (st) return st;
+        if (!h->use_pair_tma) h->use_pair = false; // not possible here: the per-tile kernel
+    }
+    return RLBM_OK;
 }
 
 int kernel_kind(const rlbm_t *h)
 {
+    if (h->use_pair_tma) return 4;
     if (h->use_pair) return h->pair_bulk ? 3 : 2;
     return h->use_tma ? 1 : 0;
 }
@@ -897,12 +1074,7 @@ static rlbm_status create_impl(rlbm_t **out, rlbm_grid grid, int order_N, int an
     h->npop = angles_K * (order_N + 1);
     h->prec = precision;
     h->tau = tau;
-    const char *env = std::getenv("RLBM_FP32_SITE_FP64");
-    // N >= 4: the radial projection weights (inverse of a factorial Gram matrix)
-    // cancel too many digits for FP32 per-site arithmetic, so the per-site part
-    // runs in FP64 for every storage type
-    h->site_fp64 = (precision != RLBM_FP64) &&
-                   (order_N >= 4 || ((precision == RLBM_FP32) && env && env[0] == '1'));
+    h->site_fp64 = site_fp64_for(precision, order_N, 0);
     if (!(onlat ? make_onlattice_quadrature(h->q) : make_quadrature(order_N, angles_K, h->q))) {
         delete h;
         return fail(nullptr, RLBM_ERR_ARG, "quadrature construction failed");
@@ -994,9 +1166,7 @@ rlbm_status rlbm_set_statistics(rlbm_t *h, int statistics, double g)
     h->stat = statistics;
     h->gdeg = statistics != 0 ? g : 1.0;
     // the quantum per-site part runs in FP64 (FP32 storage: FP64 site tables)
-    const char *env = std::getenv("RLBM_FP32_SITE_FP64");
-    h->site_fp64 = (h->prec != RLBM_FP64) &&
-                   (statistics != 0 || h->N >= 4 || ((h->prec == RLBM_FP32) && env && env[0] == '1'));
+    h->site_fp64 = site_fp64_for(h->prec, h->N, statistics);
     return retile(h, h->P, 0);
 }
 
@@ -1020,6 +1190,7 @@ void rlbm_destroy(rlbm_t *h)
     if (h->d_status) cudaFree(h->d_status);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete[] h->tma;
+    delete[] h->ptma;
     delete h;
 }
 
@@ -1177,7 +1348,7 @@ int rlbm_step_kernel_variant(const rlbm_t *h) { return h ? kernel_kind(h) : -1; 
 rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
 {
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
-    if (kind < 0 || kind > 3) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0..3 (got %d)", kind);
+    if (kind < 0 || kind > 4) return fail(h, RLBM_ERR_ARG, "kernel kind must be 0..4 (got %d)", kind);
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
     bool ok = false;
     for (int v : sizes) ok = ok || v == P;
@@ -1190,7 +1361,7 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
         return fail(h, RLBM_ERR_UNSUPPORTED,
                     "K=%d needs several population groups per warp: per-tile or two-sites-per-lane kernel only",
                     h->K);
-    if ((kind == 2 || kind == 3) && !pair_possible(h, P)) {
+    if ((kind == 2 || kind == 3 || kind == 4) && !pair_possible(h, P)) {
         rlbm_status st0 = retile(h, P, 0);
         if (st0) return st0;
         return fail(h, RLBM_ERR_UNSUPPORTED,
@@ -1202,8 +1373,12 @@ rlbm_status rlbm_set_tiling(rlbm_t *h, int P, int kind)
     if (kernel_kind(h) != kind) {
         st = retile(h, P, 0);
         if (st) return st;
-        return fail(h, RLBM_ERR_UNSUPPORTED, kind == 1 ? "TMA-staged kernel not possible for this grid and tiling"
-                                                       : "bulk staging needs rows of whole 16-byte chunks");
+        return fail(h, RLBM_ERR_UNSUPPORTED,
+                    kind == 1   ? "TMA-staged kernel not possible for this grid and tiling"
+                    : kind == 4 ? "tile-staged pair kernel not possible here (rows of whole 16-byte chunks, "
+                                  "nx >= one box, pull rows in chunks of 4 or 8 populations sharing sgn(v_y), "
+                                  "one population group)"
+                                : "bulk staging needs rows of whole 16-byte chunks");
     }
     return RLBM_OK;
 }
@@ -1239,7 +1414,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int launches_per_trial, float *best_ms)
         if (!group_tiling(h->N, h->K, P, gs, ng)) continue;
         if (h->q.onlat && P != 12) continue; // the on-lattice kernel is built for P = 12
         if (P > 2 * h->K) continue;
-        for (int kind = 3; kind >= 0 && st == RLBM_OK; --kind) {
+        for (int kind = 4; kind >= 0 && st == RLBM_OK; --kind) {
             st = retile(h, P, kind);
             if (st) break;
             if (kernel_kind(h) != kind) continue; // kernel kind not possible for this tiling
@@ -1279,6 +1454,8 @@ rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles)
     if (cycles < 1000) return fail(h, RLBM_ERR_ARG, "wait limit must be >= 1000 cycles");
     if (h->tma)
         for (int b = 0; b < 2; ++b) h->tma[b].wait_cycles = cycles;
+    if (h->ptma)
+        for (int b = 0; b < 2; ++b) h->ptma[b].a.wait_cycles = cycles;
     h->wait_cycles = cycles;
     h->base.wait_cycles = cycles;
     for (auto &g : h->graph)
@@ -1289,7 +1466,7 @@ rlbm_status rlbm_set_wait_limit(rlbm_t *h, long long cycles)
 rlbm_status rlbm_test_stall_next_step(rlbm_t *h)
 {
     if (!h) return fail(nullptr, RLBM_ERR_ARG, "NULL handle");
-    if (!h->use_tma && !h->pair_bulk)
+    if (!h->use_tma && !h->pair_bulk && !h->use_pair_tma)
         return fail(h, RLBM_ERR_UNSUPPORTED, "this step kernel has no device waits");
     h->stall_next = true;
     return RLBM_OK;
@@ -1444,6 +1621,8 @@ rlbm_status batch_launch(rlbm_batch *b, int nsteps, bool use_graph)
             cudaError_t e = cudaMemsetAsync(b->d_sync, 0, 4 * sizeof(unsigned), b->stream);
             if (e == cudaSuccess)
                 e = rlbmk::launch_batch(b->prec, b->N, batch_args(b, nsteps), b->grid, b->stream, nullptr);
+            if (e == cudaSuccess)
+                e = rlbmk::launch_batch_advance(b->d_args, int(b->probs.size()), nsteps, b->stream);
             cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
             if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); BATCH_CUDA(b, e); }
             BATCH_CUDA(b, e2);
@@ -1459,8 +1638,9 @@ rlbm_status batch_launch(rlbm_batch *b, int nsteps, bool use_graph)
         rlbmk::BatchArgs a = batch_args(b, nsteps);
         if (stall) a.barrier_extra = 1;
         BATCH_CUDA(b, rlbmk::launch_batch(b->prec, b->N, a, b->grid, b->stream, nullptr));
+        BATCH_CUDA(b, rlbmk::launch_batch_advance(b->d_args, int(b->probs.size()), nsteps, b->stream));
     }
-    ++b->launches;
+    b->launches += 2; // the batched kernel and the counter advance
     return RLBM_OK;
 }
 

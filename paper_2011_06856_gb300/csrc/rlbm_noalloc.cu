@@ -154,7 +154,7 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
         grid.bc_y < 0 || grid.bc_y > 1)
         return fail(RLBM_ERR_ARG, "invalid grid or boundary condition");
     if (N < 2 || K < 2 * N + 1 || !(tau > 0.0)) return fail(RLBM_ERR_ARG, "need N >= 2, K >= 2N+1, tau > 0");
-    if (!d_fin || !d_fout || d_fin == d_fout) return fail(RLBM_ERR_ARG, "need distinct input and output buffers");
+    if (!d_fin || !d_fout) return fail(RLBM_ERR_ARG, "need input and output buffers");
     if (precision != RLBM_FP64 && precision != RLBM_FP32)
         return fail(RLBM_ERR_UNSUPPORTED, "rlbm_step_noalloc supports FP64 and FP32 storage");
     if (N > 3 || npop > kMaxNpop)
@@ -164,6 +164,11 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
     const size_t es = r64 ? 8 : 4;
     if (((uintptr_t)d_fin % es) || ((uintptr_t)d_fout % es))
         return fail(RLBM_ERR_ARG, "buffers must be aligned to the element size");
+    // the step streams from d_fin into d_fout: the two byte ranges must not overlap
+    const size_t len = size_t(npop) * size_t(grid.nx) * size_t(grid.ny) * es;
+    const uintptr_t pi = (uintptr_t)d_fin, po = (uintptr_t)d_fout;
+    if (pi < po + len && po < pi + len)
+        return fail(RLBM_ERR_ARG, "input and output buffers overlap");
 
     // tiling: fewest idle population slots, then the larger P (as rlbm_create)
     static const int sizes[] = {8, 12, 16, 24, 32, 48, 64};
@@ -189,11 +194,15 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
         laguerre2(N + 2, pr[r], l, lm);
         wr[r] = pr[r] / ((N + 2.0) * (N + 2.0) * l * l);
     }
+    // per-population table in the storage's arithmetic type; the per-site part
+    // (moment folds, Landau frame, projection weights) runs in FP64 for FP32
+    // storage as well, as it does in the handle's per-tile kernel
+    const size_t ls = 8;
     const size_t o_status = 0;
     const size_t o_pop = 256;
     const size_t o_shell = o_pop + align256(size_t(npop) * TW * es);
-    const size_t o_rt = o_shell + align256(size_t(N + 1) * 2 * es);
-    const size_t o_mask = o_rt + align256(size_t(N + 1) * (N + 1) * (N + 1) * es);
+    const size_t o_rt = o_shell + align256(size_t(N + 1) * 2 * ls);
+    const size_t o_mask = o_rt + align256(size_t(N + 1) * (N + 1) * (N + 1) * ls);
     const size_t total = o_mask + align256(size_t(G) * 2 * 8);
     if (total > kScratchBytes) return fail(RLBM_ERR_ARG, "tables exceed the 32 KB scratch array");
     std::memset(g_blob, 0, total);
@@ -222,9 +231,9 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
             if (s >= 0.0) masks[2 * g + 1] |= 1ull << k;
         }
     for (int r = 0; r <= N; ++r) {
-        unsigned char *d = g_blob + o_shell + size_t(2 * r) * es;
-        if (r64) { put<double>(d, pr[r]); put<double>(d + es, pr[r] * pr[r]); }
-        else { put<float>(d, pr[r]); put<float>(d + es, pr[r] * pr[r]); }
+        unsigned char *d = g_blob + o_shell + size_t(2 * r) * ls;
+        put<double>(d, pr[r]);
+        put<double>(d + ls, pr[r] * pr[r]);
     }
     for (int m = 0; m <= N; ++m) {
         const int d = N - m + 1;
@@ -237,9 +246,8 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
                 for (int l = m; l <= N; ++l) s += std::pow(pr[r], l) * Gi[l - m][k - m];
                 double kf = 1.0;
                 for (int t = 2; t <= k; ++t) kf *= t;
-                unsigned char *dst = g_blob + o_rt + (size_t(r * (N + 1) + m) * (N + 1) + k) * es;
-                const double v = s / norm * kf / (N + 1);
-                if (r64) put<double>(dst, v); else put<float>(dst, v);
+                unsigned char *dst = g_blob + o_rt + (size_t(r * (N + 1) + m) * (N + 1) + k) * ls;
+                put<double>(dst, s / norm * kf / (N + 1));
             }
     }
     std::memcpy(g_blob + o_mask, masks, size_t(G) * 2 * 8);
@@ -283,11 +291,11 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
     a.ctr = reinterpret_cast<unsigned *>(base + o_status + 4);
 
     const dim3 gridd((grid.nx + 31) / 32, grid.ny), block(32, G);
-    const size_t smem = es * 5 * size_t(G) * 32;
+    const size_t smem = ls * 5 * size_t(G) * 32;
     const bool full = (K % P) == 0;
     const cudaError_t e = r64 ? rlbmk::launch_f64(rlbmk::MODE_STEP, N, P, grid.ny > 1, full, gridd,
                                                   block, smem, stream, a)
-                              : rlbmk::launch_f32(rlbmk::MODE_STEP, N, P, grid.ny > 1, full, false,
+                              : rlbmk::launch_f32(rlbmk::MODE_STEP, N, P, grid.ny > 1, full, true,
                                                   gridd, block, smem, stream, a);
     if (e != cudaSuccess) return fail(RLBM_ERR_CUDA, cudaGetErrorString(e));
     int status = 0;

@@ -1,0 +1,9 @@
+// Two-sites-per-lane step kernel instances: BF16 storage, FP32 accumulation, double-float Landau frame, N = 2, plain loads.
+#include "rlbm_pair.cuh"
+namespace rlbmk {
+cudaError_t launch_pair_bf16_n2p(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                   const KernelArgs &a)
+{
+    return launch_pair_nb<__nv_bfloat16, 2, false>(PP, two_d, grid, block, smem, st, a);
+}
+} // namespace rlbmk

@@ -1,0 +1,9 @@
+// Two-sites-per-lane step kernel instances: FP16 storage, FP32 accumulation, double-float Landau frame, N = 3, bulk-staged first pass.
+#include "rlbm_pair.cuh"
+namespace rlbmk {
+cudaError_t launch_pair_f16_n3b(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                   const KernelArgs &a)
+{
+    return launch_pair_nb<__half, 3, true>(PP, two_d, grid, block, smem, st, a);
+}
+} // namespace rlbmk

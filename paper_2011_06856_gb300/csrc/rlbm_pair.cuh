@@ -166,8 +166,33 @@ template <> struct PIo<__nv_bfloat16> {
     }
 };
 
-// The per-site part for site s of the tile (FP32): moments from the warps'
-// angular sums, Landau frame, and the shell-independent part of the
+// The relaxation f* + om (f^eq - f*) of two sites (packed), rounded
+// stochastically to FP32 (relax_sr in rlbm_device.cuh, for both sites at
+// once): rb gives 16 random bits per site.
+__device__ __forceinline__ float2 relax_pair_sr(float2 fs, float2 om, float2 feq, unsigned rb)
+{
+    const float2 d = f2sub(feq, fs);
+    const float2 r = __ffma2_rn(om, d, fs);
+    const float2 e = __ffma2_rn(om, d, f2sub(fs, r));
+    const float2 ulp = __fmul2_rn(f2(__uint_as_float(__float_as_uint(r.x) & 0x7f800000u),
+                                     __uint_as_float(__float_as_uint(r.y) & 0x7f800000u)),
+                                  f2(1.1920928955078125e-7f, 1.1920928955078125e-7f));
+    const float2 u = __fadd2_rn(f2(__uint_as_float(0x3f800000u | ((rb & 0xffffu) << 7)),
+                                   __uint_as_float(0x3f800000u | ((rb >> 16) << 7))),
+                                f2(-1.5f, -1.5f));
+    return __fadd2_rn(r, __ffma2_rn(u, ulp, e));
+}
+
+// 32 random bits from the thread's LCG stream, high bits folded into the low ones
+__device__ __forceinline__ unsigned next_bits(unsigned &rng)
+{
+    lcg_next(rng);
+    return rng ^ (rng >> 15);
+}
+
+// The per-site part for site s of the tile with FP32 accumulation (16-bit
+// storage): moments from the warps' angular sums, the Landau frame in
+// double-float (landau_f32dd), and the shell-independent part of the
 // equilibrium coefficients (the boosted-direction sums acc, weighted by
 // n T^(k-1)), written to sres[row 64 + s]; then U^a / tau at rows
 // (N+1)^2 + 0..2.  Every warp forms its own shell's coefficients from these.
@@ -202,7 +227,7 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
         m[7] += f2v * pcs;
     }
     float n, eps, U0, Ux, Uy;
-    const bool ok = landau_fast<float>(m, n, eps, U0, Ux, Uy);
+    const bool ok = landau_f32dd(m, n, eps, U0, Ux, Uy);
     const float T = eps / (2.f * n);
     if (!ok && act) atomicOr(a.status, 1);
     // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
@@ -258,6 +283,217 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
     sres[((N + 1) * (N + 1) + 2) * kPairSites + s] = Uy * itau;
 }
 
+// The per-site part for site s with FP64-class accuracy (FP32 storage), in
+// double-float arithmetic (rlbm_df64.cuh): the warps' FP32 angular sums are
+// folded into N^a and T^ab (Eq. discrete_sum_moments) in double-float, the
+// Landau frame is solved in double-float (landau_dd), and the shell-independent
+// equilibrium sums w_{m,k} = n T^(k-1) acc_{m,k} are formed in double-float
+// and written as hi rows 0 .. (N+1)^2 - 1 and lo rows (N+1)^2 .. 2 (N+1)^2 - 1
+// of sres; U^a / tau follow at rows 2 (N+1)^2 + 0..2 (FP32: the relaxation
+// rate enters the conserved moments only at second order).  An FP32 per-site
+// part carries the conserved moments to a relative bias of about 4e-7 per
+// step (rounding of the moment fold, the frame and the radial projection,
+// which cancels about one digit); the collision feeds omega of that into the
+// state every step and it grows linearly; in double-float it is below 1e-12.
+template <int N>
+__device__ __forceinline__ void pair_site_solve_dd(const KernelArgs &a, const float *red, int G, int s, bool act,
+                                                   float *sres)
+{
+    constexpr int W = (N + 1) * (N + 1);
+    df64 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = dd(a.off_f[u], a.off_l[u]);
+#pragma unroll
+    for (int rr = 0; rr <= N; ++rr) {
+        df64 p0 = dd(0.f), pc = dd(0.f), ps = dd(0.f), pcc = dd(0.f), pcs = dd(0.f);
+        for (int qq = 0; qq < a.Gs; ++qq) {
+            const int w = rr * a.Gs + qq;
+            p0 = p0 + red[(0 * G + w) * kPairSites + s];
+            pc = pc + red[(1 * G + w) * kPairSites + s];
+            ps = ps + red[(2 * G + w) * kPairSites + s];
+            pcc = pcc + red[(3 * G + w) * kPairSites + s];
+            pcs = pcs + red[(4 * G + w) * kPairSites + s];
+        }
+        const float2 t1 = __ldg(a.shell2 + 2 * rr), t2 = __ldg(a.shell2 + 2 * rr + 1);
+        const df64 f1 = dd(t1.x, t1.y), f2v = dd(t2.x, t2.y);
+        m[0] = m[0] + f1 * p0;
+        m[1] = m[1] + f1 * pc;
+        m[2] = m[2] + f1 * ps;
+        m[3] = m[3] + f2v * p0;
+        m[4] = m[4] + f2v * pc;
+        m[5] = m[5] + f2v * ps;
+        m[6] = m[6] + f2v * pcc;
+        m[7] = m[7] + f2v * pcs;
+    }
+    df64 n, eps, U0, Ux, Uy;
+    const bool ok = landau_dd(m, n, eps, U0, Ux, Uy);
+    if (!ok && act) atomicOr(a.status, 1);
+    const df64 T = eps / (n * 2.f);
+    const df64 inv1g = dd(1.f) / (U0 + 1.f);
+    // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
+    df64 accr[N + 1][N + 1], acci[N + 1][N + 1];
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+        for (int k = 0; k <= N; ++k) { accr[mm][k] = dd(0.f); acci[mm][k] = dd(0.f); }
+#pragma unroll
+    for (int j = 0; j <= N; ++j) {
+        const df64 cj = dd(a.smp_cf[j], a.smp_cl[j]), sj = dd(a.smp_sf[j], a.smp_sl[j]);
+        const df64 un = Ux * cj + Uy * sj;
+        const df64 h = un * inv1g + 1.f;
+        df64 qp[N + 1], pr[N + 1], pi[N + 1];
+        qp[1] = U0 + un;
+        pr[1] = cj + Ux * h;
+        pi[1] = sj + Uy * h;
+#pragma unroll
+        for (int t = 2; t <= N; ++t) {
+            qp[t] = qp[t - 1] * qp[1];
+            pr[t] = pr[t - 1] * pr[1] - pi[t - 1] * pi[1];
+            pi[t] = pr[t - 1] * pi[1] + pi[t - 1] * pr[1];
+        }
+#pragma unroll
+        for (int k = 1; k <= N; ++k) accr[0][k] = accr[0][k] + qp[k];
+#pragma unroll
+        for (int mm = 1; mm <= N; ++mm) {
+            accr[mm][mm] = accr[mm][mm] + pr[mm];
+            acci[mm][mm] = acci[mm][mm] + pi[mm];
+#pragma unroll
+            for (int k = mm + 1; k <= N; ++k) {
+                accr[mm][k] = accr[mm][k] + qp[k - mm] * pr[mm];
+                acci[mm][k] = acci[mm][k] + qp[k - mm] * pi[mm];
+            }
+        }
+    }
+    accr[0][0] = dd(float(N + 1));
+    df64 tk[N + 1];
+    tk[0] = n / T;
+    tk[1] = n;
+#pragma unroll
+    for (int k = 2; k <= N; ++k) tk[k] = tk[k - 1] * T;
+    int row = 0;
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+        for (int k = mm; k <= N; ++k, ++row) {
+            const df64 w = tk[k] * accr[mm][k];
+            sres[row * kPairSites + s] = w.hi;
+            sres[(W + row) * kPairSites + s] = w.lo;
+        }
+#pragma unroll
+    for (int mm = 1; mm <= N; ++mm)
+#pragma unroll
+        for (int k = mm; k <= N; ++k, ++row) {
+            const df64 w = tk[k] * acci[mm][k];
+            sres[row * kPairSites + s] = w.hi;
+            sres[(W + row) * kPairSites + s] = w.lo;
+        }
+    const float itau = a.inv_tau_f;
+    sres[(2 * W + 0) * kPairSites + s] = to_float(U0) * itau;
+    sres[(2 * W + 1) * kPairSites + s] = to_float(Ux) * itau;
+    sres[(2 * W + 2) * kPairSites + s] = to_float(Uy) * itau;
+}
+
+// Shell r's equilibrium coefficients for the lane's two sites, in the basis
+// (1, c, s, cc, cs [, c cc, s cc]) of the pair kernels' second pass, and the
+// relaxation factors o = U^a / tau.  The Fourier coefficients are
+// C_{r,m} = sum_k R'[r][m][k] w_{m,k} (Eq. mj-feq-expansion-truncated in the
+// per-shell Fourier form); with cos 2t = 2 cc - 1, sin 2t = 2 cs,
+// cos 3t = 4 c cc - 3 c and sin 3t = 4 s cc - s they become cr.  DD: the
+// w_{m,k} are double-floats (pair_site_solve_dd) and the radial sums and the
+// change of basis run in packed double-float, rounded to FP32 at the end;
+// otherwise everything is packed FP32.
+template <int N, bool DD>
+__device__ __forceinline__ void pair_shell_coefficients(const KernelArgs &a, int r, const float *sres, int lane,
+                                                        float2 *cr, float2 &o0, float2 &o1, float2 &o2)
+{
+    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
+    constexpr int NC = 2 * N + 1;
+    constexpr int W = (N + 1) * (N + 1);
+    const float2 *sres2 = reinterpret_cast<const float2 *>(sres);
+    if constexpr (DD) {
+        const float2 *rt = a.rtab2 + r * (N + 1) * (N + 1);
+        df2 cf[NC];
+        int row = 0;
+#pragma unroll
+        for (int mm = 0; mm <= N; ++mm) {
+            df2 acc{f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll
+            for (int k = mm; k <= N; ++k, ++row) {
+                const float2 t = __ldg(rt + mm * (N + 1) + k);
+                const df2 w{sres2[row * 32 + lane], sres2[(W + row) * 32 + lane]};
+                acc = acc + w * dd(t.x, t.y);
+            }
+            if (mm == 0)
+                cf[0] = acc - df2{f2(a.feq_off_f, a.feq_off_f), f2(a.feq_off_l, a.feq_off_l)};
+            else
+                cf[2 * mm - 1] = acc;
+        }
+#pragma unroll
+        for (int mm = 1; mm <= N; ++mm) {
+            df2 acc{f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll
+            for (int k = mm; k <= N; ++k, ++row) {
+                const float2 t = __ldg(rt + mm * (N + 1) + k);
+                const df2 w{sres2[row * 32 + lane], sres2[(W + row) * 32 + lane]};
+                acc = acc + w * dd(t.x, t.y);
+            }
+            cf[2 * mm] = acc;
+        }
+        df2 c1 = cf[1], c2 = cf[2];
+        if (N == 3) {
+            c1 = c1 - scale(cf[NC - 2], 3.f);
+            c2 = c2 - cf[NC - 1];
+            cr[NC - 2] = to_float2(scale(cf[NC - 2], 4.f));
+            cr[NC - 1] = to_float2(scale(cf[NC - 1], 4.f));
+        }
+        cr[0] = to_float2(cf[0] - cf[3]);
+        cr[1] = to_float2(c1);
+        cr[2] = to_float2(c2);
+        cr[3] = to_float2(scale(cf[3], 2.f));
+        cr[4] = to_float2(scale(cf[4], 2.f));
+    } else {
+        const float *rt = reinterpret_cast<const float *>(a.rtab) + r * (N + 1) * (N + 1);
+        float2 cf[NC];
+        int row = 0;
+#pragma unroll
+        for (int mm = 0; mm <= N; ++mm) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float w = __ldg(rt + mm * (N + 1) + k);
+                acc = __ffma2_rn(f2(w, w), sres2[(row++) * 32 + lane], acc);
+            }
+            if (mm == 0) cf[0] = __fadd2_rn(acc, f2(-a.feq_off_f, -a.feq_off_f));
+            else cf[2 * mm - 1] = acc;
+        }
+#pragma unroll
+        for (int mm = 1; mm <= N; ++mm) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int k = mm; k <= N; ++k) {
+                const float w = __ldg(rt + mm * (N + 1) + k);
+                acc = __ffma2_rn(f2(w, w), sres2[(row++) * 32 + lane], acc);
+            }
+            cf[2 * mm] = acc;
+        }
+        cr[0] = f2sub(cf[0], cf[3]);
+        cr[1] = cf[1];
+        cr[2] = cf[2];
+        cr[3] = __fmul2_rn(f2(2.f, 2.f), cf[3]);
+        cr[4] = __fmul2_rn(f2(2.f, 2.f), cf[4]);
+        if (N == 3) {
+            cr[1] = __ffma2_rn(f2(-3.f, -3.f), cf[NC - 2], cr[1]);
+            cr[2] = f2sub(cr[2], cf[NC - 1]);
+            cr[NC - 2] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 2]);
+            cr[NC - 1] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 1]);
+        }
+    }
+    constexpr int OR = DD ? 2 * W : W; // row of U^0 / tau
+    o0 = sres2[(OR + 0) * 32 + lane];
+    o1 = sres2[(OR + 1) * 32 + lane];
+    o2 = sres2[(OR + 2) * 32 + lane];
+}
+
 // St: storage type; N: quadrature order; PP: populations per warp (K is a
 // multiple of PP); TWO_D: ny > 1; BULK: staged pass 1 on interior tiles (row
 // pitch a multiple of 16 bytes, buffers 16-byte aligned).  Requires nx even
@@ -280,7 +516,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
     const St *fin = reinterpret_cast<const St *>(a.fin);
     St *fout = reinterpret_cast<St *>(a.fout);
     float *red = reinterpret_cast<float *>(smem_raw); // [5][G][64]
-    float *sres = red + 5 * G * kPairSites;           // [(N+1)^2 + 3][64] used of [(N+1) NC + 3][64]
+    float *sres = red + 5 * G * kPairSites;           // [pair_site_rows(N)][64]
     const float4 *tb = reinterpret_cast<const float4 *>(a.pairtab) + size_t(i0) * PQ;
 
     const int xm = bc_index(xa - 1, a.nx, a.bcx), xp = bc_index(xa + 2, a.nx, a.bcx);
@@ -415,62 +651,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
     red2[(3 * G + g) * 32 + lane] = scc;
     red2[(4 * G + g) * 32 + lane] = scs;
     __syncthreads();
+    constexpr bool DD = sizeof(St) == 4; // FP32 storage: FP64-class per-site part
     if (g < 2) {
         const int s = g * 32 + lane;
-        pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
+        if constexpr (DD) pair_site_solve_dd<N>(a, red, G, s, x0 + s < a.nx, sres);
+        else pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
     }
     __syncthreads();
 
-    // this warp's shell: Fourier coefficients C_{r,m} = sum_k R'[r][m][k] w_{m,k} of its two
-    // sites (packed), then the basis (1, c, s, cc, cs [, c cc, s cc]):
-    // cos 2t = 2 cc - 1, sin 2t = 2 cs, cos 3t = 4 c cc - 3 c, sin 3t = 4 s cc - s
-    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
-    const float2 *sres2 = reinterpret_cast<const float2 *>(sres);
-    const float *rt = reinterpret_cast<const float *>(a.rtab) + r * (N + 1) * (N + 1);
-    float2 cf[NC];
-    {
-        int row = 0;
-#pragma unroll
-        for (int mm = 0; mm <= N; ++mm) {
-            float2 acc = f2(0.f, 0.f);
-#pragma unroll
-            for (int k = mm; k <= N; ++k) {
-                const float w = __ldg(rt + mm * (N + 1) + k);
-                acc = __ffma2_rn(f2(w, w), sres2[(row++) * 32 + lane], acc);
-            }
-            if (mm == 0) cf[0] = __fadd2_rn(acc, f2(-a.feq_off_f, -a.feq_off_f));
-            else cf[2 * mm - 1] = acc;
-        }
-#pragma unroll
-        for (int mm = 1; mm <= N; ++mm) {
-            float2 acc = f2(0.f, 0.f);
-#pragma unroll
-            for (int k = mm; k <= N; ++k) {
-                const float w = __ldg(rt + mm * (N + 1) + k);
-                acc = __ffma2_rn(f2(w, w), sres2[(row++) * 32 + lane], acc);
-            }
-            cf[2 * mm] = acc;
-        }
-    }
-    float2 cr[NC];
-    cr[0] = f2sub(cf[0], cf[3]);
-    cr[1] = cf[1];
-    cr[2] = cf[2];
-    cr[3] = __fmul2_rn(f2(2.f, 2.f), cf[3]);
-    cr[4] = __fmul2_rn(f2(2.f, 2.f), cf[4]);
-    if (N == 3) {
-        cr[1] = __ffma2_rn(f2(-3.f, -3.f), cf[NC - 2], cr[1]);
-        cr[2] = f2sub(cr[2], cf[NC - 1]);
-        cr[NC - 2] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 2]);
-        cr[NC - 1] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 1]);
-    }
-    const float2 o0 = sres2[((N + 1) * (N + 1) + 0) * 32 + lane];
-    const float2 o1 = sres2[((N + 1) * (N + 1) + 1) * 32 + lane];
-    const float2 o2 = sres2[((N + 1) * (N + 1) + 2) * 32 + lane];
+    // this warp's shell: its equilibrium coefficients for its two sites
+    float2 cr[NC], o0, o1, o2;
+    pair_shell_coefficients<N, DD>(a, r, sres, lane, cr, o0, o1, o2);
     const float2 no1 = f2(-o1.x, -o1.y), no2 = f2(-o2.x, -o2.y);
-    constexpr bool kSR = sizeof(St) == 2;
-    unsigned rng = 0;
-    if (kSR) rng = mix32(unsigned(y * a.nx + xa) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
+    constexpr bool kSR = sizeof(St) <= 4; // FP32 and 16-bit stores round stochastically
+    unsigned rng = mix32(unsigned(y * a.nx + xa) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
     St *ob = fout + (long long)i0 * S + (long long)y * a.nx + xa;
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
@@ -488,8 +682,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
         }
         const float2 feq = __fmul2_rn(wq, pe);
         const float2 om = __ffma2_rn(no2, sn, __ffma2_rn(no1, c, o0));
-        const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
-        if (act && good) PIo<St>::st2(ob + (long long)k * S, out, rng);
+        if constexpr (sizeof(St) == 4) {
+            const float2 out = relax_pair_sr(fs[k], om, feq, next_bits(rng));
+            if (act && good) *reinterpret_cast<float2 *>(ob + (long long)k * S) = out;
+        } else {
+            const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
+            if (act && good) PIo<St>::st2(ob + (long long)k * S, out, rng);
+        }
     }
     if (kSR) {
         __syncthreads();
@@ -522,7 +721,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_gr
     const float *fin = reinterpret_cast<const float *>(a.fin);
     float *fout = reinterpret_cast<float *>(a.fout);
     float *red = reinterpret_cast<float *>(smem_raw); // [5][G][64]
-    float *sres = red + 5 * G * kPairSites;           // [(N+1)^2 + 3][64]
+    float *sres = red + 5 * G * kPairSites;           // [pair_site_rows(N)][64]
     const float4 *ptab = reinterpret_cast<const float4 *>(a.pairtab);
     const int xm = bc_index(xa - 1, a.nx, a.bcx), xp = bc_index(xa + 2, a.nx, a.bcx);
     const int ym = TWO_D ? bc_index(y - 1, a.ny, a.bcy) : y;
@@ -601,55 +800,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_gr
     __syncthreads();
     if (g < 2) {
         const int s = g * 32 + lane;
-        pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
+        pair_site_solve_dd<N>(a, red, G, s, x0 + s < a.nx, sres);
     }
     __syncthreads();
 
     // this warp's shell coefficients for its two sites (as in rlbm_pair_kernel)
-    static_assert(N == 2 || N == 3, "the polynomial basis below is written for N = 2, 3");
-    const float2 *sres2 = reinterpret_cast<const float2 *>(sres);
-    const float *rt = reinterpret_cast<const float *>(a.rtab) + r * (N + 1) * (N + 1);
-    float2 cf[NC];
-    {
-        int rw = 0;
-#pragma unroll
-        for (int mm = 0; mm <= N; ++mm) {
-            float2 acc = f2(0.f, 0.f);
-#pragma unroll
-            for (int k = mm; k <= N; ++k) {
-                const float w = __ldg(rt + mm * (N + 1) + k);
-                acc = __ffma2_rn(f2(w, w), sres2[(rw++) * 32 + lane], acc);
-            }
-            if (mm == 0) cf[0] = __fadd2_rn(acc, f2(-a.feq_off_f, -a.feq_off_f));
-            else cf[2 * mm - 1] = acc;
-        }
-#pragma unroll
-        for (int mm = 1; mm <= N; ++mm) {
-            float2 acc = f2(0.f, 0.f);
-#pragma unroll
-            for (int k = mm; k <= N; ++k) {
-                const float w = __ldg(rt + mm * (N + 1) + k);
-                acc = __ffma2_rn(f2(w, w), sres2[(rw++) * 32 + lane], acc);
-            }
-            cf[2 * mm] = acc;
-        }
-    }
-    float2 cr[NC];
-    cr[0] = f2sub(cf[0], cf[3]);
-    cr[1] = cf[1];
-    cr[2] = cf[2];
-    cr[3] = __fmul2_rn(f2(2.f, 2.f), cf[3]);
-    cr[4] = __fmul2_rn(f2(2.f, 2.f), cf[4]);
-    if (N == 3) {
-        cr[1] = __ffma2_rn(f2(-3.f, -3.f), cf[NC - 2], cr[1]);
-        cr[2] = f2sub(cr[2], cf[NC - 1]);
-        cr[NC - 2] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 2]);
-        cr[NC - 1] = __fmul2_rn(f2(4.f, 4.f), cf[NC - 1]);
-    }
-    const float2 o0 = sres2[((N + 1) * (N + 1) + 0) * 32 + lane];
-    const float2 o1 = sres2[((N + 1) * (N + 1) + 1) * 32 + lane];
-    const float2 o2 = sres2[((N + 1) * (N + 1) + 2) * 32 + lane];
+    float2 cr[NC], o0, o1, o2;
+    pair_shell_coefficients<N, true>(a, r, sres, lane, cr, o0, o1, o2);
     const float2 no1 = f2(-o1.x, -o1.y), no2 = f2(-o2.x, -o2.y);
+    unsigned rng = mix32(unsigned(y * a.nx + xa) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));
 #pragma unroll 1
     for (int rho = nrho - 1; rho >= 0; --rho) {
         const int vw = rho * a.Gs + q;
@@ -676,13 +835,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_gr
             }
             const float2 feq = __fmul2_rn(wq, pe);
             const float2 om = __ffma2_rn(no2, sn, __ffma2_rn(no1, c, o0));
-            const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
+            const float2 out = relax_pair_sr(fs[k], om, feq, next_bits(rng));
             if (act) *reinterpret_cast<float2 *>(ob + (long long)k * S) = out;
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) advance_launch_counter(a.ctr, gridDim.x * gridDim.y);
 }
 
-// Several population groups per warp (FP32 storage, plain loads).
+// Several population groups per warp (FP32 storage, plain loads): the
+// instances of one order N (one compile unit per N).
 template <int N, int PP>
 static cudaError_t launch_pair_groups_np(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                          const KernelArgs &a)
@@ -696,24 +858,28 @@ static cudaError_t launch_pair_groups_np(bool two_d, dim3 grid, dim3 block, size
     return cudaGetLastError();
 }
 
-static inline cudaError_t launch_pair_groups(int N, int PP, bool two_d, dim3 grid, dim3 block, size_t smem,
-                                             cudaStream_t st, const KernelArgs &a)
+template <int N>
+static cudaError_t launch_pair_groups_n(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                        const KernelArgs &a)
 {
-#define RLBM_PAIR_CASE(n, p)                                                                                 \
-    if (N == n && PP == p) return launch_pair_groups_np<n, p>(two_d, grid, block, smem, st, a);
-    RLBM_PAIR_CASE(2, 8) RLBM_PAIR_CASE(2, 12) RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
-    RLBM_PAIR_CASE(3, 8) RLBM_PAIR_CASE(3, 12) RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
-#undef RLBM_PAIR_CASE
-    return cudaErrorInvalidValue;
+    switch (PP) {
+    case 8: return launch_pair_groups_np<N, 8>(two_d, grid, block, smem, st, a);
+    case 12: return launch_pair_groups_np<N, 12>(two_d, grid, block, smem, st, a);
+    case 16: return launch_pair_groups_np<N, 16>(two_d, grid, block, smem, st, a);
+    case 24: return launch_pair_groups_np<N, 24>(two_d, grid, block, smem, st, a);
+    case 32: return launch_pair_groups_np<N, 32>(two_d, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-template <class St, int N, int PP>
-static cudaError_t launch_pair_np(bool two_d, bool bulk, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                                  const KernelArgs &a)
+// The two-sites-per-lane kernel of storage St, order N, plain (BULK false) or
+// bulk-staged first pass: the instances of one compile unit.
+template <class St, int N, int PP, bool BULK>
+static cudaError_t launch_pair_one(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                   const KernelArgs &a)
 {
     void (*k)(const KernelArgs) =
-        two_d ? (bulk ? rlbm_pair_kernel<St, N, PP, true, true> : rlbm_pair_kernel<St, N, PP, true, false>)
-              : (bulk ? rlbm_pair_kernel<St, N, PP, false, true> : rlbm_pair_kernel<St, N, PP, false, false>);
+        two_d ? rlbm_pair_kernel<St, N, PP, true, BULK> : rlbm_pair_kernel<St, N, PP, false, BULK>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -722,16 +888,18 @@ static cudaError_t launch_pair_np(bool two_d, bool bulk, dim3 grid, dim3 block, 
     return cudaGetLastError();
 }
 
-template <class St>
-static cudaError_t launch_pair_t(int N, int PP, bool two_d, bool bulk, dim3 grid, dim3 block, size_t smem,
-                                 cudaStream_t st, const KernelArgs &a)
+template <class St, int N, bool BULK>
+static cudaError_t launch_pair_nb(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  const KernelArgs &a)
 {
-#define RLBM_PAIR_CASE(n, p)                                                                                 \
-    if (N == n && PP == p) return launch_pair_np<St, n, p>(two_d, bulk, grid, block, smem, st, a);
-    RLBM_PAIR_CASE(2, 8) RLBM_PAIR_CASE(2, 12) RLBM_PAIR_CASE(2, 16) RLBM_PAIR_CASE(2, 24) RLBM_PAIR_CASE(2, 32)
-    RLBM_PAIR_CASE(3, 8) RLBM_PAIR_CASE(3, 12) RLBM_PAIR_CASE(3, 16) RLBM_PAIR_CASE(3, 24) RLBM_PAIR_CASE(3, 32)
-#undef RLBM_PAIR_CASE
-    return cudaErrorInvalidValue;
+    switch (PP) {
+    case 8: return launch_pair_one<St, N, 8, BULK>(two_d, grid, block, smem, st, a);
+    case 12: return launch_pair_one<St, N, 12, BULK>(two_d, grid, block, smem, st, a);
+    case 16: return launch_pair_one<St, N, 16, BULK>(two_d, grid, block, smem, st, a);
+    case 24: return launch_pair_one<St, N, 24, BULK>(two_d, grid, block, smem, st, a);
+    case 32: return launch_pair_one<St, N, 32, BULK>(two_d, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 } // namespace rlbmk

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_step_tma(const __grid_con
     }
     __syncthreads();
 
-    const unsigned step_seed = (sizeof(St) == 2) ? mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u) : 0u;
+    const unsigned step_seed = (sizeof(St) <= 4) ? mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u) : 0u;
     const int first = blockIdx.x, stride = gridDim.x;
     if (tid == 0) {
         if (first < ta.ntiles) issue_tile<St>(ta, stages, &bars[0], first, BR);
@@ -271,14 +271,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_step_tma(const __grid_con
         LR m[8];
         fold_moments<N, LR>(a, red, G, lane, m);
         LR n, eps, U0, Ux, Uy;
-        const bool ok = landau_fast<LR>(m, n, eps, U0, Ux, Uy);
+        const bool ok = site_landau<St, LR>(m, n, eps, U0, Ux, Uy);
         const LR T = eps / (LR(2) * n);
         if (!ok && act && g == 0) atomicOr(a.status, 1);
         R cr[NC];
         shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
         const LR itau = Par<LR>::inv_tau(a);
         const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
-        constexpr bool kSR = sizeof(St) == 2;
+        constexpr bool kSR = sizeof(St) <= 4; // FP32 and 16-bit stores round stochastically
         unsigned rng = 0;
         if (kSR) rng = mix32(unsigned(site) * 64u + unsigned(g) ^ step_seed);
 #pragma unroll
@@ -294,16 +294,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_step_tma(const __grid_con
 #pragma unroll
                 for (int u = 1; u < NC; ++u) feq += cr[u] * E[u];
                 const R om = o0 - o1 * c - o2 * s;
-                const R out = fs[k] + om * (feq - fs[k]);
-                if (kSR) {
-                    if (act) SR<St>::st(obase + (long long)k * S, out, rng);
-                } else if (act) {
-                    Io<St, R>::st(obase + (long long)k * S, out);
-                }
+                if (act) relax_store<St, R>(obase + (long long)k * S, fs[k], om, feq, rng);
             }
         }
     }
-    if (sizeof(St) == 2) {
+    if (sizeof(St) <= 4) {
         __syncthreads();
         if (tid == 0) advance_launch_counter(a.ctr, gridDim.x);
     }

@@ -401,7 +401,7 @@ class Simulation:
         one group per warp, see rlbm_population_groups)."""
         return lib().rlbm_population_groups(self._h)
 
-    KERNELS = ("per-tile", "tma", "pair", "pair-bulk")
+    KERNELS = ("per-tile", "tma", "pair", "pair-bulk", "pair-tma")
 
     @property
     def step_kernel(self) -> str:
@@ -562,10 +562,35 @@ class Batch:
             pass
 
 
+def _check_noalloc_tensors(nx, ny, N, K, precision, fin, fout):
+    """The C entry point cannot see buffer sizes: check the tensors here, on
+    the host, before anything is launched (dtype and size first, so that the
+    checks also run without a GPU)."""
+    import torch
+    want = {"fp64": torch.float64, "fp32": torch.float32}.get(precision)
+    if want is None:
+        raise RLBMError(ERR_UNSUPPORTED, f"rlbm_step_noalloc supports fp64 and fp32 storage, not {precision}")
+    count = int(K) * (int(N) + 1) * int(nx) * int(ny)
+    for name, t in (("fin", fin), ("fout", fout)):
+        if not isinstance(t, torch.Tensor):
+            raise RLBMError(ERR_ARG, f"{name} must be a torch tensor")
+        if t.dtype != want:
+            raise RLBMError(ERR_ARG, f"{name} has dtype {t.dtype}, {precision} storage needs {want}")
+        if t.numel() != count:
+            raise RLBMError(ERR_ARG, f"{name} holds {t.numel()} elements, need K (N+1) nx ny = {count}")
+        if not t.is_contiguous():
+            raise RLBMError(ERR_ARG, f"{name} must be contiguous")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise RLBMError(ERR_ARG, f"{name} must be a CUDA tensor on the current device")
+
+
 def step_noalloc(nx, ny, N, K, tau, precision, fin, fout, bcx=BC_COPYOUT, bcy=BC_PERIODIC,
                  stream=None):
     """One step from device tensor fin to device tensor fout through the
-    allocation-free entry point (the library allocates no device memory)."""
+    allocation-free entry point (the library allocates no device memory).
+    fin and fout: contiguous CUDA tensors on the current device, float64 for
+    'fp64' / float32 for 'fp32', of K (N+1) nx ny elements each."""
+    _check_noalloc_tensors(nx, ny, N, K, precision, fin, fout)
     st = lib().rlbm_step_noalloc(Grid(nx, ny, bcx, bcy), int(N), int(K), float(tau),
                                  PRECISIONS[precision], _vp(fin.data_ptr()), _vp(fout.data_ptr()),
                                  _vp(stream.cuda_stream if stream is not None else 0))

@@ -174,3 +174,27 @@ def test_onlattice_and_statistics_validation_without_gpu(lib):
     assert lib.rlbm_statistics(None) == -2
     assert lib.rlbm_is_onlattice(None) == -1
     assert lib.rlbm_population_groups(None) == -1
+
+
+def test_noalloc_binding_checks_tensors_before_any_launch():
+    """The allocation-free step cannot see buffer sizes on the C side: the
+    binding refuses a wrong dtype, a wrong element count, a non-contiguous
+    tensor or host memory before it calls into the library (no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    from paper_2011_06856_gb300 import rlbm as R
+    nx, ny, N, K = 8, 2, 2, 16
+    count = K * (N + 1) * nx * ny
+    good = torch.zeros(count, dtype=torch.float32)
+    cases = [
+        (torch.zeros(count, dtype=torch.float64), good, "dtype"),
+        (torch.zeros(count - 1, dtype=torch.float32), good, "elements"),
+        (torch.zeros(2 * count, dtype=torch.float32)[::2], good, "contiguous"),
+        (good, good.clone(), "CUDA"),
+    ]
+    for fin, fout, needle in cases:
+        with pytest.raises(R.RLBMError) as e:
+            R.step_noalloc(nx, ny, N, K, 1.0, "fp32", fin, fout)
+        assert e.value.status == R.ERR_ARG and needle in str(e.value), (needle, str(e.value))
+    with pytest.raises(R.RLBMError) as e:
+        R.step_noalloc(nx, ny, N, K, 1.0, "fp16", good, good.clone())
+    assert e.value.status == R.ERR_UNSUPPORTED

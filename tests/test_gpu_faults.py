@@ -83,3 +83,29 @@ def test_bulk_staged_pair_kernel_timeout_reports_and_context_survives():
     sim.set_tiling(8, "pair")  # no device waits in this form
     with pytest.raises(R.RLBMError):
         sim.test_stall_next_step()
+
+
+def test_tile_staged_pair_kernel_timeout_reports_and_context_survives():
+    """The tile-staged form: its mbarrier expects 16 bytes more than the TMA
+    brings, the bounded wait runs out, the CTA drains (bounded) and returns
+    without storing; the host reads RLBM_ERR_TIMEOUT and the handle keeps
+    working."""
+    nx, ny, N, K, tau = 256, 3, 2, 16, 3.0
+    sim = R.Simulation(nx, ny, N, K, tau, "fp32", W.BC_COPYOUT, W.BC_PERIODIC)
+    sim.set_tiling(16, "pair-tma")
+    assert sim.step_kernel == "pair-tma"
+    fl = W.random_fields(nx, ny, seed=2)
+    sim.init_fields(fl)
+    sim.set_wait_limit(2_000_000)
+    sim.test_stall_next_step()
+    sim.step(1)
+    with pytest.raises(R.DeviceTimeout):
+        sim.sync()
+    q = O.Quadrature(N, K)
+    f0 = q.init(fl.n, fl.T, fl.bx, fl.by)
+    sim.set_populations(f0.astype(np.float32))
+    sim.step(5)
+    sim.sync()
+    ref, _ = q.run(f0, tau, 5, W.BC_COPYOUT, W.BC_PERIODIC)
+    got = sim.get_populations().astype(np.float64)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-5

@@ -3,7 +3,7 @@ length 5 on the 4 shells of N = 3, perfect streaming) against the FP64 oracle.
 
 Free streaming is an exact copy, so it is compared bit for bit; steps with a
 collision to 1e-12 normwise in FP64 and to the FP32 bound of the other parity
-tests, max(1e-5, b omega_max steps) with b = 4e-7.
+tests, 1e-5.
 """
 import math
 
@@ -96,7 +96,7 @@ def test_onlattice_fp32_paper_2d_states():
     sim.autotune(2)
     sim.step(steps)
     mac = sim.moments()
-    tol = max(1e-5, 4e-7 * 1.2 / tau * steps)
+    tol = 1e-5
     for i in range(4):
         assert relerr(mac[i], mac_ref[i]) < tol, i
 

@@ -4,12 +4,12 @@ Tolerances (normwise, max|gpu - oracle| / max|oracle| per field; the two
 spatial velocity components share the scale max |U^i|):
 
 * FP64 storage and arithmetic: 1e-12.
-* FP32: max(1e-5, b * omega_max * steps) with b = 4e-7.  The FP32 equilibrium
-  carries its conserved moments only to a relative bias b per step (the
-  radial projection cancels about one digit; b was measured by emulating the
-  per-site arithmetic in float32 against the oracle).  The collision feeds a
-  fraction omega = p.U / (p^0 tau) of that bias into the state every step,
-  and conserved quantities do not relax, so it accumulates linearly.
+* FP32 storage: 1e-5, the bound stated for the FP32 path.  Its per-site part
+  (moment fold, Landau frame, equilibrium coefficients) runs at FP64-class
+  accuracy; in FP32 it would carry the conserved moments to a relative bias
+  of about 4e-7 per step, which the collision accumulates linearly (conserved
+  quantities do not relax) and which would exceed 1e-5 within a few hundred
+  steps at tau ~ 4.
 * 16-bit storage with stochastic rounding: 1e-3 for n and eps with FP16
   (unit roundoff u = 2^-11), 8e-3 with BF16 (u = 2^-8); beta 3x that.
   Stochastic rounding makes the per-store error zero-mean, so conserved
@@ -35,12 +35,6 @@ from paper_2011_06856_gb300 import rlbm as R  # noqa: E402
 B.build()
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 8e-3, "fp16n": 1e-3, "bf16n": 8e-3}
-FP32_BIAS = 4e-7
-
-
-def fp32_tol(tau, steps, umax=1.2):
-    """max(1e-5, b * omega_max * steps), omega_max = (U^0 + |U|) / tau."""
-    return max(1e-5, FP32_BIAS * umax / tau * steps)
 
 
 def relerr(a, b):
@@ -263,26 +257,48 @@ def test_fp64_2048sq_sampled_one_step():
 
 # ------------------------------------------------------------ FP32 and 16-bit storage
 
-def test_fp32_shock_tube_400x1():
+def gpu_run_kernel(N, K, fields, tau, steps, bcx, bcy, precision, kernel, P):
+    """gpu_run in a chosen step kernel: "default" (the handle's kernel after
+    rlbm_create: TMA-staged or per-tile, FP64 per-site part for FP32 storage)
+    or "pair" (two sites per lane, double-float per-site part) with P."""
+    ny, nx = fields.shape
+    sim = R.Simulation(nx, ny, N, K, tau, precision, bcx, bcy)
+    if kernel != "default":
+        sim.set_tiling(P, kernel)
+    sim.init_fields(fields)
+    sim.step(steps)
+    return sim, sim.moments()
+
+
+@pytest.mark.parametrize("kernel", ["default", "pair"])
+def test_fp32_shock_tube_400x1(kernel):
+    """The 400x1 shock tube (N=2 x K=16, Kn = 0.01 -> tau = 4, 400 steps) in FP32
+    storage within 1e-5 of the FP64 oracle: at tau = 4 an FP32 per-site part
+    would drift past 1e-5 (bias about 4e-7 per step times omega ~ 1/4)."""
     nx, N, K, steps = 400, 2, 16, 400
     tau = W.tau_from_kn(0.01, nx)
     fl = W.shock_tube(nx, 1)
     _, _, mac_ref, _ = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
-    _, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
-    errs = assert_fields_close(mac, mac_ref, fp32_tol(tau, steps), "fp32 400x1")
-    print("fp32 400x1", {k: f"{v:.2e}" for k, v in errs.items()})
+    _, mac = gpu_run_kernel(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32", kernel, 16)
+    errs = assert_fields_close(mac, mac_ref, TOL["fp32"], f"fp32 400x1 {kernel}")
+    print("fp32 400x1", kernel, {k: f"{v:.2e}" for k, v in errs.items()})
 
 
+@pytest.mark.parametrize("kernel", ["default", "pair"])
 @pytest.mark.parametrize("kn", [0.01, 0.1, 1.0, 10.0])
-def test_fp32_8192x4_N3K64_reduced_steps(kn):
-    """Config shape 8192x4, N=3 x K=64, each Kn, 200 steps (full 4000 in the benchmark)."""
+def test_fp32_8192x4_N3K64_reduced_steps(kn, kernel):
+    """Config shape 8192x4, N=3 x K=64, each Kn, 200 steps (the full 4000 at
+    Kn = 0.01 in test_gpu_configs)."""
     nx, ny, N, K, steps = 8192, 4, 3, 64, 200
     tau = W.tau_from_kn(kn, nx)
     fl = W.shock_tube(nx, ny)
-    _, _, mac_ref, flagged = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
-    assert flagged == 0
-    _, mac = gpu_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32")
-    assert_fields_close(mac, mac_ref, fp32_tol(tau, steps), f"fp32 Kn={kn}")
+    if ("mac200", kn) not in _SHOCK_STATE:
+        _, _, mac_ref, flagged = oracle_run(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC)
+        assert flagged == 0
+        _SHOCK_STATE["mac200", kn] = mac_ref
+    mac_ref = _SHOCK_STATE["mac200", kn]
+    _, mac = gpu_run_kernel(N, K, fl, tau, steps, W.BC_COPYOUT, W.BC_PERIODIC, "fp32", kernel, 32)
+    assert_fields_close(mac, mac_ref, TOL["fp32"], f"fp32 Kn={kn} {kernel}")
 
 
 @pytest.mark.parametrize("precision", ["fp16", "bf16", "fp16n", "bf16n"])

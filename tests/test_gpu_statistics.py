@@ -73,7 +73,7 @@ def test_quantum_fp32_storage(stat):
     sim.set_statistics(NAMES[stat], g)
     sim.init_fields(fl)
     sim.step(steps)
-    tol = max(1e-5, 4e-7 * 1.2 / tau * steps)
+    tol = 1e-5
     assert relerr(sim.get_populations().astype(np.float64), ref) < tol
 
 
