@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--timesteps", type=int, default=None,
                     help="override time steps per problem (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["per-tile", "tma", "pair", "pair-bulk"],
+    ap.add_argument("--kernel", default=None, choices=["per-tile", "tma", "pair", "pair-bulk", "pair-tma"],
                     help="pin the step kernel (with --tile-p) instead of autotuning; for profiling runs")
     ap.add_argument("--tile-p", type=int, default=None, help="populations per warp with --kernel")
     return ap.parse_args()
@@ -519,7 +519,8 @@ def main():
     tiling = {"populations_per_warp": sims[0].tile_populations, "kernel": sims[0].step_kernel,
               "population_groups_per_warp": sims[0].population_groups}
     kernel_names = {"per-tile": "rlbm_kernel<MODE_STEP>", "tma": "rlbm_step_tma",
-                    "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)"}
+                    "pair": "rlbm_pair_kernel", "pair-bulk": "rlbm_pair_kernel (bulk-staged)",
+                    "pair-tma": "rlbm_pair_tma_kernel"}
 
     def kernel_name(sim):
         if sim.statistics != "mj":

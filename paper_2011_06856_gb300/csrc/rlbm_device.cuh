@@ -357,7 +357,7 @@ __device__ __forceinline__ bool landau_dd(const df64 *m, df64 &n, df64 &eps, df6
         const df64 P = (lam * lam + c1) * lam - c0;
         const float dP = __fmaf_rn(3.f * lam.hi, lam.hi, c1.hi);
         if (!(dP > 0.f)) break;
-        lam = lam - __fdiv_rn(P.hi, dP);
+        lam = lam - __fdividef(P.hi, dP);
     }
     eps = lam;
     const df64 bx = Txx + lam, by = Tyy + lam;
@@ -402,13 +402,33 @@ __device__ __forceinline__ bool landau_f32dd(const float *m, float &n, float &ep
     return ok;
 }
 
+// The Landau frame for FP32 per-site arithmetic, refined in double-float where
+// T^ab is close to degenerate.  The FP32 root of the characteristic cubic
+// carries a relative error of about u_32 (E / eps)^3 / (P'(eps) / eps^2) (E =
+// T^tt; P' = 3 eps^2 + c1 is (eps + P)^2 = 2.25 eps^2 for a fluid at rest): it
+// grows like gamma^6 with the boost and blows up near a double root.  Where
+// E > 3 eps (gamma^2 above ~2.3), P'(eps) < eps^2 / 2, or the FP32 solve failed,
+// the frame is solved again in double-float (landau_f32dd); elsewhere the FP32
+// frame is accurate to a few 1e-7, far below the rounding of 16-bit storage.
+__device__ __forceinline__ bool landau_f32_adaptive(const float *m, float &n, float &eps, float &U0, float &Ux,
+                                                    float &Uy)
+{
+    bool ok = landau_fast<float>(m, n, eps, U0, Ux, Uy);
+    const float E = m[3], Ttx = m[4], Tty = m[5], Txx = m[6], Txy = m[7];
+    const float c1 = -E * E + Ttx * Ttx + Tty * Tty + Txx * (E - Txx) - Txy * Txy;
+    const bool refine = !ok || E > 3.f * eps || 3.f * eps * eps + c1 < 0.5f * eps * eps;
+    if (refine) ok = landau_f32dd(m, n, eps, U0, Ux, Uy);
+    return ok;
+}
+
 // The Landau solve of a kernel with storage St and per-site type LR: 16-bit
-// storage with FP32 per-site arithmetic solves the frame in double-float, every
-// other combination in LR itself (FP64, or FP32 where nothing else applies).
+// storage with FP32 per-site arithmetic refines the FP32 frame in
+// double-float where T^ab is near-degenerate (landau_f32_adaptive); every other
+// combination solves it in LR itself (FP64 for FP32 and FP64 storage).
 template <class St, class LR>
 __device__ __forceinline__ bool site_landau(const LR *m, LR &n, LR &eps, LR &U0, LR &Ux, LR &Uy)
 {
-    if constexpr (sizeof(St) == 2 && sizeof(LR) == 4) return landau_f32dd(m, n, eps, U0, Ux, Uy);
+    if constexpr (sizeof(St) == 2 && sizeof(LR) == 4) return landau_f32_adaptive(m, n, eps, U0, Ux, Uy);
     else return landau_fast<LR>(m, n, eps, U0, Ux, Uy);
 }
 

@@ -48,12 +48,13 @@ __device__ __forceinline__ df64 two_prod(float a, float b)
     return {p, __fmaf_rn(a, b, -p)};
 }
 
+// Sum with one TwoSum of the high parts and the low parts added in FP32: its
+// error is below about 2 u^2 (|x| + |y|) (u = 2^-24), the bound of FP64
+// arithmetic on operands that carry rounding errors of their own.
 __device__ __forceinline__ df64 operator+(df64 x, df64 y)
 {
     const df64 s = two_sum(x.hi, y.hi);
-    const df64 t = two_sum(x.lo, y.lo);
-    df64 u = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return fast_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 __device__ __forceinline__ df64 operator-(df64 x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
@@ -91,7 +92,7 @@ __device__ __forceinline__ df64 dd_sqrt(df64 x)
     if (!(x.hi > 0.f)) return {0.f, 0.f};
     const float s = __fsqrt_rn(x.hi);
     const df64 res = x - two_prod(s, s);
-    return fast_two_sum(s, __fdiv_rn(res.hi, __fadd_rn(s, s)));
+    return fast_two_sum(s, __fdividef(res.hi, __fadd_rn(s, s)));
 }
 
 // 1 / sqrt(x): y = rsqrt(x) in FP32, then y + y (1 - x y^2) / 2
@@ -162,9 +163,7 @@ __device__ __forceinline__ df2 p_fast_two_sum(float2 a, float2 b)
 __device__ __forceinline__ df2 operator+(df2 x, df2 y)
 {
     const df2 s = p_two_sum(x.hi, y.hi);
-    const df2 t = p_two_sum(x.lo, y.lo);
-    const df2 u = p_fast_two_sum(s.hi, padd(s.lo, t.hi));
-    return p_fast_two_sum(u.hi, padd(u.lo, t.lo));
+    return p_fast_two_sum(s.hi, padd(s.lo, padd(x.lo, y.lo)));
 }
 __device__ __forceinline__ df2 operator-(df2 x, df2 y) { return x + df2{pneg(y.hi), pneg(y.lo)}; }
 // x * (b_hi + b_lo) for a scalar double-float b (the same for both sites)

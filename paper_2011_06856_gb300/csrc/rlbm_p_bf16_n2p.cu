@@ -1,4 +1,4 @@
-// Two-sites-per-lane step kernel instances: BF16 storage, FP32 accumulation, double-float Landau frame, N = 2, plain loads.
+// Two-sites-per-lane step kernel instances: BF16 storage, FP32 accumulation, Landau frame refined in double-float where T^ab is near-degenerate, N = 2, plain loads.
 #include "rlbm_pair.cuh"
 namespace rlbmk {
 cudaError_t launch_pair_bf16_n2p(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -1,4 +1,4 @@
-// Two-sites-per-lane step kernel instances: FP16 storage, FP32 accumulation, double-float Landau frame, N = 2, bulk-staged first pass.
+// Two-sites-per-lane step kernel instances: FP16 storage, FP32 accumulation, Landau frame refined in double-float where T^ab is near-degenerate, N = 2, bulk-staged first pass.
 #include "rlbm_pair.cuh"
 namespace rlbmk {
 cudaError_t launch_pair_f16_n2b(int PP, bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,

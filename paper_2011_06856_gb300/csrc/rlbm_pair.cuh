@@ -64,10 +64,10 @@ __device__ __forceinline__ bool pbar_try_wait(unsigned bar, unsigned parity)
 {
     unsigned ok;
     asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(ok)
-                 : "r"(bar), "r"(parity)
+                 : "r"(bar), "r"(parity), "r"(kWaitHintNs)
                  : "memory");
     return ok != 0;
 }
@@ -183,16 +183,19 @@ __device__ __forceinline__ float2 relax_pair_sr(float2 fs, float2 om, float2 feq
     return __fadd2_rn(r, __ffma2_rn(u, ulp, e));
 }
 
-// 32 random bits from the thread's LCG stream, high bits folded into the low ones
-__device__ __forceinline__ unsigned next_bits(unsigned &rng)
+// 32 random bits from the thread's LCG stream: the high halves of two draws
+// (the low bits of a power-of-two LCG have short periods; each 16-bit half
+// of the result feeds the rounding of one site)
+__device__ __forceinline__ unsigned next_bits2(unsigned &rng)
 {
-    lcg_next(rng);
-    return rng ^ (rng >> 15);
+    const unsigned a = lcg_next(rng), b = lcg_next(rng);
+    return __byte_perm(a, b, 0x7632);
 }
 
 // The per-site part for site s of the tile with FP32 accumulation (16-bit
-// storage): moments from the warps' angular sums, the Landau frame in
-// double-float (landau_f32dd), and the shell-independent part of the
+// storage): moments from the warps' angular sums, the Landau frame in FP32,
+// refined in double-float where T^ab is near-degenerate
+// (landau_f32_adaptive), and the shell-independent part of the
 // equilibrium coefficients (the boosted-direction sums acc, weighted by
 // n T^(k-1)), written to sres[row 64 + s]; then U^a / tau at rows
 // (N+1)^2 + 0..2.  Every warp forms its own shell's coefficients from these.
@@ -227,7 +230,7 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
         m[7] += f2v * pcs;
     }
     float n, eps, U0, Ux, Uy;
-    const bool ok = landau_f32dd(m, n, eps, U0, Ux, Uy);
+    const bool ok = landau_f32_adaptive(m, n, eps, U0, Ux, Uy);
     const float T = eps / (2.f * n);
     if (!ok && act) atomicOr(a.status, 1);
     // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
@@ -683,7 +686,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
         const float2 feq = __fmul2_rn(wq, pe);
         const float2 om = __ffma2_rn(no2, sn, __ffma2_rn(no1, c, o0));
         if constexpr (sizeof(St) == 4) {
-            const float2 out = relax_pair_sr(fs[k], om, feq, next_bits(rng));
+            const float2 out = relax_pair_sr(fs[k], om, feq, next_bits2(rng));
             if (act && good) *reinterpret_cast<float2 *>(ob + (long long)k * S) = out;
         } else {
             const float2 out = __ffma2_rn(om, f2sub(feq, fs[k]), fs[k]);
@@ -835,7 +838,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_gr
             }
             const float2 feq = __fmul2_rn(wq, pe);
             const float2 om = __ffma2_rn(no2, sn, __ffma2_rn(no1, c, o0));
-            const float2 out = relax_pair_sr(fs[k], om, feq, next_bits(rng));
+            const float2 out = relax_pair_sr(fs[k], om, feq, next_bits2(rng));
             if (act) *reinterpret_cast<float2 *>(ob + (long long)k * S) = out;
         }
     }

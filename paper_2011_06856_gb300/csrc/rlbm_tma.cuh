@@ -49,10 +49,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
 {
     unsigned ok;
     asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
                  : "memory");
     return ok != 0;
 }
