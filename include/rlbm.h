@@ -218,13 +218,12 @@ long long rlbm_kernel_launches(const rlbm_t *h);
  * nx even, K a multiple of P in {8, 12, 16, 24, 32}, at most 16 warps),
  * 3 = the same with its first pass staged through shared memory by
  * cp.async.bulk on interior tiles (row pitch a multiple of 16 bytes; bounded
- * mbarrier waits), 4 = the same arithmetic in persistent CTAs that stage
- * whole 64-site tiles into shared memory by TMA (cp.async.bulk.tensor: the
+ * mbarrier waits), 4 = the same arithmetic with the whole 64-site tile staged
+ * into shared memory by TMA at the CTA's start (cp.async.bulk.tensor: the
  * centre row and the upwind pull row of every population, the pull rows in
- * chunks of 4 or 8 populations that share sgn(v_y)) through one or two
- * stages, the next tile loading while this one is computed (row pitch a
- * multiple of 16 bytes, nx >= 64 + 32 bytes of halo, one population group;
- * bounded mbarrier waits; 16-bit stores round stochastically with cvt.rs),
+ * chunks of 4 or 8 populations that share sgn(v_y); row pitch a multiple of
+ * 16 bytes, nx >= 64 + 32 bytes of halo, one population group; bounded
+ * mbarrier wait; 16-bit stores round stochastically with cvt.rs),
  * 0 = per-tile kernel. */
 int rlbm_step_kernel_variant(const rlbm_t *h);
 

@@ -209,23 +209,22 @@ struct alignas(128) PairTmaArgs {
     KernelArgs a;
     int CB, ncbox;    // populations per centre box, boxes per tile (CB ncbox = npop)
     int DB, npbox;    // populations per pull-row chunk, chunks per tile (DB npbox = npop)
-    int nst;          // shared-memory stages (1 or 2) each CTA cycles its tiles through
     unsigned long long chunk_up[4]; // bit c: chunk c pulls from row y - 1 (its v_y >= 0), else y + 1
 };
 
-// Shared-memory layout of rlbm_pair_tma_kernel: nst stages, each a staged
-// tile (centre rows, then pull rows in 2D: [rows][npop][BW] storage elements,
-// BW = 64 sites + 16 bytes of halo on each side), the angular sums [5][G][64],
-// the per-site results [pair_site_rows(N)][64], one mbarrier per stage; + 1 KB
-// of slack to align the base for the TMA.
+// Shared-memory layout of rlbm_pair_tma_kernel: the staged tile (centre rows,
+// then pull rows in 2D: [rows][npop][BW] storage elements, BW = 64 sites +
+// 16 bytes of halo on each side), the pair table [npop][3] float4, the
+// angular sums [5][G][64], the per-site results [pair_site_rows(N)][64], the
+// mbarrier; + 1 KB of slack to align the base for the TMA.
 struct PairTmaSmem {
-    size_t stage, stage_bytes, red, sres, bar, total;
-    __host__ __device__ PairTmaSmem(int N, int G, int npop, int es, bool two_d, int nst)
+    size_t stage, tab, red, sres, bar, total;
+    __host__ __device__ PairTmaSmem(int N, int G, int npop, int es, bool two_d)
     {
         const size_t BW = size_t(kPairSites) + 2 * size_t(16 / es);
         stage = 0;
-        stage_bytes = align_up(size_t(two_d ? 2 : 1) * size_t(npop) * BW * size_t(es), 128);
-        red = size_t(nst) * stage_bytes;
+        tab = align_up(size_t(two_d ? 2 : 1) * size_t(npop) * BW * size_t(es), 128);
+        red = align_up(tab + size_t(npop) * 3 * 16, 16);
         sres = red + size_t(5) * G * kPairSites * 4;
         bar = align_up(sres + size_t(pair_site_rows(N)) * kPairSites * 4, 16);
         total = bar + 16 + 1024;
@@ -233,16 +232,16 @@ struct PairTmaSmem {
 };
 
 #define RLBM_DECLARE_PAIR_TMA(name)                                                                      \
-    cudaError_t launch_pair_tma_##name##_n2(int PP, bool two_d, int grid, dim3 block, size_t smem,       \
+    cudaError_t launch_pair_tma_##name##_n2(int PP, bool two_d, dim3 block, size_t smem,       \
                                             cudaStream_t st, const PairTmaArgs &ta, int *bps);           \
-    cudaError_t launch_pair_tma_##name##_n3(int PP, bool two_d, int grid, dim3 block, size_t smem,       \
+    cudaError_t launch_pair_tma_##name##_n3(int PP, bool two_d, dim3 block, size_t smem,       \
                                             cudaStream_t st, const PairTmaArgs &ta, int *bps);           \
-    inline cudaError_t launch_pair_tma_##name(int N, int PP, bool two_d, int grid, dim3 block,           \
+    inline cudaError_t launch_pair_tma_##name(int N, int PP, bool two_d, dim3 block,           \
                                               size_t smem, cudaStream_t st, const PairTmaArgs &ta,       \
                                               int *bps)                                                  \
     {                                                                                                    \
-        if (N == 2) return launch_pair_tma_##name##_n2(PP, two_d, grid, block, smem, st, ta, bps);       \
-        if (N == 3) return launch_pair_tma_##name##_n3(PP, two_d, grid, block, smem, st, ta, bps);       \
+        if (N == 2) return launch_pair_tma_##name##_n2(PP, two_d, block, smem, st, ta, bps);       \
+        if (N == 3) return launch_pair_tma_##name##_n3(PP, two_d, block, smem, st, ta, bps);       \
         return cudaErrorInvalidValue;                                                                    \
     }
 RLBM_DECLARE_PAIR_TMA(f32)

@@ -282,7 +282,6 @@ struct rlbm {
     bool use_pair_tma = false;          // ... with the whole tile staged by TMA (rlbm_pair_tma.cuh)
     rlbmk::PairTmaArgs *ptma = nullptr; // [2]: input buffer 0 / 1
     size_t ptma_smem = 0;
-    int ptma_grid = 0;                  // persistent CTAs of the tile-staged kernel
     long long wait_cycles = 4000000000LL; // bound of the device waits (about 2 s at the maximum clock)
     std::string err;
 };
@@ -668,23 +667,23 @@ cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
     return e;
 }
 
-// grid <= 0 with bps set: only the occupancy query (CTAs per SM)
-cudaError_t launch_pair_tma_raw(rlbm_t *h, const rlbmk::PairTmaArgs &ta, int grid, int *bps)
+// with bps set: only the occupancy query (CTAs per SM)
+cudaError_t launch_pair_tma_raw(rlbm_t *h, const rlbmk::PairTmaArgs &ta, int *bps)
 {
     const dim3 block(32, h->G);
     const bool two_d = h->grid.ny > 1;
     switch (h->prec) {
-    case RLBM_FP32: return rlbmk::launch_pair_tma_f32(h->N, h->P, two_d, grid, block, h->ptma_smem, h->stream, ta, bps);
+    case RLBM_FP32: return rlbmk::launch_pair_tma_f32(h->N, h->P, two_d, block, h->ptma_smem, h->stream, ta, bps);
     case RLBM_FP16_DEV:
     case RLBM_FP16_NORM:
-        return rlbmk::launch_pair_tma_f16(h->N, h->P, two_d, grid, block, h->ptma_smem, h->stream, ta, bps);
-    default: return rlbmk::launch_pair_tma_bf16(h->N, h->P, two_d, grid, block, h->ptma_smem, h->stream, ta, bps);
+        return rlbmk::launch_pair_tma_f16(h->N, h->P, two_d, block, h->ptma_smem, h->stream, ta, bps);
+    default: return rlbmk::launch_pair_tma_bf16(h->N, h->P, two_d, block, h->ptma_smem, h->stream, ta, bps);
     }
 }
 
 cudaError_t launch_pair_tma(rlbm_t *h, const rlbmk::PairTmaArgs &ta)
 {
-    cudaError_t e = launch_pair_tma_raw(h, ta, h->ptma_grid, nullptr);
+    cudaError_t e = launch_pair_tma_raw(h, ta, nullptr);
     if (e == cudaSuccess) ++h->launches;
     return e;
 }
@@ -875,13 +874,7 @@ rlbm_status setup_pair_tma(rlbm_t *h)
     RLBM_CUDA(h, cudaGetDevice(&dev));
     RLBM_CUDA(h, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     RLBM_CUDA(h, cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    // two stages (the next tile loads during this one) where they fit, else one
-    int nst = 2;
-    size_t need = rlbmk::PairTmaSmem(h->N, h->G, npop, int(es), two_d, 2).total;
-    if (need > size_t(max_smem)) {
-        nst = 1;
-        need = rlbmk::PairTmaSmem(h->N, h->G, npop, int(es), two_d, 1).total;
-    }
+    const size_t need = rlbmk::PairTmaSmem(h->N, h->G, npop, int(es), two_d).total;
     if (need > size_t(max_smem)) return RLBM_OK;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult qres;
@@ -920,20 +913,17 @@ rlbm_status setup_pair_tma(rlbm_t *h)
         ta.ncbox = ncbox;
         ta.DB = DB;
         ta.npbox = npop / DB;
-        ta.nst = nst;
         std::memcpy(ta.chunk_up, up, sizeof(up));
     }
     h->ptma_smem = need;
     int bps = 0;
-    cudaError_t e = launch_pair_tma_raw(h, h->ptma[0], 0, &bps);
+    cudaError_t e = launch_pair_tma_raw(h, h->ptma[0], &bps);
     if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query of the tile-staged step kernel");
     if (bps < 1) {
         delete[] h->ptma;
         h->ptma = nullptr;
         return RLBM_OK;
     }
-    const long long ntiles = (long long)((nx + rlbmk::kPairSites - 1) / rlbmk::kPairSites) * ny;
-    h->ptma_grid = int(std::min<long long>(ntiles, (long long)bps * h->sm_count));
     h->use_pair_tma = true;
     return RLBM_OK;
 }
