@@ -112,7 +112,8 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h", "rlbm_pair.cuh", "rlbm_df64.cuh"):
+    for f in ("rlbm_device.cuh", "rlbm_launch.cuh", "rlbm_args.h", "rlbm_pair.cuh", "rlbm_df64.cuh",
+              "rlbm_pair_tma.cuh", "rlbm_tma.cuh"):
         with open(os.path.join(ROOT, "paper_2011_06856_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
