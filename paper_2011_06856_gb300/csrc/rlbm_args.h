@@ -64,6 +64,16 @@ struct KernelArgs {
 
 __host__ __device__ constexpr int tab_width(int N) { return ((2 * N + 5) + 3) / 4 * 4; }
 
+// Dynamic shared memory of the per-tile kernel (rlbm_kernel): the angular sums
+// [5][G][32] in the per-site type (ls bytes), then either the per-site sums
+// shared by the warps when the per-site part runs once per site in FP64
+// [(N+1)^2 + 3][32] or, for the quantum statistics, (eta, T) [2][32] doubles.
+__host__ __device__ constexpr size_t tile_smem_bytes(int N, int G, size_t ls, bool quantum)
+{
+    return ls * 5 * size_t(G) * 32 +
+           (quantum ? 2 * 32 * sizeof(double) : (ls == 8 ? size_t((N + 1) * (N + 1) + 3) * 32 * 8 : 0));
+}
+
 // Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory:
 // angular sums [5][G][64] and the per-site results [2 (N+1)^2 + 3][64] (FP32;
 // the (N+1)^2 shell-independent equilibrium sums as double-floats, hi and lo

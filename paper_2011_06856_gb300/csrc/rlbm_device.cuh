@@ -503,6 +503,77 @@ __device__ __forceinline__ void shell_coefficients_tk(const KernelArgs &a, int r
     }
 }
 
+// The same in two halves, for kernels that solve each site once and share the
+// result: site_sums forms the shell-independent sums w_{m,k} = tk[k] acc_{m,k}
+// ((N+1)^2 rows: Re for m = 0..N, k = m..N, then Im for m = 1..N, k = m..N),
+// shell_from_sums combines them into shell r's coefficients (w[row * ws]).
+template <int N, class LR>
+__device__ __forceinline__ void site_sums(const KernelArgs &a, const LR *tk, LR U0, LR Ux, LR Uy, LR *w, int ws)
+{
+    LR accr[N + 1][N + 1], acci[N + 1][N + 1];
+#pragma unroll
+    for (int m = 0; m <= N; ++m)
+#pragma unroll
+        for (int k = 0; k <= N; ++k) { accr[m][k] = LR(0); acci[m][k] = LR(0); }
+    const LR inv1g = LR(1) / (LR(1) + U0);
+#pragma unroll
+    for (int j = 0; j <= N; ++j) {
+        const LR cj = Par<LR>::smp_c(a, j), sj = Par<LR>::smp_s(a, j);
+        const LR un = Ux * cj + Uy * sj;
+        const LR q0 = U0 + un;
+        const LR h = LR(1) + un * inv1g;
+        const LR zr = cj + Ux * h, zi = sj + Uy * h;
+        LR qp[N + 1], pr[N + 1], pi[N + 1];
+        qp[0] = LR(1);
+        pr[0] = LR(1);
+        pi[0] = LR(0);
+#pragma unroll
+        for (int t = 1; t <= N; ++t) {
+            qp[t] = qp[t - 1] * q0;
+            pr[t] = pr[t - 1] * zr - pi[t - 1] * zi;
+            pi[t] = pr[t - 1] * zi + pi[t - 1] * zr;
+        }
+#pragma unroll
+        for (int m = 0; m <= N; ++m)
+#pragma unroll
+            for (int k = m; k <= N; ++k) {
+                accr[m][k] += qp[k - m] * pr[m];
+                acci[m][k] += qp[k - m] * pi[m];
+            }
+    }
+    int row = 0;
+#pragma unroll
+    for (int m = 0; m <= N; ++m)
+#pragma unroll
+        for (int k = m; k <= N; ++k) w[(row++) * ws] = tk[k] * accr[m][k];
+#pragma unroll
+    for (int m = 1; m <= N; ++m)
+#pragma unroll
+        for (int k = m; k <= N; ++k) w[(row++) * ws] = tk[k] * acci[m][k];
+}
+
+template <int N, class LR, class R>
+__device__ __forceinline__ void shell_from_sums(const KernelArgs &a, int r, const LR *w, int ws, R *cr)
+{
+    const LR *rt = reinterpret_cast<const LR *>(a.rtab) + r * (N + 1) * (N + 1);
+    int row = 0;
+#pragma unroll
+    for (int m = 0; m <= N; ++m) {
+        LR cre = LR(0);
+#pragma unroll
+        for (int k = m; k <= N; ++k) cre += __ldg(rt + m * (N + 1) + k) * w[(row++) * ws];
+        if (m == 0) cr[0] = R(cre - Par<LR>::feq_off(a));
+        else cr[2 * m - 1] = R(cre);
+    }
+#pragma unroll
+    for (int m = 1; m <= N; ++m) {
+        LR cim = LR(0);
+#pragma unroll
+        for (int k = m; k <= N; ++k) cim += __ldg(rt + m * (N + 1) + k) * w[(row++) * ws];
+        cr[2 * m] = R(cim);
+    }
+}
+
 template <int N, class LR, class R>
 __device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, LR n, LR T, LR U0,
                                                    LR Ux, LR Uy, R *cr)
@@ -639,7 +710,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     if (MODE != MODE_INIT) __syncthreads();
     if (MODE == MODE_MOMENTS && g != 0) return;
 
-    // every warp: the Landau frame of its 32 sites and its own shell's coefficients
+    // the Landau frame of the tile's 32 sites and every warp's own shell coefficients:
+    // with an FP64 per-site part once per site (ONCE), else in every warp
+    constexpr bool ONCE = (sizeof(LR) == 8) && STEP && !QUANT;
+    constexpr int W = (N + 1) * (N + 1);
+    LR *wsh = reinterpret_cast<LR *>(smem_raw + size_t(5) * G * 32 * sizeof(LR)); // [W + 3][32]
+    (void)wsh;
     LR n, eps, U0, Ux, Uy, T;
     if (MODE == MODE_INIT) {
         const double bx = a.in_bx[site], by = a.in_by[site];
@@ -650,6 +726,29 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         Ux = LR(gam * bx);
         Uy = LR(gam * by);
         eps = LR(2) * n * T;
+    } else if constexpr (ONCE) {
+        // FP64 per-site part of a step: warp 0 solves the Landau frame of the
+        // tile's 32 sites and forms the shell-independent sums w_{m,k} once; the
+        // other warps read them (and U^a) from shared memory after the moments
+        if (g == 0) {
+            LR m[8];
+            fold_moments<N, LR>(a, red, G, lane, m);
+            const bool ok = site_landau<St, LR>(m, n, eps, U0, Ux, Uy);
+            T = eps / (LR(2) * n);
+            if (!ok && act) atomicOr(a.status, 1);
+            LR tk[N + 1];
+            tk[0] = n / T;
+#pragma unroll
+            for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
+            site_sums<N, LR>(a, tk, U0, Ux, Uy, wsh + lane, 32);
+            wsh[(W + 0) * 32 + lane] = U0;
+            wsh[(W + 1) * 32 + lane] = Ux;
+            wsh[(W + 2) * 32 + lane] = Uy;
+        }
+        __syncthreads();
+        U0 = wsh[(W + 0) * 32 + lane];
+        Ux = wsh[(W + 1) * 32 + lane];
+        Uy = wsh[(W + 2) * 32 + lane];
     } else {
         LR m[8];
         fold_moments<N, LR>(a, red, G, lane, m);
@@ -695,6 +794,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     R cr[NC];
     if constexpr (QUANT)
         shell_coefficients_tk<N, LR, R>(a, r, tkq, U0, Ux, Uy, cr);
+    else if constexpr (ONCE)
+        shell_from_sums<N, LR, R>(a, r, wsh + lane, 32, cr);
     else
         shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
     const LR itau = Par<LR>::inv_tau(a);

@@ -583,8 +583,7 @@ void *buffer(rlbm_t *h, int which) { return (unsigned char *)h->buf + size_t(whi
 size_t smem_bytes(const rlbm_t *h)
 {
     const size_t ls = (h->prec == RLBM_FP64 || h->site_fp64) ? 8 : 4;
-    // angular sums [5][G][32]; quantum statistics: (eta, T) of the 32 sites after them
-    return ls * 5 * size_t(h->G) * 32 + (h->stat ? 2 * 32 * sizeof(double) : 0);
+    return rlbmk::tile_smem_bytes(h->N, h->G, ls, h->stat != 0);
 }
 
 cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)

@@ -291,7 +291,7 @@ extern "C" rlbm_status rlbm_step_noalloc(rlbm_grid grid, int order_N, int angles
     a.ctr = reinterpret_cast<unsigned *>(base + o_status + 4);
 
     const dim3 gridd((grid.nx + 31) / 32, grid.ny), block(32, G);
-    const size_t smem = ls * 5 * size_t(G) * 32;
+    const size_t smem = rlbmk::tile_smem_bytes(N, G, ls, false);
     const bool full = (K % P) == 0;
     const cudaError_t e = r64 ? rlbmk::launch_f64(rlbmk::MODE_STEP, N, P, grid.ny > 1, full, gridd,
                                                   block, smem, stream, a)
