@@ -93,6 +93,11 @@ __device__ __forceinline__ float r_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double r_sqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float r_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double r_rsqrt(double v) { return rsqrt(v); }
+// Division in the per-site arithmetic: FP32 uses the approximate quotient (2 ulp;
+// the FP32 per-site part serves 16-bit storage, and where it is not accurate
+// enough landau_f32_adaptive solves again in double-float), FP64 the exact one.
+__device__ __forceinline__ float r_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double r_div(double a, double b) { return a / b; }
 
 // Stochastic rounding of 16-bit stores.  Round-to-nearest repeats the same
 // rounding error every step wherever the flow is steady, and the conserved
@@ -291,7 +296,7 @@ __device__ __forceinline__ bool landau_fast(const LR *m, LR &n, LR &eps, LR &U0,
                   Tty * Tty * Txx;
     const LR M = r_sqrt(Ttx * Ttx + Tty * Tty);
     const LR disc = LR(9) * E * E - LR(8) * M * M;
-    const LR b0 = LR(4) * M / (LR(3) * E + r_sqrt(disc > LR(0) ? disc : LR(0)));
+    const LR b0 = r_div(LR(4) * M, LR(3) * E + r_sqrt(disc > LR(0) ? disc : LR(0)));
     LR lam = E - b0 * M;
     if ((lam * lam + c1) * lam - c0 < LR(0)) lam = E;
     const LR tol = LR(sizeof(LR) == 8 ? 4e-16 : 2e-7);
@@ -300,7 +305,7 @@ __device__ __forceinline__ bool landau_fast(const LR *m, LR &n, LR &eps, LR &U0,
         const LR P = (lam * lam + c1) * lam - c0;
         const LR dP = LR(3) * lam * lam + c1;
         if (!(dP > LR(0))) break;
-        const LR d = P / dP;
+        const LR d = r_div(P, dP);
         lam -= d;
         if (!(fabs(d) > tol * lam)) break;
     }

@@ -231,7 +231,7 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
     }
     float n, eps, U0, Ux, Uy;
     const bool ok = landau_f32_adaptive(m, n, eps, U0, Ux, Uy);
-    const float T = eps / (2.f * n);
+    const float T = __fdividef(eps, 2.f * n);
     if (!ok && act) atomicOr(a.status, 1);
     // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
     float accr[N + 1][N + 1], acci[N + 1][N + 1];
@@ -239,7 +239,7 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
     for (int mm = 0; mm <= N; ++mm)
 #pragma unroll
         for (int k = 0; k <= N; ++k) { accr[mm][k] = 0.f; acci[mm][k] = 0.f; }
-    const float inv1g = 1.f / (1.f + U0);
+    const float inv1g = __fdividef(1.f, 1.f + U0);
 #pragma unroll
     for (int j = 0; j <= N; ++j) {
         const float cj = a.smp_cf[j], sj = a.smp_sf[j];
@@ -266,7 +266,7 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
             }
     }
     float tk[N + 1];
-    tk[0] = n / T;
+    tk[0] = __fdividef(n, T);
 #pragma unroll
     for (int k = 1; k <= N; ++k) tk[k] = (k == 1) ? n : tk[k - 1] * T;
     // shell-independent part of the coefficients, T^(k-1)-weighted: w_{m,k} = tk[k] acc_{m,k}
