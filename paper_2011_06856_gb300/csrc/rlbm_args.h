@@ -56,6 +56,8 @@ struct KernelArgs {
     const unsigned long long *masks; // per warp: bit k = (v_x >= 0), (v_y >= 0) of its population k (k < 64)
     const void *pairtab; // npop x 3 float4: paired constants of the two-sites-per-lane kernel (FP32 arithmetic)
     const int2 *shifts;  // npop: integer stencil vectors of the on-lattice rule (else NULL)
+    double *qeta;        // quantum statistics: per site, eta = ln z of the last solve (the next
+                         // step's Newton start; NaN: none yet), else NULL
     long long wait_cycles; // bound of every mbarrier wait of the bulk-staged pair kernel (SM cycles)
     unsigned extra_tx;     // test hook: bytes expected on top of the copies (makes the waits run out)
     int *status;

@@ -769,9 +769,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
         double qeta = 0.0, qT = T;
         double *qsh = reinterpret_cast<double *>(smem_raw + size_t(5) * G * 32 * sizeof(LR));
         if (g == 0) {
+            // warm start from the site's eta of the previous solve, kept in a.qeta
+            const double x0 = a.qeta ? a.qeta[site] : __longlong_as_double(0x7ff8000000000000ll);
             const bool ok = (MODE == MODE_INIT) ? stat_fugacity(n, T, a.gdeg, a.stat, qeta)
-                                                : stat_solve(n, eps, a.gdeg, a.stat, qeta, qT);
+                                                : stat_solve(n, eps, a.gdeg, a.stat, qeta, qT, x0);
             if (!ok && act) atomicOr(a.status, 1);
+            if (a.qeta && act && MODE != MODE_MOMENTS) a.qeta[site] = qeta;
             if (MODE != MODE_MOMENTS) {
                 qsh[lane] = qeta;
                 qsh[32 + lane] = qT;

@@ -265,6 +265,7 @@ struct rlbm {
     int P = 0, Gs = 0, G = 0;
     int R = 1; // groups of P populations per warp (K beyond one group per warp)
     int stat = 0;       // equilibrium statistic: 0 Maxwell-Juttner, +1 Fermi-Dirac, -1 Bose-Einstein
+    double *d_qeta = nullptr; // quantum statistics: per-site eta of the last solve (Newton warm start)
     double gdeg = 1.0;  // normalisation g of the quantum statistics
     bool site_fp64 = false;
     // CUDA graphs of kGraphSteps steps starting from buffer 0 / buffer 1
@@ -573,6 +574,7 @@ rlbm_status build_tables(rlbm_t *h)
     a.shifts = shifts.empty() ? nullptr : reinterpret_cast<const int2 *>((const unsigned char *)h->d_tabs + o_shift);
     a.status = h->d_status;
     a.ctr = reinterpret_cast<unsigned *>(h->d_status + 1);
+    a.qeta = h->d_qeta;
     a.wait_cycles = h->wait_cycles;
     a.extra_tx = 0;
     return RLBM_OK;
@@ -1176,6 +1178,12 @@ rlbm_status rlbm_set_statistics(rlbm_t *h, int statistics, double g)
     }
     h->stat = statistics;
     h->gdeg = statistics != 0 ? g : 1.0;
+    // the per-site eta of the last solve, the Newton start of the next one (NaN: none yet)
+    if (statistics != 0 && !h->d_qeta) {
+        const size_t bytes = sizeof(double) * size_t(h->grid.nx) * size_t(h->grid.ny);
+        RLBM_CUDA(h, cudaMalloc(&h->d_qeta, bytes));
+        RLBM_CUDA(h, cudaMemsetAsync(h->d_qeta, 0xff, bytes, h->stream));
+    }
     // the quantum per-site part runs in FP64 (FP32 storage: FP64 site tables)
     h->site_fp64 = site_fp64_for(h->prec, h->N, statistics);
     return retile(h, h->P, 0);
@@ -1187,7 +1195,10 @@ double rlbm_quantum_phi(int s, double eta, int statistics)
 {
     if (s < 0 || s > 6 || (statistics != 1 && statistics != -1) || (statistics < 0 && !(eta < 0.0)))
         return std::nan("");
-    return rlbmk::stat_phi(s, eta, statistics);
+    if (s == 0) return rlbmk::stat_phi(0, eta, statistics);
+    double ph[6]; // the fused evaluation the kernels use (phi_1 .. phi_s in one pass)
+    rlbmk::stat_phi_upto(s, eta, statistics, ph);
+    return ph[s - 1];
 }
 
 void rlbm_destroy(rlbm_t *h)
@@ -1199,6 +1210,7 @@ void rlbm_destroy(rlbm_t *h)
     if (h->own_buf && h->buf) cudaFree(h->buf);
     if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->d_status) cudaFree(h->d_status);
+    if (h->d_qeta) cudaFree(h->d_qeta);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete[] h->tma;
     delete[] h->ptma;
@@ -1336,6 +1348,8 @@ rlbm_status rlbm_set_populations(rlbm_t *h, const void *host, size_t bytes, long
     RLBM_CUDA(h, cudaMemcpyAsync(buffer(h, 0), host, bytes, cudaMemcpyHostToDevice, h->stream));
     const unsigned ctr[2] = {unsigned(step), 0u};
     RLBM_CUDA(h, cudaMemcpyAsync(h->d_status + 1, ctr, sizeof(ctr), cudaMemcpyHostToDevice, h->stream));
+    if (h->d_qeta) // a new state: no previous eta to start from
+        RLBM_CUDA(h, cudaMemsetAsync(h->d_qeta, 0xff, sizeof(double) * size_t(h->grid.nx) * h->grid.ny, h->stream));
     RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->cur = 0;
     h->steps = step;

@@ -51,6 +51,30 @@ RLBM_HDX double stat_alt_series(int s, double x)
     return sum / d;
 }
 
+// The same series for every s = 1..smax at once (smax <= 6): the weights of the
+// acceleration do not depend on s, so one pass over the 24 terms serves all
+// orders, out[s-1] = sum_j (-1)^(j+1) x^j / j^s.
+RLBM_HDX void stat_alt_series_upto(int smax, double x, double *out)
+{
+    const int n = 24;
+    double d = stat_ipow(3.0 + sqrt(8.0), n);
+    d = 0.5 * (d + 1.0 / d);
+    double b = -1.0, c = -d, xk = x;
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) {
+        c = b - c;
+        const double r = 1.0 / (k + 1.0);
+        double t = c * xk;
+        for (int q = 0; q < smax; ++q) {
+            t *= r;
+            acc[q] += t;
+        }
+        b = (double(k) + n) * (double(k) - n) * b / ((k + 0.5) * (k + 1.0));
+        xk *= x;
+    }
+    for (int q = 0; q < smax; ++q) out[q] = acc[q] / d;
+}
+
 // Fermi-Dirac F_s(eta) = -Li_s(-e^eta), s >= 1.  eta <= 0: the alternating series
 // at x = e^eta; eta > 0: the inversion identity for integer s,
 //   F_s(eta) = (-1)^(s+1) F_s(-eta) + 2 sum_{j=0}^{s/2} eta_D(2j) eta^(s-2j) / (s-2j)!,
@@ -98,26 +122,59 @@ RLBM_HDX double stat_be(int s, double eta)
     return acc + scale * sum;
 }
 
+// phi_1 .. phi_smax at once (smax <= 6): Fermi-Dirac from one pass of the
+// accelerated series (and the inversion identity for eta > 0), Bose-Einstein
+// order by order.
+RLBM_HDX void stat_phi_upto(int smax, double eta, int stat, double *phi)
+{
+    if (stat < 0) {
+        for (int q = 1; q <= smax; ++q) phi[q - 1] = stat_be(q, eta);
+        return;
+    }
+    if (eta <= 0.0) {
+        stat_alt_series_upto(smax, exp(eta), phi);
+        return;
+    }
+    const double pi2 = 9.8696044010893586188; // pi^2
+    const double etaD[4] = {0.5, pi2 / 12.0, 7.0 * pi2 * pi2 / 720.0, 31.0 * pi2 * pi2 * pi2 / 30240.0};
+    double mirror[6];
+    stat_alt_series_upto(smax, exp(-eta), mirror);
+    for (int q = 1; q <= smax; ++q) {
+        double poly = 0.0;
+        for (int j = 0; 2 * j <= q; ++j) {
+            const int m = q - 2 * j;
+            double fact = 1.0;
+            for (int i = 2; i <= m; ++i) fact *= i;
+            poly += etaD[j] * stat_ipow(eta, m) / fact;
+        }
+        phi[q - 1] = ((q & 1) ? mirror[q - 1] : -mirror[q - 1]) + 2.0 * poly;
+    }
+}
+
 // phi_s(eta) of the statistic (+1 Fermi-Dirac, -1 Bose-Einstein), s = 0..6.
 RLBM_HD double stat_phi(int s, double eta, int stat) { return stat > 0 ? stat_fd(s, eta) : stat_be(s, eta); }
 
 // (eta, T) of the equilibrium with density n and energy density e:
 // ln phi_3 - 3/2 ln phi_2 = ln(e sqrt(2 pi g) / (2 n^1.5)) =: L is decreasing in eta
 // (Maxwell-Boltzmann limit: -eta/2), solved by Newton steps kept inside a
-// bisection bracket (at most 100 iterations).  Returns false for a Bose-Einstein
+// bisection bracket (at most 100 iterations), from x0 (the previous step's eta
+// of the site; NaN or out of range: the Maxwell-Boltzmann value).  Returns false for a Bose-Einstein
 // state beyond condensation (no z < 1), or bad input; eta then sits at the bracket end.
-RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, double &T)
+RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, double &T, double x0)
 {
     const double twopi = 6.283185307179586477;
     if (!(n > 0.0) || !(e > 0.0)) { eta = -30.0; T = 1.0; return false; }
     const double L = log(e * sqrt(twopi * g) / (2.0 * n * sqrt(n)));
     double lo = -60.0, hi = stat > 0 ? 700.0 : -1e-13;
-    double x = -2.0 * L; // Maxwell-Boltzmann start
+    // start: the site's eta of the previous step where given, else Maxwell-Boltzmann
+    double x = (x0 > lo && x0 < hi) ? x0 : -2.0 * L;
     if (x <= lo) x = lo + 1.0;
     if (x >= hi) x = stat > 0 ? hi - 1.0 : -1e-3;
     bool ok = false;
     for (int it = 0; it < 100; ++it) {
-        const double p1 = stat_phi(1, x, stat), p2 = stat_phi(2, x, stat), p3 = stat_phi(3, x, stat);
+        double ph[3];
+        stat_phi_upto(3, x, stat, ph);
+        const double p1 = ph[0], p2 = ph[1], p3 = ph[2];
         const double H = log(p3) - 1.5 * log(p2) - L;
         if (H > 0.0) lo = x; else hi = x;
         const double dH = p2 / p3 - 1.5 * p1 / p2;
@@ -144,7 +201,9 @@ RLBM_HDX bool stat_fugacity(double n, double T, double g, int stat, double &eta)
     if (x >= hi) x = stat > 0 ? hi - 1.0 : -1e-3;
     bool ok = false;
     for (int it = 0; it < 100; ++it) {
-        const double p1 = stat_phi(1, x, stat), p2 = stat_phi(2, x, stat);
+        double ph[2];
+        stat_phi_upto(2, x, stat, ph);
+        const double p1 = ph[0], p2 = ph[1];
         const double H = log(p2) - target; // increasing in eta
         if (H < 0.0) lo = x; else hi = x;
         double xn = x - H * p2 / p1;
@@ -163,9 +222,11 @@ template <int N>
 RLBM_HD void stat_radial(double T, double eta, double g, int stat, double *tk)
 {
     const double twopi = 6.283185307179586477;
+    double ph[N + 1];
+    stat_phi_upto(N + 1, eta, stat, ph);
     double Tp = T;
     for (int k = 0; k <= N; ++k) {
-        tk[k] = twopi * g * Tp * stat_phi(k + 1, eta, stat);
+        tk[k] = twopi * g * Tp * ph[k];
         Tp *= T;
     }
 }
