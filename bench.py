@@ -411,6 +411,7 @@ def run_closure(args):
     del X, T
     fl = W.riemann_2d(n, n, CL.RIEMANN, jitter=0.01)
     kn = 0.3
+    feat = CL.kn_feature(W.tau_from_kn(kn, n), 128)  # trained on 128^2 runs
     times = {}
     for name, K, corrected in (("fine_K128", 128, False), ("coarse_K24", 24, False),
                                ("coarse_K24_closure", 24, True)):
@@ -424,7 +425,7 @@ def run_closure(args):
             for _ in range(k):
                 sim.step(1)
                 if corrected:
-                    cl.apply(sim, kn)
+                    cl.apply(sim, feat)
         run(3)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -459,6 +460,12 @@ def run_closure(args):
         dist.destroy_process_group()
 
 
+# Training runs of the config-5 closure: 1024^2 Riemann problems at four Kn,
+# snapshots every `every` steps over `steps` steps (1024 steps of a 1024^2
+# grid span the physical time of the 4000 deployed steps at 4096^2).
+CONFIG5_TRAIN = {"grid": 1024, "kn": (0.01, 0.1, 1.0, 5.0), "steps": 1024, "every": 64}
+
+
 def run_closure_config5(args):
     """The learned closure at the size of the survey's fifth configuration.
     Training data: 1024^2 four-quadrant Riemann runs at K = 128 (3 x 128 angles)
@@ -481,7 +488,8 @@ def run_closure_config5(args):
         dist.init_process_group("nccl")
     t0 = time.perf_counter()
     cl = R.Closure(2, 24, seed=7)
-    X, T = CL.generate(cl, 1024, 128, (0.01, 0.1, 1.0, 5.0), 512, every=32)
+    tr = CONFIG5_TRAIN
+    X, T = CL.generate(cl, tr["grid"], 128, tr["kn"], tr["steps"], every=tr["every"])
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -492,6 +500,7 @@ def run_closure_config5(args):
     del X, T
     torch.cuda.empty_cache()
     n, steps, kn = 4096, 4000, 1.0
+    feat = CL.kn_feature(W.tau_from_kn(kn, n), CONFIG5_TRAIN["grid"])
     fl = W.riemann_2d(n, n, CL.RIEMANN, jitter=0.01, seed=99)
     runs = {}
     for name, K, corrected in (("plain_K128", 128, False), ("corrected_K24", 24, True), ("plain_K24", 24, False),
@@ -506,7 +515,7 @@ def run_closure_config5(args):
         if corrected:
             for _ in range(steps):
                 sim.step(1)
-                cl.apply(sim, kn)
+                cl.apply(sim, feat)
         else:
             sim.step(steps)
         e1.record(cl.stream)
@@ -532,8 +541,9 @@ def run_closure_config5(args):
                        "plain_runs_meeting_accuracy": plain_meets, "corrected_meets_accuracy":
                        max(out["corrected_K24"]["rel_l2_n_eps_vs_K128"]) <= tol,
                        "fastest_plain_meeting_accuracy_s": min(plain_meets.values()) if plain_meets else None,
-                       "training": {"grid": [1024, 1024], "K_fine": 128, "kn": [0.01, 0.1, 1.0, 5.0],
-                                    "steps": 512, "snapshot_every": 32, "columns": columns,
+                       "kn_feature": feat,
+                       "training": {"grid": [tr["grid"], tr["grid"]], "K_fine": 128, "kn": list(tr["kn"]),
+                                    "steps": tr["steps"], "snapshot_every": tr["every"], "columns": columns,
                                     "adam_steps": 8000, "batch": 65536, "generate_s": gen_s, "train_s": train_s,
                                     "loss_first_last": [float(losses[0]), float(losses[-1])]}},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}

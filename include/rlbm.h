@@ -357,8 +357,10 @@ rlbm_status rlbm_batch_test_stall_next_step(rlbm_batch_t *b);
 /* Learned angular closure (an extension; the paper has no counterpart)  */
 /* ------------------------------------------------------------------ */
 /* A small MLP corrects a coarse-angle run toward the fine-angle solution.
- * Per site: features x = (N^a, T^ab)/N^0 (9 values), Kn, f_i/(w_i N^0)
- * (N_pop values); y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3 with hidden
+ * Per site: features x = (N^a, T^ab)/N^0 (9 values), a scalar kn,
+ * f_i/(w_i N^0) (N_pop values).  kn is the caller's: the Python driver passes
+ * tau / L_train, the Knudsen number of the run's relaxation time on the
+ * training grid (equal to Kn on that grid); y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3 with hidden
  * width 64 and N_pop outputs; the correction d_i = y_i w_i N^0 minus its
  * weighted least-squares component along p^0, p^0 p^0, p^0 p^x, p^0 p^y is
  * added to the post-collision populations, so N^0, T^00, T^0x, T^0y of every

@@ -23,9 +23,27 @@ from . import workloads as W
 RIEMANN = [(1.0, 1.0, 0.0, 0.0), (0.5, 0.8, 0.0, 0.0), (0.25, 0.6, 0.0, 0.0), (0.5, 0.8, 0.0, 0.0)]
 
 
+def kn_feature(tau: float, train_n: int) -> float:
+    """The network's scalar input for a run with relaxation time tau (in time
+    steps): tau / train_n, the Knudsen number that tau has on the n x n grid
+    the network was trained on.
+
+    The correction the network predicts is the coarse rule's error over one
+    time step, which scales with the field's gradients in lattice units.  Its
+    inputs are local, and near equilibrium the non-equilibrium part of f is
+    about tau times those gradients (Chapman-Enskog), so the relaxation time
+    in steps, not the grid-independent Kn = tau / L, is what ties the local
+    state to the size of the correction.  On the training grid the two agree;
+    on a finer grid (same Kn, larger tau) the gradients per cell are smaller
+    and so is the correction.
+    """
+    return float(tau) / float(train_n)
+
+
 def generate(closure: R.Closure, n: int, K_fine: int, kns, steps: int, seed: int = 1,
              every: int = 1):
-    """Training pairs from runs at each Kn on an n x n Riemann problem; returns (X, T) tensors."""
+    """Training pairs from runs at each Kn on an n x n Riemann problem; returns (X, T) tensors.
+    The scalar feature is kn_feature(tau, n) = Kn."""
     import torch
     N, K = closure.N, closure.K
     S = n * n
@@ -50,7 +68,7 @@ def generate(closure: R.Closure, n: int, K_fine: int, kns, steps: int, seed: int
                 closure.restrict(K_fine, fview, cview)      # coarse state := R f_fine(t)
                 coarse.step(1)
                 cview = _view(coarse)
-                closure.features(cview, kn, X, off)
+                closure.features(cview, kn_feature(tau, n), X, off)
             fine.step(1)
             if t % every == 0:
                 closure.restrict(K_fine, _view(fine), tmp)  # R f_fine(t+1)
@@ -89,11 +107,14 @@ def train(closure: R.Closure, X, T, iters: int = 300, batch: int = 4096, lr: flo
     return losses
 
 
-def deploy(closure: R.Closure, n: int, K_fine: int, kn: float, steps: int, seed: int = 99):
+def deploy(closure: R.Closure, n: int, K_fine: int, kn: float, steps: int, seed: int = 99,
+           train_n: int | None = None):
     """Fine, plain coarse and corrected coarse runs of one Riemann problem; returns
-    (moments fine, moments coarse, moments corrected), each (6, n, n)."""
+    (moments fine, moments coarse, moments corrected), each (6, n, n).  train_n:
+    the side of the training grid (default n)."""
     N, K = closure.N, closure.K
     tau = W.tau_from_kn(kn, n)
+    feat = kn_feature(tau, train_n or n)
     fl = W.riemann_2d(n, n, RIEMANN, jitter=0.01, seed=seed)
     out = []
     for (k, corrected) in ((K_fine, False), (K, False), (K, True)):
@@ -102,7 +123,7 @@ def deploy(closure: R.Closure, n: int, K_fine: int, kn: float, steps: int, seed:
         if corrected:
             for _ in range(steps):
                 sim.step(1)
-                closure.apply(sim, kn)
+                closure.apply(sim, feat)
         else:
             sim.step(steps)
         out.append(sim.moments())

@@ -75,6 +75,15 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int N, int G, size_t ls, bo
     return ls * 5 * size_t(G) * 32 +
            (quantum ? 2 * 32 * sizeof(double) : (ls == 8 ? size_t((N + 1) * (N + 1) + 3) * 32 * 8 : 0));
 }
+// The same for an FP32-storage step with the double-float per-site part split
+// over the warps (site_split_dd): FP32 angular sums, then [2 (N+1)^2 + 3][32]
+// floats (the sums as hi and lo rows, then U^a / tau), the frame
+// [6 + 2 (N+1)][32] and the partial sums [N+1][2 (N+1)^2][32].
+__host__ __device__ constexpr size_t tile_smem_bytes_dd(int N, int G)
+{
+    return 4 * 5 * size_t(G) * 32 +
+           size_t(2 * (N + 1) * (N + 1) + 3 + 6 + 2 * (N + 1) + (N + 1) * 2 * (N + 1) * (N + 1)) * 32 * 4;
+}
 
 // Two-sites-per-lane step kernel: sites per CTA and dynamic shared memory:
 // angular sums [5][G][64] and the per-site results [2 (N+1)^2 + 3][64] (FP32;
@@ -148,11 +157,21 @@ cudaError_t launch_f64(int mode, int N, int P, bool two_d, bool full, dim3 grid,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_f32(int mode, int N, int P, bool two_d, bool full, bool site_fp64, dim3 grid,
                        dim3 block, size_t smem, cudaStream_t st, const KernelArgs &a);
+// FP32 storage, a step (N = 2, 3) with the double-float per-site part once per
+// site (needs the split tables shell2, rtab2 and the lo parts of KernelArgs;
+// shared memory tile_smem_bytes_dd).
+cudaError_t launch_f32_dd(int N, int P, bool two_d, bool full, dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t st, const KernelArgs &a);
+cudaError_t launch_f32_dd_n2(int P, bool two_d, bool full, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             const KernelArgs &a);
+cudaError_t launch_f32_dd_n3(int P, bool two_d, bool full, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             const KernelArgs &a);
 cudaError_t launch_f16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                        size_t smem, cudaStream_t st, const KernelArgs &a);
 cudaError_t launch_bf16(int mode, int N, int P, bool two_d, bool full, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t st, const KernelArgs &a);
-// A step of the on-lattice rule (per-tile kernel, N = 3, P = 12), FP64 and FP32 storage.
+// A step of the on-lattice rule (per-tile kernel, N = 3, P = 12), FP64 and FP32 storage
+// (FP32: the double-float per-site part, shared memory tile_smem_bytes_dd).
 cudaError_t launch_lattice_f64(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                const KernelArgs &a);
 cudaError_t launch_lattice_f32(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -1,5 +1,5 @@
 // Batched persistent kernel instances (FP64 and FP32 storage, N = 2, 3; the
-// per-site part in FP64 for both).
+// per-site part in FP64 for FP64 storage, in double-float for FP32).
 #include "rlbm_batch.cuh"
 
 namespace rlbmk {
@@ -33,9 +33,9 @@ cudaError_t launch_batch(int prec, int N, const BatchArgs &b, int grid, cudaStre
         if (N == 2) return launch_b<double, double, double, 2>(b, grid, st, bps);
         if (N == 3) return launch_b<double, double, double, 3>(b, grid, st, bps);
     } else if (prec == 1) {
-        // FP32 storage: FP32 per-population arithmetic, FP64 per-site part
-        if (N == 2) return launch_b<float, float, double, 2>(b, grid, st, bps);
-        if (N == 3) return launch_b<float, float, double, 3>(b, grid, st, bps);
+        // FP32 storage: FP32 per-population arithmetic, double-float per-site part
+        if (N == 2) return launch_b<float, float, float, 2>(b, grid, st, bps);
+        if (N == 3) return launch_b<float, float, float, 3>(b, grid, st, bps);
     }
     return cudaErrorInvalidValue;
 }

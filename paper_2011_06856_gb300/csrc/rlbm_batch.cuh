@@ -13,8 +13,12 @@
 // Per tile the arithmetic is that of the per-tile kernel (rlbm_device.cuh):
 // bilinear pull from global memory (L2-coherent loads, since the values were
 // written by other CTAs earlier in the same launch), per-warp angular sums,
-// every warp solving the Landau frame and its own shell's equilibrium, and
-// relaxation (Sec. 2.2); FP32 stores round stochastically (relax_store).
+// the Landau frame and the equilibrium (Sec. 2.2) -- FP64 storage: every warp
+// solves the frame and its own shell's equilibrium in FP64; FP32 storage: the
+// group solves each site once in double-float, split over its warps by sample
+// direction (site_split_dd), and every warp combines its shell's coefficients
+// from the shared sums --
+// and relaxation; FP32 stores round stochastically (relax_store).
 #pragma once
 
 #include "rlbm_device.cuh"
@@ -25,8 +29,13 @@ namespace rlbmk {
 template <class St, class R, class LR, int N, bool TWO_D>
 __device__ __forceinline__ void batch_tile(const KernelArgs &a, const St *fin, St *fout, int tile,
                                            int ntiles_x, bool valid, int gw, int G, int lane,
-                                           LR *red, unsigned seed)
+                                           LR *red, float *wdd, unsigned seed)
 {
+    // FP32 storage: the per-site part once per site in double-float, split over
+    // the group's warps (site_split_dd); wdd holds the group's [2 (N+1)^2 + 3][32]
+    // sums and U^a / tau, then the frame and the partial sums
+    constexpr bool DDS = (sizeof(St) == 4) && (sizeof(LR) == 4);
+    constexpr int W = (N + 1) * (N + 1);
     constexpr int P = 32;
     constexpr int NC = 2 * N + 1;
     constexpr int TW = tab_width(N);
@@ -90,16 +99,28 @@ __device__ __forceinline__ void batch_tile(const KernelArgs &a, const St *fin, S
     red[(3 * G + gw) * 32 + lane] = LR(scc);
     red[(4 * G + gw) * 32 + lane] = LR(scs);
     __syncthreads();
-    LR m[8];
-    fold_moments<N, LR>(a, red, G, lane, m);
-    LR n, eps, U0, Ux, Uy;
-    const bool ok = site_landau<St, LR>(m, n, eps, U0, Ux, Uy);
-    const LR T = eps / (LR(2) * n);
-    if (!ok && act && gw == 0) atomicOr(a.status, 1);
     R cr[NC];
-    shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
-    const LR itau = Par<LR>::inv_tau(a);
-    const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
+    R o0, o1, o2;
+    if constexpr (DDS) {
+        site_split_dd<N, 32>(a, reinterpret_cast<const float *>(red), G, gw * 32 + lane, G * 32, act, wdd,
+                             wdd + (2 * W + 3) * 32, wdd + (2 * W + 3 + kSplitFrameRows(N)) * 32);
+        shell_from_sums_dd<N>(a, r, wdd + lane, 32, cr);
+        o0 = wdd[(2 * W + 0) * 32 + lane];
+        o1 = wdd[(2 * W + 1) * 32 + lane];
+        o2 = wdd[(2 * W + 2) * 32 + lane];
+    } else {
+        LR m[8];
+        fold_moments<N, LR>(a, red, G, lane, m);
+        LR n, eps, U0, Ux, Uy;
+        const bool ok = site_landau<St, LR>(m, n, eps, U0, Ux, Uy);
+        const LR T = eps / (LR(2) * n);
+        if (!ok && act && gw == 0) atomicOr(a.status, 1);
+        shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
+        const LR itau = Par<LR>::inv_tau(a);
+        o0 = R(U0 * itau);
+        o1 = R(Ux * itau);
+        o2 = R(Uy * itau);
+    }
     unsigned rng = mix32(unsigned(y * a.nx + x) * 64u + unsigned(gw) ^ seed);
 #pragma unroll
     for (int k = 0; k < P; ++k) {
@@ -159,6 +180,11 @@ template <class St, class R, class LR, int N>
 __global__ void __launch_bounds__(kBatchWarps * 32) rlbm_batch_kernel(const BatchArgs b)
 {
     __shared__ LR red_all[kBatchWarps * 5 * 32];
+    // FP32 storage: the double-float per-site sums of each tile of a unit
+    // (at most kBatchWarps / (N + 1) tiles per unit)
+    constexpr bool DDS = (sizeof(St) == 4) && (sizeof(LR) == 4);
+    constexpr int kRows = 2 * (N + 1) * (N + 1) + 3 + kSplitFrameRows(N) + (N + 1) * 2 * (N + 1) * (N + 1);
+    __shared__ float wdd_all[DDS ? (kBatchWarps / (N + 1)) * kRows * 32 : 1];
     __shared__ int s_unit;
     const int lane = threadIdx.x, g = threadIdx.y;
     for (int step = 0; step < b.nsteps; ++step) {
@@ -180,16 +206,17 @@ __global__ void __launch_bounds__(kBatchWarps * 32) rlbm_batch_kernel(const Batc
             const St *fin = reinterpret_cast<const St *>(par ? a.fout : a.fin);
             St *fout = reinterpret_cast<St *>(par ? const_cast<void *>(a.fin) : a.fout);
             LR *red = red_all + grp * (G * 5 * 32);
+            float *wdd = DDS ? wdd_all + grp * kRows * 32 : nullptr;
             // stochastic rounding of FP32 stores: seeded by the problem's launch
             // counter plus the step (the host advances the counters by nsteps after
             // the launch, batch_advance_kernel)
             const unsigned seed = mix32((__ldcg(a.ctr) + unsigned(step)) * 0x9E3779B9u + 1u);
             if (a.ny > 1)
                 batch_tile<St, R, LR, N, true>(a, fin, fout, tile, b.ntiles_x[bu.prob], valid, gw, G, lane, red,
-                                               seed);
+                                               wdd, seed);
             else
                 batch_tile<St, R, LR, N, false>(a, fin, fout, tile, b.ntiles_x[bu.prob], valid, gw, G, lane, red,
-                                                seed);
+                                                wdd, seed);
         }
         if (step + 1 < b.nsteps && !batch_grid_barrier(b, step + 1)) return;
     }

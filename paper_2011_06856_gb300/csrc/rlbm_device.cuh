@@ -590,6 +590,285 @@ __device__ __forceinline__ void shell_coefficients(const KernelArgs &a, int r, L
     shell_coefficients_tk<N, LR, R>(a, r, tk, U0, Ux, Uy, cr);
 }
 
+// The per-site part for site s with FP64-class accuracy (FP32 storage), in
+// double-float arithmetic (rlbm_df64.cuh): the warps' FP32 angular sums are
+// folded into N^a and T^ab (Eq. discrete_sum_moments) in double-float, the
+// Landau frame is solved in double-float (landau_dd), and the shell-independent
+// equilibrium sums w_{m,k} = n T^(k-1) acc_{m,k} are formed in double-float
+// and written as hi rows 0 .. (N+1)^2 - 1 and lo rows (N+1)^2 .. 2 (N+1)^2 - 1
+// of sres; U^a / tau follow at rows 2 (N+1)^2 + 0..2 (FP32: the relaxation
+// rate enters the conserved moments only at second order).  An FP32 per-site
+// part carries the conserved moments to a relative bias of about 4e-7 per
+// step (rounding of the moment fold, the frame and the radial projection,
+// which cancels about one digit); the collision feeds omega of that into the
+// state every step and it grows linearly; in double-float it is below 1e-12.
+// ST: sites per tile (the stride of red and sres): 64 in the two-sites-per-lane
+// kernels, 32 in the per-tile kernel.
+template <int N, int ST = 64>
+__device__ __forceinline__ void pair_site_solve_dd(const KernelArgs &a, const float *red, int G, int s, bool act,
+                                                   float *sres)
+{
+    constexpr int W = (N + 1) * (N + 1);
+    df64 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = dd(a.off_f[u], a.off_l[u]);
+#pragma unroll
+    for (int rr = 0; rr <= N; ++rr) {
+        df64 p0 = dd(0.f), pc = dd(0.f), ps = dd(0.f), pcc = dd(0.f), pcs = dd(0.f);
+        for (int qq = 0; qq < a.Gs; ++qq) {
+            const int w = rr * a.Gs + qq;
+            p0 = p0 + red[(0 * G + w) * ST + s];
+            pc = pc + red[(1 * G + w) * ST + s];
+            ps = ps + red[(2 * G + w) * ST + s];
+            pcc = pcc + red[(3 * G + w) * ST + s];
+            pcs = pcs + red[(4 * G + w) * ST + s];
+        }
+        const float2 t1 = __ldg(a.shell2 + 2 * rr), t2 = __ldg(a.shell2 + 2 * rr + 1);
+        const df64 f1 = dd(t1.x, t1.y), f2v = dd(t2.x, t2.y);
+        m[0] = m[0] + f1 * p0;
+        m[1] = m[1] + f1 * pc;
+        m[2] = m[2] + f1 * ps;
+        m[3] = m[3] + f2v * p0;
+        m[4] = m[4] + f2v * pc;
+        m[5] = m[5] + f2v * ps;
+        m[6] = m[6] + f2v * pcc;
+        m[7] = m[7] + f2v * pcs;
+    }
+    df64 n, eps, U0, Ux, Uy;
+    const bool ok = landau_dd(m, n, eps, U0, Ux, Uy);
+    if (!ok && act) atomicOr(a.status, 1);
+    const df64 T = eps / (n * 2.f);
+    const df64 inv1g = dd(1.f) / (U0 + 1.f);
+    // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
+    df64 accr[N + 1][N + 1], acci[N + 1][N + 1];
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+        for (int k = 0; k <= N; ++k) { accr[mm][k] = dd(0.f); acci[mm][k] = dd(0.f); }
+#pragma unroll
+    for (int j = 0; j <= N; ++j) {
+        const df64 cj = dd(a.smp_cf[j], a.smp_cl[j]), sj = dd(a.smp_sf[j], a.smp_sl[j]);
+        const df64 un = Ux * cj + Uy * sj;
+        const df64 h = un * inv1g + 1.f;
+        df64 qp[N + 1], pr[N + 1], pi[N + 1];
+        qp[1] = U0 + un;
+        pr[1] = cj + Ux * h;
+        pi[1] = sj + Uy * h;
+#pragma unroll
+        for (int t = 2; t <= N; ++t) {
+            qp[t] = qp[t - 1] * qp[1];
+            pr[t] = pr[t - 1] * pr[1] - pi[t - 1] * pi[1];
+            pi[t] = pr[t - 1] * pi[1] + pi[t - 1] * pr[1];
+        }
+#pragma unroll
+        for (int k = 1; k <= N; ++k) accr[0][k] = accr[0][k] + qp[k];
+#pragma unroll
+        for (int mm = 1; mm <= N; ++mm) {
+            accr[mm][mm] = accr[mm][mm] + pr[mm];
+            acci[mm][mm] = acci[mm][mm] + pi[mm];
+#pragma unroll
+            for (int k = mm + 1; k <= N; ++k) {
+                accr[mm][k] = accr[mm][k] + qp[k - mm] * pr[mm];
+                acci[mm][k] = acci[mm][k] + qp[k - mm] * pi[mm];
+            }
+        }
+    }
+    accr[0][0] = dd(float(N + 1));
+    df64 tk[N + 1];
+    tk[0] = n / T;
+    tk[1] = n;
+#pragma unroll
+    for (int k = 2; k <= N; ++k) tk[k] = tk[k - 1] * T;
+    int row = 0;
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+        for (int k = mm; k <= N; ++k, ++row) {
+            const df64 w = tk[k] * accr[mm][k];
+            sres[row * ST + s] = w.hi;
+            sres[(W + row) * ST + s] = w.lo;
+        }
+#pragma unroll
+    for (int mm = 1; mm <= N; ++mm)
+#pragma unroll
+        for (int k = mm; k <= N; ++k, ++row) {
+            const df64 w = tk[k] * acci[mm][k];
+            sres[row * ST + s] = w.hi;
+            sres[(W + row) * ST + s] = w.lo;
+        }
+    const float itau = a.inv_tau_f;
+    sres[(2 * W + 0) * ST + s] = to_float(U0) * itau;
+    sres[(2 * W + 1) * ST + s] = to_float(Ux) * itau;
+    sres[(2 * W + 2) * ST + s] = to_float(Uy) * itau;
+}
+
+// Shell r's equilibrium coefficients in the per-shell Fourier form of the
+// per-tile kernel (cr[0] = Re C_{r,0} - feq_off, cr[2m-1], cr[2m] = Re, Im C_{r,m})
+// from the double-float sums of pair_site_solve_dd (hi rows, then lo rows, of
+// stride ws), in double-float, rounded to FP32 at the end.
+template <int N>
+__device__ __forceinline__ void shell_from_sums_dd(const KernelArgs &a, int r, const float *w, int ws, float *cr)
+{
+    constexpr int W = (N + 1) * (N + 1);
+    const float2 *rt = a.rtab2 + r * (N + 1) * (N + 1);
+    int row = 0;
+#pragma unroll
+    for (int m = 0; m <= N; ++m) {
+        df64 acc = dd(0.f);
+#pragma unroll
+        for (int k = m; k <= N; ++k, ++row) {
+            const float2 t = __ldg(rt + m * (N + 1) + k);
+            acc = acc + dd(w[row * ws], w[(W + row) * ws]) * dd(t.x, t.y);
+        }
+        if (m == 0) cr[0] = to_float(acc - dd(a.feq_off_f, a.feq_off_l));
+        else cr[2 * m - 1] = to_float(acc);
+    }
+#pragma unroll
+    for (int m = 1; m <= N; ++m) {
+        df64 acc = dd(0.f);
+#pragma unroll
+        for (int k = m; k <= N; ++k, ++row) {
+            const float2 t = __ldg(rt + m * (N + 1) + k);
+            acc = acc + dd(w[row * ws], w[(W + row) * ws]) * dd(t.x, t.y);
+        }
+        cr[2 * m] = to_float(acc);
+    }
+}
+
+// The double-float per-site part of pair_site_solve_dd split over the threads
+// of a CTA, for kernels with more threads than sites.  Three phases, each ended
+// by a CTA barrier (every thread of the CTA calls site_split_dd):
+//  1. threads tid < ST: moment fold and Landau frame of site tid; U^a and
+//     t_k = n T^(k-1) (double-floats) into fr, U^a / tau into sres rows 2 W + 0..2;
+//  2. item (j, s), j = 0..N: the boosted sample direction j's terms of the sums,
+//     t_k acc_{m,k}(j) (double-floats), into part[j];
+//  3. item (row, s): w_{m,k} = sum_j part[j], into sres (hi rows, then lo rows).
+// The serial chain per site falls from the whole solve to the frame plus one
+// direction; the partial sums cost (N + 1) 2 W ST floats of shared memory.
+// Layouts (row stride ST): fr [kSplitFrameRows(N)][ST]: U0, Ux, Uy as hi, lo
+// pairs, then t_0..t_N as hi, lo pairs; part [N + 1][2 W][ST].
+__host__ __device__ constexpr int kSplitFrameRows(int N) { return 6 + 2 * (N + 1); }
+
+template <int N, int ST>
+__device__ __forceinline__ void site_frame_dd(const KernelArgs &a, const float *red, int G, int s, bool act,
+                                              float *fr, float *sres)
+{
+    constexpr int W = (N + 1) * (N + 1);
+    df64 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = dd(a.off_f[u], a.off_l[u]);
+#pragma unroll
+    for (int rr = 0; rr <= N; ++rr) {
+        df64 p0 = dd(0.f), pc = dd(0.f), ps = dd(0.f), pcc = dd(0.f), pcs = dd(0.f);
+        for (int qq = 0; qq < a.Gs; ++qq) {
+            const int w = rr * a.Gs + qq;
+            p0 = p0 + red[(0 * G + w) * ST + s];
+            pc = pc + red[(1 * G + w) * ST + s];
+            ps = ps + red[(2 * G + w) * ST + s];
+            pcc = pcc + red[(3 * G + w) * ST + s];
+            pcs = pcs + red[(4 * G + w) * ST + s];
+        }
+        const float2 t1 = __ldg(a.shell2 + 2 * rr), t2 = __ldg(a.shell2 + 2 * rr + 1);
+        const df64 f1 = dd(t1.x, t1.y), f2v = dd(t2.x, t2.y);
+        m[0] = m[0] + f1 * p0;
+        m[1] = m[1] + f1 * pc;
+        m[2] = m[2] + f1 * ps;
+        m[3] = m[3] + f2v * p0;
+        m[4] = m[4] + f2v * pc;
+        m[5] = m[5] + f2v * ps;
+        m[6] = m[6] + f2v * pcc;
+        m[7] = m[7] + f2v * pcs;
+    }
+    df64 n, eps, U0, Ux, Uy;
+    const bool ok = landau_dd(m, n, eps, U0, Ux, Uy);
+    if (!ok && act) atomicOr(a.status, 1);
+    const df64 T = eps / (n * 2.f);
+    fr[0 * ST + s] = U0.hi;
+    fr[1 * ST + s] = U0.lo;
+    fr[2 * ST + s] = Ux.hi;
+    fr[3 * ST + s] = Ux.lo;
+    fr[4 * ST + s] = Uy.hi;
+    fr[5 * ST + s] = Uy.lo;
+    df64 tk = n / T;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        if (k == 1) tk = n;
+        else if (k > 1) tk = tk * T;
+        fr[(6 + 2 * k) * ST + s] = tk.hi;
+        fr[(7 + 2 * k) * ST + s] = tk.lo;
+    }
+    const float itau = a.inv_tau_f;
+    sres[(2 * W + 0) * ST + s] = to_float(U0) * itau;
+    sres[(2 * W + 1) * ST + s] = to_float(Ux) * itau;
+    sres[(2 * W + 2) * ST + s] = to_float(Uy) * itau;
+}
+
+template <int N, int ST>
+__device__ __forceinline__ void site_direction_dd(const KernelArgs &a, const float *fr, int j, int s, float *part)
+{
+    constexpr int W = (N + 1) * (N + 1);
+    const df64 U0 = dd(fr[0 * ST + s], fr[1 * ST + s]);
+    const df64 Ux = dd(fr[2 * ST + s], fr[3 * ST + s]);
+    const df64 Uy = dd(fr[4 * ST + s], fr[5 * ST + s]);
+    df64 tk[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) tk[k] = dd(fr[(6 + 2 * k) * ST + s], fr[(7 + 2 * k) * ST + s]);
+    const df64 inv1g = dd(1.f) / (U0 + 1.f);
+    const df64 cj = dd(a.smp_cf[j], a.smp_cl[j]), sj = dd(a.smp_sf[j], a.smp_sl[j]);
+    const df64 un = Ux * cj + Uy * sj;
+    const df64 h = un * inv1g + 1.f;
+    df64 qp[N + 1], pr[N + 1], pi[N + 1];
+    qp[1] = U0 + un;
+    pr[1] = cj + Ux * h;
+    pi[1] = sj + Uy * h;
+#pragma unroll
+    for (int t = 2; t <= N; ++t) {
+        qp[t] = qp[t - 1] * qp[1];
+        pr[t] = pr[t - 1] * pr[1] - pi[t - 1] * pi[1];
+        pi[t] = pr[t - 1] * pi[1] + pi[t - 1] * pr[1];
+    }
+    float *pj = part + j * (2 * W) * ST + s;
+    int row = 0;
+    // Re rows: m = 0 (q0^k), then m = 1..N (q0^(k-m) Re z^m)
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm)
+#pragma unroll
+        for (int k = mm; k <= N; ++k, ++row) {
+            df64 v;
+            if (mm == 0) v = (k == 0) ? tk[0] : tk[k] * qp[k];
+            else v = tk[k] * ((k == mm) ? pr[mm] : qp[k - mm] * pr[mm]);
+            pj[row * ST] = v.hi;
+            pj[(W + row) * ST] = v.lo;
+        }
+#pragma unroll
+    for (int mm = 1; mm <= N; ++mm)
+#pragma unroll
+        for (int k = mm; k <= N; ++k, ++row) {
+            const df64 v = tk[k] * ((k == mm) ? pi[mm] : qp[k - mm] * pi[mm]);
+            pj[row * ST] = v.hi;
+            pj[(W + row) * ST] = v.lo;
+        }
+}
+
+template <int N, int ST>
+__device__ __forceinline__ void site_split_dd(const KernelArgs &a, const float *red, int G, int tid, int nthr,
+                                              bool act, float *sres, float *fr, float *part)
+{
+    constexpr int W = (N + 1) * (N + 1);
+    if (tid < ST) site_frame_dd<N, ST>(a, red, G, tid, act, fr, sres);
+    __syncthreads();
+    for (int e = tid; e < (N + 1) * ST; e += nthr) site_direction_dd<N, ST>(a, fr, e / ST, e % ST, part);
+    __syncthreads();
+    for (int e = tid; e < W * ST; e += nthr) {
+        df64 acc = dd(part[e], part[W * ST + e]);
+#pragma unroll
+        for (int j = 1; j <= N; ++j) acc = acc + dd(part[j * 2 * W * ST + e], part[(j * 2 * W + W) * ST + e]);
+        sres[e] = acc.hi;
+        sres[W * ST + e] = acc.lo;
+    }
+    __syncthreads();
+}
+
 // St: storage type; R: per-population arithmetic; LR: per-site arithmetic
 // (moment sums, Landau frame, equilibrium coefficients); N: quadrature order;
 // P: populations per thread (compile-time upper bound); TWO_D: ny > 1;
@@ -716,13 +995,25 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     if (MODE == MODE_MOMENTS && g != 0) return;
 
     // the Landau frame of the tile's 32 sites and every warp's own shell coefficients:
-    // with an FP64 per-site part once per site (ONCE), else in every warp
+    // with an FP64 per-site part once per site (ONCE), with a double-float one
+    // once per site (DDS: FP32 storage, FP32 LR), else in every warp
     constexpr bool ONCE = (sizeof(LR) == 8) && STEP && !QUANT;
+    constexpr bool DDS = (sizeof(St) == 4) && (sizeof(LR) == 4) && STEP && !QUANT;
     constexpr int W = (N + 1) * (N + 1);
-    LR *wsh = reinterpret_cast<LR *>(smem_raw + size_t(5) * G * 32 * sizeof(LR)); // [W + 3][32]
+    // ONCE: [W + 3][32] LR; DDS: [2 W + 3][32] floats (the sums as hi, lo rows, then
+    // U^a / tau), then site_split_dd's frame and partial sums
+    LR *wsh = reinterpret_cast<LR *>(smem_raw + size_t(5) * G * 32 * sizeof(LR));
     (void)wsh;
-    LR n, eps, U0, Ux, Uy, T;
-    if (MODE == MODE_INIT) {
+    LR n = LR(0), eps = LR(0), U0 = LR(0), Ux = LR(0), Uy = LR(0), T = LR(0);
+    if constexpr (DDS) {
+        // FP32 storage: the moment fold, the Landau frame and the shell-independent
+        // sums in double-float (FP64-class accuracy on the FP32 pipes), split over
+        // the CTA's warps by sample direction; U^a / tau follow in rows 2 W + 0..2
+        float *sres = reinterpret_cast<float *>(wsh);
+        float *fr = sres + (2 * W + 3) * 32;
+        site_split_dd<N, 32>(a, reinterpret_cast<const float *>(red), G, g * 32 + lane, G * 32, act, sres, fr,
+                             fr + kSplitFrameRows(N) * 32);
+    } else if (MODE == MODE_INIT) {
         const double bx = a.in_bx[site], by = a.in_by[site];
         const double gam = 1.0 / sqrt(1.0 - bx * bx - by * by);
         n = LR(a.in_n[site]);
@@ -802,12 +1093,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     R cr[NC];
     if constexpr (QUANT)
         shell_coefficients_tk<N, LR, R>(a, r, tkq, U0, Ux, Uy, cr);
+    else if constexpr (DDS)
+        shell_from_sums_dd<N>(a, r, reinterpret_cast<const float *>(wsh) + lane, 32, cr);
     else if constexpr (ONCE)
         shell_from_sums<N, LR, R>(a, r, wsh + lane, 32, cr);
     else
         shell_coefficients<N, LR, R>(a, r, n, T, U0, Ux, Uy, cr);
     const LR itau = Par<LR>::inv_tau(a);
-    const R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
+    R o0 = R(U0 * itau), o1 = R(Ux * itau), o2 = R(Uy * itau);
+    if constexpr (DDS) {
+        o0 = wsh[(2 * W + 0) * 32 + lane];
+        o1 = wsh[(2 * W + 1) * 32 + lane];
+        o2 = wsh[(2 * W + 2) * 32 + lane];
+    }
     constexpr bool kSR = (sizeof(St) <= 4) && STEP; // FP32 and 16-bit stores round stochastically
     unsigned rng = 0;
     if (kSR) rng = mix32(unsigned(site) * 64u + unsigned(g) ^ mix32(__ldcg(a.ctr) * 0x9E3779B9u + 1u));

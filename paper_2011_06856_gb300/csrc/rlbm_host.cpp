@@ -215,9 +215,11 @@ bool make_onlattice_quadrature(Quad &q)
 
 // ---------------------------------------------------------------- handle
 
-// FP64 per-site tables (moment folds, projection weights) for the per-tile,
-// TMA-staged and batched kernels of non-FP64 storage, whose per-site part then
-// runs in FP64 (the two-sites-per-lane kernels run it in double-float):
+// FP64 per-site tables (moment folds, projection weights) for the kernels of
+// non-FP64 storage whose per-site part runs in FP64: the init and moments
+// passes, the TMA-staged per-tile kernel, N >= 4 and the quantum statistics.
+// (FP32-storage steps with N <= 3 in the per-tile, batched and
+// two-sites-per-lane kernels run it in double-float from the split tables.)
 //  - FP32 storage: an FP32 per-site part carries the conserved moments to a
 //    relative bias of about 4e-7 per step, which the collision accumulates
 //    linearly (1e-5 after a few hundred steps at tau ~ 4);
@@ -603,9 +605,17 @@ cudaError_t launch(rlbm_t *h, int mode, const rlbmk::KernelArgs &a)
         if (e == cudaSuccess) ++h->launches;
         return e;
     }
+    // an FP32-storage step carries its per-site part in double-float (N = 2, 3)
+    const bool dd_step = mode == rlbmk::MODE_STEP && h->prec == RLBM_FP32 && h->N <= 3;
+    const size_t smem_dd = rlbmk::tile_smem_bytes_dd(h->N, h->G);
     if (mode == rlbmk::MODE_STEP && h->q.onlat) { // perfect streaming (FP32/FP64, P = 12: create, set_tiling)
         e = h->prec == RLBM_FP64 ? rlbmk::launch_lattice_f64(two_d, grid, block, smem, h->stream, a)
-                                 : rlbmk::launch_lattice_f32(two_d, grid, block, smem, h->stream, a);
+                                 : rlbmk::launch_lattice_f32(two_d, grid, block, smem_dd, h->stream, a);
+        if (e == cudaSuccess) ++h->launches;
+        return e;
+    }
+    if (dd_step) {
+        e = rlbmk::launch_f32_dd(h->N, h->P, two_d, full, grid, block, smem_dd, h->stream, a);
         if (e == cudaSuccess) ++h->launches;
         return e;
     }

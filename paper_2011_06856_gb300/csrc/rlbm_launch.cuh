@@ -100,4 +100,40 @@ static cudaError_t launch_lattice_t(bool two_d, dim3 grid, dim3 block, size_t sm
     return cudaGetLastError();
 }
 
+// FP32 storage, step kernels with the double-float per-site part (DDS in
+// rlbm_kernel); the init and moments passes stay FP64.
+template <int N, int P>
+static cudaError_t launch_dd_np(bool two_d, bool full, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                const KernelArgs &a)
+{
+    void (*k)(const KernelArgs);
+    if (full)
+        k = two_d ? rlbm_kernel<float, float, float, N, P, true, MODE_STEP, true>
+                  : rlbm_kernel<float, float, float, N, P, false, MODE_STEP, true>;
+    else
+        k = two_d ? rlbm_kernel<float, float, float, N, P, true, MODE_STEP, false>
+                  : rlbm_kernel<float, float, float, N, P, false, MODE_STEP, false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_dd_n(int P, bool two_d, bool full, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               const KernelArgs &a)
+{
+    switch (P) {
+    case 8: return launch_dd_np<N, 8>(two_d, full, grid, block, smem, st, a);
+    case 12: return launch_dd_np<N, 12>(two_d, full, grid, block, smem, st, a);
+    case 16: return launch_dd_np<N, 16>(two_d, full, grid, block, smem, st, a);
+    case 24: return launch_dd_np<N, 24>(two_d, full, grid, block, smem, st, a);
+    case 32: return launch_dd_np<N, 32>(two_d, full, grid, block, smem, st, a);
+    case 48: return launch_dd_np<N, 48>(two_d, full, grid, block, smem, st, a);
+    case 64: return launch_dd_np<N, 64>(two_d, full, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 } // namespace rlbmk

@@ -286,116 +286,6 @@ __device__ __forceinline__ void pair_site_solve(const KernelArgs &a, const float
     sres[((N + 1) * (N + 1) + 2) * kPairSites + s] = Uy * itau;
 }
 
-// The per-site part for site s with FP64-class accuracy (FP32 storage), in
-// double-float arithmetic (rlbm_df64.cuh): the warps' FP32 angular sums are
-// folded into N^a and T^ab (Eq. discrete_sum_moments) in double-float, the
-// Landau frame is solved in double-float (landau_dd), and the shell-independent
-// equilibrium sums w_{m,k} = n T^(k-1) acc_{m,k} are formed in double-float
-// and written as hi rows 0 .. (N+1)^2 - 1 and lo rows (N+1)^2 .. 2 (N+1)^2 - 1
-// of sres; U^a / tau follow at rows 2 (N+1)^2 + 0..2 (FP32: the relaxation
-// rate enters the conserved moments only at second order).  An FP32 per-site
-// part carries the conserved moments to a relative bias of about 4e-7 per
-// step (rounding of the moment fold, the frame and the radial projection,
-// which cancels about one digit); the collision feeds omega of that into the
-// state every step and it grows linearly; in double-float it is below 1e-12.
-template <int N>
-__device__ __forceinline__ void pair_site_solve_dd(const KernelArgs &a, const float *red, int G, int s, bool act,
-                                                   float *sres)
-{
-    constexpr int W = (N + 1) * (N + 1);
-    df64 m[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) m[u] = dd(a.off_f[u], a.off_l[u]);
-#pragma unroll
-    for (int rr = 0; rr <= N; ++rr) {
-        df64 p0 = dd(0.f), pc = dd(0.f), ps = dd(0.f), pcc = dd(0.f), pcs = dd(0.f);
-        for (int qq = 0; qq < a.Gs; ++qq) {
-            const int w = rr * a.Gs + qq;
-            p0 = p0 + red[(0 * G + w) * kPairSites + s];
-            pc = pc + red[(1 * G + w) * kPairSites + s];
-            ps = ps + red[(2 * G + w) * kPairSites + s];
-            pcc = pcc + red[(3 * G + w) * kPairSites + s];
-            pcs = pcs + red[(4 * G + w) * kPairSites + s];
-        }
-        const float2 t1 = __ldg(a.shell2 + 2 * rr), t2 = __ldg(a.shell2 + 2 * rr + 1);
-        const df64 f1 = dd(t1.x, t1.y), f2v = dd(t2.x, t2.y);
-        m[0] = m[0] + f1 * p0;
-        m[1] = m[1] + f1 * pc;
-        m[2] = m[2] + f1 * ps;
-        m[3] = m[3] + f2v * p0;
-        m[4] = m[4] + f2v * pc;
-        m[5] = m[5] + f2v * ps;
-        m[6] = m[6] + f2v * pcc;
-        m[7] = m[7] + f2v * pcs;
-    }
-    df64 n, eps, U0, Ux, Uy;
-    const bool ok = landau_dd(m, n, eps, U0, Ux, Uy);
-    if (!ok && act) atomicOr(a.status, 1);
-    const df64 T = eps / (n * 2.f);
-    const df64 inv1g = dd(1.f) / (U0 + 1.f);
-    // boosted rest-frame directions: acc_{m,k} = sum_j q0^(k-m) z^m (as in shell_coefficients)
-    df64 accr[N + 1][N + 1], acci[N + 1][N + 1];
-#pragma unroll
-    for (int mm = 0; mm <= N; ++mm)
-#pragma unroll
-        for (int k = 0; k <= N; ++k) { accr[mm][k] = dd(0.f); acci[mm][k] = dd(0.f); }
-#pragma unroll
-    for (int j = 0; j <= N; ++j) {
-        const df64 cj = dd(a.smp_cf[j], a.smp_cl[j]), sj = dd(a.smp_sf[j], a.smp_sl[j]);
-        const df64 un = Ux * cj + Uy * sj;
-        const df64 h = un * inv1g + 1.f;
-        df64 qp[N + 1], pr[N + 1], pi[N + 1];
-        qp[1] = U0 + un;
-        pr[1] = cj + Ux * h;
-        pi[1] = sj + Uy * h;
-#pragma unroll
-        for (int t = 2; t <= N; ++t) {
-            qp[t] = qp[t - 1] * qp[1];
-            pr[t] = pr[t - 1] * pr[1] - pi[t - 1] * pi[1];
-            pi[t] = pr[t - 1] * pi[1] + pi[t - 1] * pr[1];
-        }
-#pragma unroll
-        for (int k = 1; k <= N; ++k) accr[0][k] = accr[0][k] + qp[k];
-#pragma unroll
-        for (int mm = 1; mm <= N; ++mm) {
-            accr[mm][mm] = accr[mm][mm] + pr[mm];
-            acci[mm][mm] = acci[mm][mm] + pi[mm];
-#pragma unroll
-            for (int k = mm + 1; k <= N; ++k) {
-                accr[mm][k] = accr[mm][k] + qp[k - mm] * pr[mm];
-                acci[mm][k] = acci[mm][k] + qp[k - mm] * pi[mm];
-            }
-        }
-    }
-    accr[0][0] = dd(float(N + 1));
-    df64 tk[N + 1];
-    tk[0] = n / T;
-    tk[1] = n;
-#pragma unroll
-    for (int k = 2; k <= N; ++k) tk[k] = tk[k - 1] * T;
-    int row = 0;
-#pragma unroll
-    for (int mm = 0; mm <= N; ++mm)
-#pragma unroll
-        for (int k = mm; k <= N; ++k, ++row) {
-            const df64 w = tk[k] * accr[mm][k];
-            sres[row * kPairSites + s] = w.hi;
-            sres[(W + row) * kPairSites + s] = w.lo;
-        }
-#pragma unroll
-    for (int mm = 1; mm <= N; ++mm)
-#pragma unroll
-        for (int k = mm; k <= N; ++k, ++row) {
-            const df64 w = tk[k] * acci[mm][k];
-            sres[row * kPairSites + s] = w.hi;
-            sres[(W + row) * kPairSites + s] = w.lo;
-        }
-    const float itau = a.inv_tau_f;
-    sres[(2 * W + 0) * kPairSites + s] = to_float(U0) * itau;
-    sres[(2 * W + 1) * kPairSites + s] = to_float(Ux) * itau;
-    sres[(2 * W + 2) * kPairSites + s] = to_float(Uy) * itau;
-}
-
 // Shell r's equilibrium coefficients for the lane's two sites, in the basis
 // (1, c, s, cc, cs [, c cc, s cc]) of the pair kernels' second pass, and the
 // relaxation factors o = U^a / tau.  The Fourier coefficients are
