@@ -112,6 +112,20 @@ __host__ __device__ constexpr size_t pair_smem_bytes(int N, int G, bool bulk, in
     return bulk ? pair_slots_offset(N, G) + size_t(G) * kPairDepth * pair_slot_bytes(elem_bytes, two_d)
                 : pair_bars_offset(N, G);
 }
+// Rows of site_split_dd's frame [6 + 2 (N+1)] and partial sums [N+1][2 (N+1)^2].
+__host__ __device__ constexpr int split_rows(int N) { return 6 + 2 * (N + 1) + (N + 1) * 2 * (N + 1) * (N + 1); }
+// The two-sites-per-lane kernels with FP32 storage split their double-float
+// per-site part over the warps when the CTA has a thread for every (sample
+// direction, site) item; its frame and partial sums then follow the layout
+// above ([split_rows(N)][64] floats).  With fewer warps two of them solve the
+// sites whole (the split's extra shared memory would cost more occupancy than
+// the shorter chain gains).
+__host__ __device__ constexpr bool pair_split(int N, int G) { return G * 32 >= (N + 1) * kPairSites; }
+__host__ __device__ constexpr size_t pair_smem_total(int N, int G, bool bulk, int elem_bytes, bool two_d)
+{
+    return pair_smem_bytes(N, G, bulk, elem_bytes, two_d) +
+           (elem_bytes == 4 && pair_split(N, G) ? size_t(split_rows(N)) * kPairSites * 4 : 0);
+}
 
 // Arguments of the persistent TMA-staged step kernel.
 struct alignas(128) TmaArgs {

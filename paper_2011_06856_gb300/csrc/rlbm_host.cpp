@@ -658,8 +658,9 @@ cudaError_t launch_pair(rlbm_t *h, const rlbmk::KernelArgs &a)
 {
     const dim3 grid((h->grid.nx + rlbmk::kPairSites - 1) / rlbmk::kPairSites, h->grid.ny);
     const dim3 block(32, h->G);
-    const bool two_d = h->grid.ny > 1, bulk = h->pair_bulk;
-    const size_t smem = rlbmk::pair_smem_bytes(h->N, h->G, bulk, int(storage_size(h->prec)), two_d);
+    // the population-groups kernel has no bulk staging
+    const bool two_d = h->grid.ny > 1, bulk = h->pair_bulk && h->R == 1;
+    const size_t smem = rlbmk::pair_smem_total(h->N, h->G, bulk, int(storage_size(h->prec)), two_d);
     cudaError_t e;
     if (h->R > 1) { // several population groups per warp (FP32 storage: pair_possible)
         e = rlbmk::launch_pair_groups_f32(h->N, h->P, two_d, grid, block, smem, h->stream, a);

@@ -545,12 +545,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_ke
     red2[(4 * G + g) * 32 + lane] = scs;
     __syncthreads();
     constexpr bool DD = sizeof(St) == 4; // FP32 storage: FP64-class per-site part
-    if (g < 2) {
-        const int s = g * 32 + lane;
-        if constexpr (DD) pair_site_solve_dd<N>(a, red, G, s, x0 + s < a.nx, sres);
-        else pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
+    if (DD && pair_split(N, G)) { // double-float, split over the warps by sample direction
+        float *fr = reinterpret_cast<float *>(smem_raw + pair_smem_bytes(N, G, BULK, 4, TWO_D));
+        const int tid = g * 32 + lane;
+        site_split_dd<N, kPairSites>(a, red, G, tid, G * 32, x0 + tid < a.nx, sres, fr,
+                                     fr + kSplitFrameRows(N) * kPairSites);
+    } else {
+        if (g < 2) {
+            const int s = g * 32 + lane;
+            if constexpr (DD) pair_site_solve_dd<N>(a, red, G, s, x0 + s < a.nx, sres);
+            else pair_site_solve<N>(a, red, G, s, x0 + s < a.nx, sres);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     // this warp's shell: its equilibrium coefficients for its two sites
     float2 cr[NC], o0, o1, o2;
@@ -691,11 +698,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1) rlbm_pair_gr
     red2[(3 * G + g) * 32 + lane] = scc;
     red2[(4 * G + g) * 32 + lane] = scs;
     __syncthreads();
-    if (g < 2) {
-        const int s = g * 32 + lane;
-        pair_site_solve_dd<N>(a, red, G, s, x0 + s < a.nx, sres);
+    if (pair_split(N, G)) { // the per-site part in double-float, split over the warps by sample direction
+        float *fr = reinterpret_cast<float *>(smem_raw + pair_bars_offset(N, G));
+        const int tid = g * 32 + lane;
+        site_split_dd<N, kPairSites>(a, red, G, tid, G * 32, x0 + tid < a.nx, sres, fr,
+                                     fr + kSplitFrameRows(N) * kPairSites);
+    } else {
+        if (g < 2) {
+            const int s = g * 32 + lane;
+            pair_site_solve_dd<N>(a, red, G, s, x0 + s < a.nx, sres);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     // this warp's shell coefficients for its two sites (as in rlbm_pair_kernel)
     float2 cr[NC], o0, o1, o2;
