@@ -614,14 +614,14 @@ __device__ __forceinline__ void pair_site_solve_dd(const KernelArgs &a, const fl
     for (int u = 0; u < 8; ++u) m[u] = dd(a.off_f[u], a.off_l[u]);
 #pragma unroll
     for (int rr = 0; rr <= N; ++rr) {
-        df64 p0 = dd(0.f), pc = dd(0.f), ps = dd(0.f), pcc = dd(0.f), pcs = dd(0.f);
+        float p0 = 0.f, pc = 0.f, ps = 0.f, pcc = 0.f, pcs = 0.f; // the warps' FP32 sums, in FP32
         for (int qq = 0; qq < a.Gs; ++qq) {
             const int w = rr * a.Gs + qq;
-            p0 = p0 + red[(0 * G + w) * ST + s];
-            pc = pc + red[(1 * G + w) * ST + s];
-            ps = ps + red[(2 * G + w) * ST + s];
-            pcc = pcc + red[(3 * G + w) * ST + s];
-            pcs = pcs + red[(4 * G + w) * ST + s];
+            p0 += red[(0 * G + w) * ST + s];
+            pc += red[(1 * G + w) * ST + s];
+            ps += red[(2 * G + w) * ST + s];
+            pcc += red[(3 * G + w) * ST + s];
+            pcs += red[(4 * G + w) * ST + s];
         }
         const float2 t1 = __ldg(a.shell2 + 2 * rr), t2 = __ldg(a.shell2 + 2 * rr + 1);
         const df64 f1 = dd(t1.x, t1.y), f2v = dd(t2.x, t2.y);
@@ -741,8 +741,8 @@ __device__ __forceinline__ void shell_from_sums_dd(const KernelArgs &a, int r, c
 //  1. threads tid < ST: moment fold and Landau frame of site tid; U^a and
 //     t_k = n T^(k-1) (double-floats) into fr, U^a / tau into sres rows 2 W + 0..2;
 //  2. item (j, s), j = 0..N: the boosted sample direction j's terms of the sums,
-//     t_k acc_{m,k}(j) (double-floats), into part[j];
-//  3. item (row, s): w_{m,k} = sum_j part[j], into sres (hi rows, then lo rows).
+//     acc_{m,k}(j) = q0^(k-m) z^m (double-floats), into part[j];
+//  3. item (row, s): w_{m,k} = t_k sum_j part[j], into sres (hi rows, then lo rows).
 // The serial chain per site falls from the whole solve to the frame plus one
 // direction; the partial sums cost (N + 1) 2 W ST floats of shared memory.
 // Layouts (row stride ST): fr [kSplitFrameRows(N)][ST]: U0, Ux, Uy as hi, lo
@@ -754,19 +754,22 @@ __device__ __forceinline__ void site_frame_dd(const KernelArgs &a, const float *
                                               float *fr, float *sres)
 {
     constexpr int W = (N + 1) * (N + 1);
+    // The warps' FP32 angular sums of one shell are added in FP32 (one more
+    // rounding of the kind the per-warp accumulation already carries); the shell
+    // factors and the fold across shells are double-float.
     df64 m[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) m[u] = dd(a.off_f[u], a.off_l[u]);
 #pragma unroll
     for (int rr = 0; rr <= N; ++rr) {
-        df64 p0 = dd(0.f), pc = dd(0.f), ps = dd(0.f), pcc = dd(0.f), pcs = dd(0.f);
+        float p0 = 0.f, pc = 0.f, ps = 0.f, pcc = 0.f, pcs = 0.f;
         for (int qq = 0; qq < a.Gs; ++qq) {
             const int w = rr * a.Gs + qq;
-            p0 = p0 + red[(0 * G + w) * ST + s];
-            pc = pc + red[(1 * G + w) * ST + s];
-            ps = ps + red[(2 * G + w) * ST + s];
-            pcc = pcc + red[(3 * G + w) * ST + s];
-            pcs = pcs + red[(4 * G + w) * ST + s];
+            p0 += red[(0 * G + w) * ST + s];
+            pc += red[(1 * G + w) * ST + s];
+            ps += red[(2 * G + w) * ST + s];
+            pcc += red[(3 * G + w) * ST + s];
+            pcs += red[(4 * G + w) * ST + s];
         }
         const float2 t1 = __ldg(a.shell2 + 2 * rr), t2 = __ldg(a.shell2 + 2 * rr + 1);
         const df64 f1 = dd(t1.x, t1.y), f2v = dd(t2.x, t2.y);
@@ -810,9 +813,6 @@ __device__ __forceinline__ void site_direction_dd(const KernelArgs &a, const flo
     const df64 U0 = dd(fr[0 * ST + s], fr[1 * ST + s]);
     const df64 Ux = dd(fr[2 * ST + s], fr[3 * ST + s]);
     const df64 Uy = dd(fr[4 * ST + s], fr[5 * ST + s]);
-    df64 tk[N + 1];
-#pragma unroll
-    for (int k = 0; k <= N; ++k) tk[k] = dd(fr[(6 + 2 * k) * ST + s], fr[(7 + 2 * k) * ST + s]);
     const df64 inv1g = dd(1.f) / (U0 + 1.f);
     const df64 cj = dd(a.smp_cf[j], a.smp_cl[j]), sj = dd(a.smp_sf[j], a.smp_sl[j]);
     const df64 un = Ux * cj + Uy * sj;
@@ -829,14 +829,14 @@ __device__ __forceinline__ void site_direction_dd(const KernelArgs &a, const flo
     }
     float *pj = part + j * (2 * W) * ST + s;
     int row = 0;
-    // Re rows: m = 0 (q0^k), then m = 1..N (q0^(k-m) Re z^m)
+    // Re rows: m = 0 (q0^k; the k = 0 row is 1 and is not stored), then
+    // m = 1..N (q0^(k-m) Re z^m); the reduction multiplies by t_k
 #pragma unroll
     for (int mm = 0; mm <= N; ++mm)
 #pragma unroll
         for (int k = mm; k <= N; ++k, ++row) {
-            df64 v;
-            if (mm == 0) v = (k == 0) ? tk[0] : tk[k] * qp[k];
-            else v = tk[k] * ((k == mm) ? pr[mm] : qp[k - mm] * pr[mm]);
+            if (mm == 0 && k == 0) continue;
+            const df64 v = (mm == 0) ? qp[k] : ((k == mm) ? pr[mm] : qp[k - mm] * pr[mm]);
             pj[row * ST] = v.hi;
             pj[(W + row) * ST] = v.lo;
         }
@@ -844,10 +844,32 @@ __device__ __forceinline__ void site_direction_dd(const KernelArgs &a, const flo
     for (int mm = 1; mm <= N; ++mm)
 #pragma unroll
         for (int k = mm; k <= N; ++k, ++row) {
-            const df64 v = tk[k] * ((k == mm) ? pi[mm] : qp[k - mm] * pi[mm]);
+            const df64 v = (k == mm) ? pi[mm] : qp[k - mm] * pi[mm];
             pj[row * ST] = v.hi;
             pj[(W + row) * ST] = v.lo;
         }
+}
+
+// The power k of T in row `row` of the sums (Re rows m = 0..N, k = m..N, then
+// Im rows m = 1..N, k = m..N).
+template <int N>
+__device__ __forceinline__ int sums_row_k(int row)
+{
+    int k = 0;
+    bool found = false;
+#pragma unroll
+    for (int mm = 0; mm <= N; ++mm) {
+        const int len = N + 1 - mm;
+        if (!found && row < len) { k = mm + row; found = true; }
+        if (!found) row -= len;
+    }
+#pragma unroll
+    for (int mm = 1; mm <= N; ++mm) {
+        const int len = N + 1 - mm;
+        if (!found && row < len) { k = mm + row; found = true; }
+        if (!found) row -= len;
+    }
+    return k;
 }
 
 template <int N, int ST>
@@ -860,9 +882,17 @@ __device__ __forceinline__ void site_split_dd(const KernelArgs &a, const float *
     for (int e = tid; e < (N + 1) * ST; e += nthr) site_direction_dd<N, ST>(a, fr, e / ST, e % ST, part);
     __syncthreads();
     for (int e = tid; e < W * ST; e += nthr) {
-        df64 acc = dd(part[e], part[W * ST + e]);
+        const int row = e / ST, s = e - row * ST;
+        const int k = sums_row_k<N>(row);
+        df64 acc;
+        if (row == 0) {
+            acc = dd(float(N + 1)); // sum over the N + 1 directions of q0^0
+        } else {
+            acc = dd(part[e], part[W * ST + e]);
 #pragma unroll
-        for (int j = 1; j <= N; ++j) acc = acc + dd(part[j * 2 * W * ST + e], part[(j * 2 * W + W) * ST + e]);
+            for (int j = 1; j <= N; ++j) acc = acc + dd(part[j * 2 * W * ST + e], part[(j * 2 * W + W) * ST + e]);
+        }
+        acc = acc * dd(fr[(6 + 2 * k) * ST + s], fr[(7 + 2 * k) * ST + s]);
         sres[e] = acc.hi;
         sres[W * ST + e] = acc.lo;
     }
