@@ -69,11 +69,13 @@ __host__ __device__ constexpr int tab_width(int N) { return ((2 * N + 5) + 3) / 
 // Dynamic shared memory of the per-tile kernel (rlbm_kernel): the angular sums
 // [5][G][32] in the per-site type (ls bytes), then either the per-site sums
 // shared by the warps when the per-site part runs once per site in FP64
-// [(N+1)^2 + 3][32] or, for the quantum statistics, (eta, T) [2][32] doubles.
+// [(N+1)^2 + 3][32] or, for the quantum statistics, T and the radial weights
+// t_0..t_N [1 + N + 1][32] doubles.
 __host__ __device__ constexpr size_t tile_smem_bytes(int N, int G, size_t ls, bool quantum)
 {
     return ls * 5 * size_t(G) * 32 +
-           (quantum ? 2 * 32 * sizeof(double) : (ls == 8 ? size_t((N + 1) * (N + 1) + 3) * 32 * 8 : 0));
+           (quantum ? size_t(N + 2) * 32 * sizeof(double)
+                    : (ls == 8 ? size_t((N + 1) * (N + 1) + 3) * 32 * 8 : 0));
 }
 // The same for an FP32-storage step with the double-float per-site part split
 // over the warps (site_split_dd): FP32 angular sums, then [2 (N+1)^2 + 3][32]

@@ -1087,27 +1087,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
     // (after the angular sums: qsh = [2][32] doubles); in the moments pass only warp 0 runs.
     LR tkq[N + 1];
     if constexpr (QUANT) {
+        // warp 0 solves each site and forms its radial weights once; the other
+        // warps read T and t_k from shared memory (qsh = [1 + N + 1][32] doubles)
         double qeta = 0.0, qT = T;
         double *qsh = reinterpret_cast<double *>(smem_raw + size_t(5) * G * 32 * sizeof(LR));
         if (g == 0) {
             // warm start from the site's eta of the previous solve, kept in a.qeta
             const double x0 = a.qeta ? a.qeta[site] : __longlong_as_double(0x7ff8000000000000ll);
+            double phr[N + 1]; // phi_1..phi_{N+1} at the solved eta (steps)
             const bool ok = (MODE == MODE_INIT) ? stat_fugacity(n, T, a.gdeg, a.stat, qeta)
-                                                : stat_solve(n, eps, a.gdeg, a.stat, qeta, qT, x0);
+                                                : stat_solve(n, eps, a.gdeg, a.stat, qeta, qT, x0,
+                                                             MODE == MODE_MOMENTS ? nullptr : phr,
+                                                             MODE == MODE_MOMENTS ? 0 : N + 1);
             if (!ok && act) atomicOr(a.status, 1);
             if (a.qeta && act && MODE != MODE_MOMENTS) a.qeta[site] = qeta;
             if (MODE != MODE_MOMENTS) {
-                qsh[lane] = qeta;
-                qsh[32 + lane] = qT;
+                if (MODE == MODE_INIT) stat_radial<N>(qT, qeta, a.gdeg, a.stat, tkq);
+                else stat_radial_from_phi<N>(qT, a.gdeg, phr, tkq);
+                qsh[lane] = qT;
+#pragma unroll
+                for (int k = 0; k <= N; ++k) qsh[(1 + k) * 32 + lane] = tkq[k];
             }
         }
         if (MODE != MODE_MOMENTS) {
             __syncthreads();
-            qeta = qsh[lane];
-            qT = qsh[32 + lane];
+            qT = qsh[lane];
+#pragma unroll
+            for (int k = 0; k <= N; ++k) tkq[k] = qsh[(1 + k) * 32 + lane];
         }
         T = qT;
-        stat_radial<N>(T, qeta, a.gdeg, a.stat, tkq);
     }
     if (MODE == MODE_MOMENTS) {
         if (act) {
