@@ -264,16 +264,31 @@ struct alignas(128) PairTmaArgs {
 // 16 bytes of halo on each side), the pair table [npop][3] float4, the
 // angular sums [5][G][64], the per-site results [pair_site_rows(N)][64], the
 // mbarrier; + 1 KB of slack to align the base for the TMA.
+// The angular sums and the per-site results are needed only after pass 1, when
+// the stage is dead: where the stage is large enough they alias it (alias = true;
+// the kernel then separates the last stage read from the first write by a CTA
+// barrier), which lets more CTAs share an SM.
 struct PairTmaSmem {
     size_t stage, tab, red, sres, bar, total;
+    bool alias;
     __host__ __device__ PairTmaSmem(int N, int G, int npop, int es, bool two_d)
     {
         const size_t BW = size_t(kPairSites) + 2 * size_t(16 / es);
+        const size_t stage_bytes = size_t(two_d ? 2 : 1) * size_t(npop) * BW * size_t(es);
+        const size_t red_bytes = size_t(5) * G * kPairSites * 4;
+        const size_t sres_bytes = size_t(pair_site_rows(N)) * kPairSites * 4;
         stage = 0;
-        tab = align_up(size_t(two_d ? 2 : 1) * size_t(npop) * BW * size_t(es), 128);
-        red = align_up(tab + size_t(npop) * 3 * 16, 16);
-        sres = red + size_t(5) * G * kPairSites * 4;
-        bar = align_up(sres + size_t(pair_site_rows(N)) * kPairSites * 4, 16);
+        tab = align_up(stage_bytes, 128);
+        alias = stage_bytes >= red_bytes + sres_bytes;
+        if (alias) {
+            red = 0;
+            sres = red_bytes;
+            bar = align_up(tab + size_t(npop) * 3 * 16, 16);
+        } else {
+            red = align_up(tab + size_t(npop) * 3 * 16, 16);
+            sres = red + red_bytes;
+            bar = align_up(sres + sres_bytes, 16);
+        }
         total = bar + 16 + 1024;
     }
 };

@@ -60,8 +60,7 @@ template <> __device__ __forceinline__ void st2_rs<__nv_bfloat16>(__nv_bfloat16 
 }
 
 template <class St, int N, int PP, bool TWO_D>
-__global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1)
-    rlbm_pair_tma_kernel(const __grid_constant__ PairTmaArgs ta)
+__device__ __forceinline__ void pair_tma_body(const PairTmaArgs &ta)
 {
     constexpr int NC = 2 * N + 1;
     constexpr int PQ = 3; // float4 per population in the pair table
@@ -178,6 +177,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1)
         scc = __ffma2_rn(c, cv, scc);
         scs = __ffma2_rn(sn, cv, scs);
     }
+    if (L.alias) __syncthreads(); // red and sres alias the stage: every warp is done reading it
     float2 *red2 = reinterpret_cast<float2 *>(red);
     red2[(0 * G + g) * 32 + lane] = s0;
     red2[(1 * G + g) * 32 + lane] = sc;
@@ -228,12 +228,32 @@ __global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1)
     if (tid == 0) advance_launch_counter(a.ctr, gridDim.x * gridDim.y);
 }
 
+// FP32 storage: the launch bounds of the other two-sites-per-lane kernels.
+template <class St, int N, int PP, bool TWO_D>
+__global__ void __launch_bounds__(kMaxWarps * 32, PP <= 16 ? 2 : 1)
+    rlbm_pair_tma_kernel(const __grid_constant__ PairTmaArgs ta)
+{
+    pair_tma_body<St, N, PP, TWO_D>(ta);
+}
+
+// 16-bit storage: with PP <= 16, at most 56 registers, so that four CTAs of nine
+// warps (the 2048^2 N = 2 K = 48 tiling, 54 KB of shared memory with the aliased
+// sums) share an SM.
+template <class St, int N, int PP, bool TWO_D>
+__global__ void __maxnreg__(PP <= 16 ? 56 : 128) rlbm_pair_tma_kernel16(const __grid_constant__ PairTmaArgs ta)
+{
+    pair_tma_body<St, N, PP, TWO_D>(ta);
+}
+
 template <class St, int N, int PP>
 static cudaError_t launch_pair_tma_np(bool two_d, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                       const PairTmaArgs &ta, int *bps)
 {
-    void (*k)(const PairTmaArgs) =
-        two_d ? rlbm_pair_tma_kernel<St, N, PP, true> : rlbm_pair_tma_kernel<St, N, PP, false>;
+    void (*k)(const PairTmaArgs);
+    if constexpr (sizeof(St) == 2)
+        k = two_d ? rlbm_pair_tma_kernel16<St, N, PP, true> : rlbm_pair_tma_kernel16<St, N, PP, false>;
+    else
+        k = two_d ? rlbm_pair_tma_kernel<St, N, PP, true> : rlbm_pair_tma_kernel<St, N, PP, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (bps) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, int(block.x * block.y), smem);
