@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="riemann2d_2048_N2K48",
-                    choices=sorted(W.WORKLOADS) + ["batch256", "closure4096", "closure_config5"])
+                    choices=sorted(W.WORKLOADS) + ["batch256", "closure4096", "closure4096_4000steps"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16", "bf16", "fp16n", "bf16n"])
     ap.add_argument("--timesteps", type=int, default=None,
                     help="override time steps per problem (default: the workload's)")
@@ -481,13 +481,13 @@ def run_closure(args):
 # Training runs of the config-5 closure: 1024^2 Riemann problems at four Kn,
 # snapshots every `every` steps over `steps` steps (1024 steps of a 1024^2
 # grid span the physical time of the 4000 deployed steps at 4096^2).
-CONFIG5_TRAIN = {"grid": 1024, "kn": (0.01, 0.1, 1.0, 5.0), "steps": 1024, "every": 64}
+CLOSURE_LONG_TRAIN = {"grid": 1024, "kn": (0.01, 0.1, 1.0, 5.0), "steps": 1024, "every": 64}
 
 
-def run_closure_config5(args):
-    """The learned closure at the size of the survey's fifth configuration.
+def run_closure_long(args):
+    """The learned closure trained on 1024^2 runs and deployed on 4096^2 for 4000 steps.
     Training data: 1024^2 four-quadrant Riemann runs at K = 128 (3 x 128 angles)
-    and Kn in {0.01, 0.1, 1, 5}, a snapshot every 32 of 512 steps; the network
+    and Kn in {0.01, 0.1, 1, 5}, a snapshot every 64 of 1024 steps; the network
     is trained on the GPU by the library's tensor-core kernels.  Deployment: a
     4096^2 Riemann problem (not in the training set) at K = 24 for 4000 steps with
     the correction after every step, judged against the plain K = 128 run of the
@@ -506,7 +506,7 @@ def run_closure_config5(args):
         dist.init_process_group("nccl")
     t0 = time.perf_counter()
     cl = R.Closure(2, 24, seed=7)
-    tr = CONFIG5_TRAIN
+    tr = CLOSURE_LONG_TRAIN
     X, T = CL.generate(cl, tr["grid"], 128, tr["kn"], tr["steps"], every=tr["every"])
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
@@ -518,7 +518,7 @@ def run_closure_config5(args):
     del X, T
     torch.cuda.empty_cache()
     n, steps, kn = 4096, 4000, 1.0
-    feat = CL.kn_feature(W.tau_from_kn(kn, n), CONFIG5_TRAIN["grid"])
+    feat = CL.kn_feature(W.tau_from_kn(kn, n), CLOSURE_LONG_TRAIN["grid"])
     fl = W.riemann_2d(n, n, CL.RIEMANN, jitter=0.01, seed=99)
     runs = {}
     for name, K, corrected in (("plain_K128", 128, False), ("corrected_K24", 24, True), ("plain_K24", 24, False),
@@ -554,7 +554,7 @@ def run_closure_config5(args):
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": 1, "warmup": 0,
             "ms_per_step": t_corr * 1e3 / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (bf16 network weights)", "data": "synthetic",
-            "config": {"workload": "closure_config5", "grid": [n, n], "N": 2, "K_coarse": 24, "K_judge": 128,
+            "config": {"workload": "closure4096_4000steps", "grid": [n, n], "N": 2, "K_coarse": 24, "K_reference": 128,
                        "kn": kn, "time_steps": steps, "runs": out, "stated_accuracy": tol,
                        "plain_runs_meeting_accuracy": plain_meets, "corrected_meets_accuracy":
                        max(out["corrected_K24"]["rel_l2_n_eps_vs_K128"]) <= tol,
@@ -581,8 +581,8 @@ def main():
     if args.workload == "closure4096" and args.impl == "ours":
         run_closure(args)
         return
-    if args.workload == "closure_config5" and args.impl == "ours":
-        run_closure_config5(args)
+    if args.workload == "closure4096_4000steps" and args.impl == "ours":
+        run_closure_long(args)
         return
     w = W.WORKLOADS[args.workload]
     precision = args.precision or w.precision
