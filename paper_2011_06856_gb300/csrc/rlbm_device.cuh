@@ -1098,7 +1098,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rlbm_kernel(const KernelArgs a
             const bool ok = (MODE == MODE_INIT) ? stat_fugacity(n, T, a.gdeg, a.stat, qeta)
                                                 : stat_solve(n, eps, a.gdeg, a.stat, qeta, qT, x0,
                                                              MODE == MODE_MOMENTS ? nullptr : phr,
-                                                             MODE == MODE_MOMENTS ? 0 : N + 1);
+                                                             MODE == MODE_MOMENTS ? 0 : N + 1,
+                                                             sizeof(St) == 8 ? 1e-10 : 1e-5);
             if (!ok && act) atomicOr(a.status, 1);
             if (a.qeta && act && MODE != MODE_MOMENTS) a.qeta[site] = qeta;
             if (MODE != MODE_MOMENTS) {

@@ -252,14 +252,17 @@ RLBM_HD double stat_presolve_fd(double L, double x, double lo, double hi)
 // (Maxwell-Boltzmann limit: -eta/2).  Start: x0 (the previous step's eta of the
 // site; NaN or out of range: the Maxwell-Boltzmann value), refined by FP32 Newton
 // steps for Fermi-Dirac; then FP64 Newton steps kept inside a bisection bracket
-// (at most 100), until a Newton step is below 1e-10 (1 + |eta|): with quadratic
-// convergence the accepted iterate is then exact to rounding.  phi_root (may be
+// (at most 100), until a Newton step is below tol (1 + |eta|).  With quadratic
+// convergence the accepted iterate's error is about the square of that step:
+// tol = 1e-10 leaves eta exact to rounding (FP64 storage); tol = 1e-5 accepts the
+// first FP64 step after the FP32 ones, whose error stays below 1e-12 (FP32
+// storage, whose own rounding is 1e-7).  phi_root (may be
 // NULL): phi_1..phi_nphi at the returned eta (nphi <= 6), from the last
 // evaluation by d phi_s / d eta = phi_{s-1} (the step is below 1e-10).  Returns
 // false for a Bose-Einstein state beyond condensation (no z < 1), or bad
 // input; eta then sits at the bracket end.
 RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, double &T, double x0,
-                         double *phi_root = nullptr, int nphi = 0)
+                         double *phi_root = nullptr, int nphi = 0, double tol = 1e-10)
 {
     const double twopi = 6.283185307179586477;
     if (!(n > 0.0) || !(e > 0.0)) { eta = -30.0; T = 1.0; return false; }
@@ -282,7 +285,7 @@ RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, do
         double xn = x - H / dH;
         const bool newton = xn > lo && xn < hi;
         if (!newton) xn = 0.5 * (lo + hi);
-        if (newton && fabs(xn - x) <= 1e-10 * (1.0 + fabs(x))) { x = xn; ok = true; break; }
+        if (newton && fabs(xn - x) <= tol * (1.0 + fabs(x))) { x = xn; ok = true; break; }
         x = xn;
         if (hi - lo < 1e-15 * (1.0 + fabs(x))) { ok = true; break; }
     }
@@ -290,8 +293,9 @@ RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, do
     eta = x;
     double phr[6];
     const double dx = x - xl;
-    if (fabs(dx) <= 1e-8 * (1.0 + fabs(x)) && phl[1] > 0.0) {
-        // phi_0 = d phi_1 / d eta, needed to first order only
+    if (fabs(dx) <= 1e-4 * (1.0 + fabs(x)) && phl[1] > 0.0) {
+        // phi_s(x) = phi_s(xl) + phi_{s-1}(xl) dx + O(dx^2); phi_0 = d phi_1 / d eta
+        // (dx <= tol: the second-order term is below 1e-10 relative for FP32 storage)
         const double phi0 = stat > 0 ? 1.0 / (1.0 + double(expf(float(-xl)))) : 1.0 / (exp(-xl) - 1.0);
         phr[0] = phl[0] + phi0 * dx;
         for (int q = 1; q < nq; ++q) phr[q] = phl[q] + phl[q - 1] * dx;
