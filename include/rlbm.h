@@ -158,6 +158,19 @@ int rlbm_statistics(const rlbm_t *h);
  * eta < 0).  NaN for arguments outside that range.  No GPU needed. */
 double rlbm_quantum_phi(int s, double eta, int statistics);
 
+/* Host evaluation of the kernels' (eta, T) solve for the quantum statistics:
+ * the equilibrium of statistics +1 / -1 and degeneracy g > 0 with density
+ * n > 0 and energy density e > 0 (2 pi g T^2 phi_2 = n, 4 pi g T^3 phi_3 = e).
+ * eta0: a start (the previous step's eta of a site), or NaN for the
+ * Maxwell-Boltzmann start.  fp32_storage != 0: the stopping rule of the
+ * FP32-storage kernels (FP64 Newton steps stop below 1e-5 (1 + |eta|): eta
+ * within about 1e-12 from a start near the root, 1e-9 from a cold one), else
+ * that of FP64 storage (below 1e-10: exact to rounding).  Writes eta and T (neither may be NULL) and returns 1, or 0 where
+ * no equilibrium exists (Bose-Einstein beyond condensation) or the input is
+ * not physical (eta and T are then written but meaningless).  No GPU needed. */
+int rlbm_quantum_solve(double n, double e, double g, int statistics, double eta0, int fp32_storage,
+                       double *eta, double *T);
+
 void rlbm_destroy(rlbm_t *h);
 
 /* Message of the most recent failure on h (or of the last failed create when

@@ -1212,6 +1212,16 @@ double rlbm_quantum_phi(int s, double eta, int statistics)
     return ph[s - 1];
 }
 
+int rlbm_quantum_solve(double n, double e, double g, int statistics, double eta0, int fp32_storage,
+                       double *eta, double *T)
+{
+    if (!eta || !T) return 0;
+    *eta = std::nan("");
+    *T = std::nan("");
+    if ((statistics != 1 && statistics != -1) || !(g > 0.0)) return 0;
+    return rlbmk::stat_solve(n, e, g, statistics, *eta, *T, eta0, nullptr, 0, fp32_storage ? 1e-5 : 1e-10) ? 1 : 0;
+}
+
 void rlbm_destroy(rlbm_t *h)
 {
     if (!h) return;

@@ -27,7 +27,8 @@ BC_PERIODIC, BC_COPYOUT = 0, 1
 # Symbols declared in include/rlbm.h (checked by the CPU test suite).
 EXPORTS = [
     "rlbm_quadrature", "rlbm_population_bytes", "rlbm_create", "rlbm_create_onlattice",
-    "rlbm_is_onlattice", "rlbm_set_statistics", "rlbm_statistics", "rlbm_quantum_phi", "rlbm_destroy",
+    "rlbm_is_onlattice", "rlbm_set_statistics", "rlbm_statistics", "rlbm_quantum_phi", "rlbm_quantum_solve",
+    "rlbm_destroy",
     "rlbm_last_error", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_get_populations", "rlbm_set_populations",
     "rlbm_current_buffer", "rlbm_steps_done", "rlbm_sync", "rlbm_kernel_launches",
@@ -101,6 +102,10 @@ def lib(path: str = LIB_PATH):
     L.rlbm_statistics.argtypes = [_vp]
     L.rlbm_quantum_phi.restype = ctypes.c_double
     L.rlbm_quantum_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    L.rlbm_quantum_solve.restype = ctypes.c_int
+    L.rlbm_quantum_solve.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
     L.rlbm_destroy.restype = None
     L.rlbm_destroy.argtypes = [_vp]
     L.rlbm_last_error.restype = ctypes.c_char_p
@@ -241,6 +246,18 @@ def quantum_phi(s: int, z: float, statistics: str) -> float:
     Li_s(z) for 'be'; runs on the host."""
     import math
     return lib().rlbm_quantum_phi(int(s), math.log(z), {"fd": 1, "be": -1}[statistics])
+
+
+def quantum_solve(n: float, e: float, g: float, statistics: str, eta0: float = float("nan"),
+                  storage: str = "fp64"):
+    """(eta, T, ok) of the equilibrium with density n and energy density e, as the
+    kernels solve it (rlbm_quantum_solve; storage 'fp32' selects the FP32-storage
+    stopping rule); runs on the host."""
+    eta = ctypes.c_double()
+    T = ctypes.c_double()
+    ok = lib().rlbm_quantum_solve(float(n), float(e), float(g), {"fd": 1, "be": -1}[statistics], float(eta0),
+                                  1 if storage == "fp32" else 0, ctypes.byref(eta), ctypes.byref(T))
+    return eta.value, T.value, bool(ok)
 
 
 def population_bytes(nx, ny, N, K, precision="fp64", bcx=BC_COPYOUT, bcy=BC_PERIODIC) -> int:

@@ -147,6 +147,50 @@ def test_quantum_phi_matches_oracle(lib):
     assert math.isnan(lib.rlbm_quantum_phi(9, -0.1, 1))
 
 
+def test_quantum_solve_matches_oracle(lib):
+    """The kernels' (eta, T) solve (FP32 Newton steps from the start, then FP64
+    Newton steps to the storage's stopping rule; rlbm_stat.cuh compiled into the
+    host library) against the oracle's bracketed root of the same equations
+    (scipy's Brent method on the integral definition of phi), from a cold start
+    and from a start near the root (the previous step's eta in the kernels).
+    FP64 rule within 1e-12.  FP32-storage rule within 1e-9: it accepts a Newton
+    step below 1e-5 (1 + |eta|), and a cold Bose-Einstein start (no FP32 steps
+    for that statistic) can accept one near that size, leaving an error of its
+    square order (2.5e-10 measured), far below the FP32 rounding of 6e-8."""
+    from oracle import statistics as S
+    worst = {"fp64": 0.0, "fp32": 0.0}
+    cases = 0
+    for stat in (S.FD, S.BE):
+        for n in (0.05, 1.0, 7.0):
+            for ratio in (2.0005, 2.01, 2.3, 3.0, 10.0, 100.0):
+                for g in (0.1, 1.0, 4.0):
+                    e = ratio * n ** 1.5
+                    try:
+                        T_ref, z_ref = S.solve_Tz(n, e, stat, g)
+                    except ValueError:  # no equilibrium of this statistic
+                        continue
+                    eta_ref = math.log(z_ref)
+                    for storage in ("fp64", "fp32"):
+                        for eta0 in (float("nan"), eta_ref + 1e-3):
+                            eta, T, ok = R.quantum_solve(n, e, g, "fd" if stat == S.FD else "be", eta0, storage)
+                            assert ok, (stat, n, ratio, g, storage)
+                            err = max(abs(eta - eta_ref) / (1.0 + abs(eta_ref)), abs(T - T_ref) / T_ref)
+                            worst[storage] = max(worst[storage], err)
+                            cases += 1
+    assert cases > 100
+    assert worst["fp64"] < 1e-12 and worst["fp32"] < 1e-9, worst
+    # no equilibrium: Bose-Einstein beyond condensation (with g = 1, e / n^1.5 below
+    # 2 zeta(3) / (zeta(2)^1.5 sqrt(2 pi)) = 0.455), bad input
+    with pytest.raises(ValueError):
+        S.solve_Tz(1.0, 0.3, S.BE, 1.0)
+    eta, T, ok = R.quantum_solve(1.0, 0.3, 1.0, "be")
+    assert not ok
+    assert R.quantum_solve(1.0, 0.5, 1.0, "be")[2]
+    assert R.quantum_solve(-1.0, 2.0, 1.0, "fd")[2] is False
+    assert lib.rlbm_quantum_solve(1.0, 2.0, 1.0, 2, float("nan"), 0, R.ctypes.byref(R.ctypes.c_double()),
+                                  R.ctypes.byref(R.ctypes.c_double())) == 0
+
+
 @pytest.mark.parametrize("args,status,needle", [
     ((R.Grid(8, 1, 0, 0), 6, 16, 1.0, 0), R.ERR_UNSUPPORTED, "N = 2..5"),
     ((R.Grid(8, 1, 0, 0), 5, 10, 1.0, 0), R.ERR_ARG, "K must be"),
