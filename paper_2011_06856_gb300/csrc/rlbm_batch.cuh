@@ -176,8 +176,9 @@ __device__ __forceinline__ bool batch_grid_barrier(const BatchArgs &b, int next_
     return s_ok != 0;
 }
 
+// FP32 storage: at most 80 registers, four 6-warp CTAs per SM (FP64: no bound).
 template <class St, class R, class LR, int N>
-__global__ void __launch_bounds__(kBatchWarps * 32) rlbm_batch_kernel(const BatchArgs b)
+__global__ void __launch_bounds__(kBatchWarps * 32, sizeof(St) == 4 ? 4 : 1) rlbm_batch_kernel(const BatchArgs b)
 {
     __shared__ LR red_all[kBatchWarps * 5 * 32];
     // FP32 storage: the double-float per-site sums of each tile of a unit

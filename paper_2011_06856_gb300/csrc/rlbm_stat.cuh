@@ -41,13 +41,15 @@ RLBM_HD double stat_ipow(double x, int e)
 // costs multiplications only.  d = ((3 + sqrt 8)^n + (3 + sqrt 8)^-n) / 2 is the
 // Chebyshev value T_n(3), from T_{k+1} = 6 T_k - T_{k-1}, T_0 = 1, T_1 = 3.
 constexpr int kStatTerms = 24;
+// 16 terms (error below 2 (3 + sqrt 8)^-16 ~ 1e-12 of the first): the
+// FP32-storage solve, whose accepted FP64 step needs no more.
+constexpr int kStatTermsShort = 16;
 struct StatSeriesTab {
     double w[kStatTerms];   // c_k / d
     double inv[kStatTerms]; // 1 / (k + 1)
 };
-constexpr StatSeriesTab stat_series_tab()
+constexpr StatSeriesTab stat_series_tab(int n)
 {
-    constexpr int n = kStatTerms;
     StatSeriesTab t{};
     double tm = 1.0, tc = 3.0;
     for (int k = 1; k < n; ++k) {
@@ -66,16 +68,18 @@ constexpr StatSeriesTab stat_series_tab()
     return t;
 }
 #ifdef __CUDACC__
-static __constant__ StatSeriesTab kStatSeriesDev = stat_series_tab();
+static __constant__ StatSeriesTab kStatSeriesDev = stat_series_tab(kStatTerms);
+static __constant__ StatSeriesTab kStatSeriesShortDev = stat_series_tab(kStatTermsShort);
 #endif
-static constexpr StatSeriesTab kStatSeriesHost = stat_series_tab();
+static constexpr StatSeriesTab kStatSeriesHost = stat_series_tab(kStatTerms);
+static constexpr StatSeriesTab kStatSeriesShortHost = stat_series_tab(kStatTermsShort);
 
-RLBM_HD const StatSeriesTab &stat_series()
+RLBM_HD const StatSeriesTab &stat_series(bool short_series = false)
 {
 #ifdef __CUDA_ARCH__
-    return kStatSeriesDev;
+    return short_series ? kStatSeriesShortDev : kStatSeriesDev;
 #else
-    return kStatSeriesHost;
+    return short_series ? kStatSeriesShortHost : kStatSeriesHost;
 #endif
 }
 
@@ -96,12 +100,13 @@ RLBM_HDX double stat_alt_series(int s, double x)
 // The same series for every s = 1..smax at once (smax <= 6): the weights of the
 // acceleration do not depend on s, so one pass over the 24 terms serves all
 // orders, out[s-1] = sum_j (-1)^(j+1) x^j / j^s.
-RLBM_HDX void stat_alt_series_upto(int smax, double x, double *out)
+RLBM_HDX void stat_alt_series_upto(int smax, double x, double *out, bool short_series = false)
 {
-    const StatSeriesTab &tab = stat_series();
+    const StatSeriesTab &tab = stat_series(short_series);
+    const int nt = short_series ? kStatTermsShort : kStatTerms;
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double xk = x;
-    for (int k = 0; k < kStatTerms; ++k) {
+    for (int k = 0; k < nt; ++k) {
         double t = tab.w[k] * xk;
         const double r = tab.inv[k];
 #pragma unroll
@@ -166,20 +171,20 @@ RLBM_HDX double stat_be(int s, double eta)
 // phi_1 .. phi_smax at once (smax <= 6): Fermi-Dirac from one pass of the
 // accelerated series (and the inversion identity for eta > 0), Bose-Einstein
 // order by order.
-RLBM_HDX void stat_phi_upto(int smax, double eta, int stat, double *phi)
+RLBM_HDX void stat_phi_upto(int smax, double eta, int stat, double *phi, bool short_series = false)
 {
     if (stat < 0) {
         for (int q = 1; q <= smax; ++q) phi[q - 1] = stat_be(q, eta);
         return;
     }
     if (eta <= 0.0) {
-        stat_alt_series_upto(smax, exp(eta), phi);
+        stat_alt_series_upto(smax, exp(eta), phi, short_series);
         return;
     }
     const double pi2 = 9.8696044010893586188; // pi^2
     const double etaD[4] = {0.5, pi2 / 12.0, 7.0 * pi2 * pi2 / 720.0, 31.0 * pi2 * pi2 * pi2 / 30240.0};
     double mirror[6];
-    stat_alt_series_upto(smax, exp(-eta), mirror);
+    stat_alt_series_upto(smax, exp(-eta), mirror, short_series);
     for (int q = 1; q <= smax; ++q) {
         double poly = 0.0;
         for (int j = 0; 2 * j <= q; ++j) {
@@ -273,10 +278,11 @@ RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, do
     if (x >= hi) x = stat > 0 ? hi - 1.0 : -1e-3;
     if (stat > 0) x = stat_presolve_fd(L, x, lo, hi);
     const int nq = nphi > 6 ? 6 : (nphi > 3 ? nphi : 3);
+    const bool short_series = tol >= 1e-6; // the FP32-storage rule: 16 terms suffice
     bool ok = false;
     double xl = x, phl[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}; // the last evaluation point and phi there
     for (int it = 0; it < 100; ++it) {
-        stat_phi_upto(nq, x, stat, phl);
+        stat_phi_upto(nq, x, stat, phl, short_series);
         xl = x;
         const double p1 = phl[0], p2 = phl[1], p3 = phl[2];
         const double H = log(p3) - 1.5 * log(p2) - L;
@@ -300,7 +306,7 @@ RLBM_HDX bool stat_solve(double n, double e, double g, int stat, double &eta, do
         phr[0] = phl[0] + phi0 * dx;
         for (int q = 1; q < nq; ++q) phr[q] = phl[q] + phl[q - 1] * dx;
     } else {
-        stat_phi_upto(nq, x, stat, phr);
+        stat_phi_upto(nq, x, stat, phr, short_series);
     }
     T = sqrt(n / (twopi * g * phr[1]));
     if (phi_root)
