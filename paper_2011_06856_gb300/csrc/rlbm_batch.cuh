@@ -176,9 +176,11 @@ __device__ __forceinline__ bool batch_grid_barrier(const BatchArgs &b, int next_
     return s_ok != 0;
 }
 
-// FP32 storage: at most 80 registers, four 6-warp CTAs per SM (FP64: no bound).
+// FP32 storage: at most 56 registers, six 6-warp CTAs per SM (FP64: no bound).  On the
+// 256-problem set 4, 5, 6 and 8 CTAs per SM gave 62.9, 57.1, 52.5 and 59.6 ms per time
+// step (more warps hide the per-site chain; at 8 the spills win).
 template <class St, class R, class LR, int N>
-__global__ void __launch_bounds__(kBatchWarps * 32, sizeof(St) == 4 ? 4 : 1) rlbm_batch_kernel(const BatchArgs b)
+__global__ void __launch_bounds__(kBatchWarps * 32, sizeof(St) == 4 ? 6 : 1) rlbm_batch_kernel(const BatchArgs b)
 {
     __shared__ LR red_all[kBatchWarps * 5 * 32];
     // FP32 storage: the double-float per-site sums of each tile of a unit
