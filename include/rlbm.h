@@ -446,16 +446,17 @@ rlbm_status rlbm_closure_set_train_path(rlbm_closure_t *c, int tensor_cores);
  * caller-owned device buffers of N_pop * nx * ny elements each (FP64 or FP32
  * storage, f[i][y][x]; the two byte ranges must not overlap, else
  * RLBM_ERR_ARG), on cuda_stream (NULL: the default stream).  The per-site part
- * runs in FP64 for both storages, as in a handle's per-tile kernel.  This entry
+ * runs in FP64 for both storages (a handle's FP32-storage steps run it in
+ * double-float; the two agree to about 1e-6 over two steps).  This entry
  * point has no counterpart in the paper: it exists for callers that cannot
  * let a library allocate device memory -- their memory comes from their own
  * pool or framework allocator, or they run under a fixed budget -- so it calls
  * no cudaMalloc, cudaFree or other allocating routine.  Its constant tables
  * and status word live in one file-scope __device__ array of 32 KB that every
  * GPU loading the library holds until the process exits; the first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current, so make the first call on each device before any stream
- * capture.  Limits: N in {2, 3}, K (N+1) <= 256 populations; larger sizes
+ * device looks up that array's device address (cudaGetSymbolAddress, kept per
+ * device) with the device current.  A call cannot be captured into a CUDA graph: it copies from pageable host
+ * memory and synchronises its stream (below).  Limits: N in {2, 3}, K (N+1) <= 256 populations; larger sizes
  * return RLBM_ERR_ARG.  Every call rewrites the array and clears its status
  * word, so calls that overlap on the GPU race: serialise them.  Every call
  * copies the tables in from host memory and synchronises the stream to read
